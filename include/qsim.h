@@ -1,0 +1,267 @@
+/*
+ * qsim.h -- C ABI of libqsim, a GB300 (sm_103a) state-vector simulator.
+ *
+ * The library applies quantum gates to a 2^n-amplitude state vector by the
+ * contraction of Eq. (1) of arXiv 2203.08826 (Sec. 1):
+ *
+ *     psi'(s_1..tau..s_n) = sum_{tau'} G(tau, tau') psi(s_1..tau'..s_n)
+ *
+ * in place (Sec. 2: custom operators update the state without a copy), and
+ * measures the result (probabilities, shots, Pauli expectation values).
+ *
+ * Conventions used by every entry point
+ *   - Amplitudes are interleaved (re, im).  QSIM_C64 stores two floats per
+ *     amplitude (8 bytes), QSIM_C128 two doubles (16 bytes).  Amplitude x is at
+ *     element x; qubit q is bit q of x (qubit 0 = least significant bit), as in
+ *     the single-qubit kernel of Sec. 2 which pairs x with x + 2^target.
+ *   - A k-qubit gate matrix is row-major complex128 (2^k * 2^k pairs of
+ *     doubles, re then im), and targets[0] is the MOST significant bit of its
+ *     row/column index: G(tau_1..tau_k, tau_1'..tau_k') of Eq. (1) takes tau_1
+ *     from targets[0].
+ *   - Controls (Sec. 2, "controlled gates") act when all control bits are 1.
+ *   - Host arrays passed in are read during the call and may be reused when it
+ *     returns.  Device work runs asynchronously on the state's CUDA stream;
+ *     calls that return host values synchronise that stream.
+ *
+ * Errors: every int-returning call returns QSIM_OK (0) or a negative code;
+ * qsim_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(QSIM_BUILD) && defined(__GNUC__)
+#define QSIM_API __attribute__((visibility("default")))
+#else
+#define QSIM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define QSIM_OK 0
+#define QSIM_EINVAL (-1)       /* bad argument: qubit >= n, duplicate qubit, k too large, NULL */
+#define QSIM_ENOMEM (-2)       /* a device or host allocation failed */
+#define QSIM_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define QSIM_ETIMEOUT (-4)     /* a bounded device-side wait expired */
+#define QSIM_EUNSUPPORTED (-5) /* valid request that this build cannot run */
+
+#define QSIM_C64 0
+#define QSIM_C128 1
+
+#define QSIM_MAX_TARGETS 6     /* largest dense gate / fused block */
+#define QSIM_MAX_CONTROLS 16
+
+/* ---------------------------------------------------------------- gates */
+/* Named gates; the library builds their matrices itself.
+ *   H X Y Z S T        fixed single-qubit gates
+ *   RX RY RZ (theta)   exp(-i theta P / 2), P the Pauli matrix
+ *   PHASE (phi)        diag(1, e^{i phi})   (with a control: the QFT's R_k)
+ *   CZ                 diag(1, 1, 1, -1) on two targets
+ *   SWAP               exchange of two targets
+ *   SU2 (a, b, c, d)   [[a + ib, c + id], [-c + id, a - ib]] (unit quaternion)
+ *   MATRIX             explicit matrix given by the caller                     */
+enum {
+    QSIM_GATE_MATRIX = 0,
+    QSIM_GATE_H = 1,
+    QSIM_GATE_X = 2,
+    QSIM_GATE_Y = 3,
+    QSIM_GATE_Z = 4,
+    QSIM_GATE_S = 5,
+    QSIM_GATE_T = 6,
+    QSIM_GATE_RX = 7,
+    QSIM_GATE_RY = 8,
+    QSIM_GATE_RZ = 9,
+    QSIM_GATE_PHASE = 10,
+    QSIM_GATE_CZ = 11,
+    QSIM_GATE_SWAP = 12,
+    QSIM_GATE_SU2 = 13
+};
+
+QSIM_API const char *qsim_last_error(void);
+QSIM_API const char *qsim_version(void);
+
+/* ---------------------------------------------------------------- state */
+typedef struct qsim_state qsim_state;
+
+/* Create a state of n qubits (1 <= n <= 34) in precision dtype (QSIM_C64 or
+ * QSIM_C128) whose work runs on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  If dev_ptr is non-NULL it must point to 2^n amplitudes of
+ * device memory, 256-byte aligned, that the caller owns and keeps alive until
+ * qsim_state_destroy (the library borrows it); otherwise the library
+ * allocates the amplitudes and destroy frees them.  The contents are
+ * undefined until qsim_state_init.  Citation: the state vector of 2^n
+ * amplitudes, Sec. 1; in-place updates, Sec. 2. */
+QSIM_API int qsim_state_create(int n, int dtype, void *dev_ptr, void *cuda_stream, qsim_state **out);
+QSIM_API int qsim_state_destroy(qsim_state *s);
+QSIM_API int qsim_state_set_stream(qsim_state *s, void *cuda_stream);
+/* n, dtype and the device pointer of the amplitudes (any may be NULL). */
+QSIM_API int qsim_state_info(const qsim_state *s, int *n, int *dtype, void **dev_ptr);
+
+#define QSIM_INIT_ZERO 0   /* |0...0>                                      */
+#define QSIM_INIT_BASIS 1  /* |basis>                                      */
+#define QSIM_INIT_HOST 2   /* copy 2^n amplitudes (state precision) from host `src` */
+#define QSIM_INIT_DEVICE 3 /* copy 2^n amplitudes (state precision) from device `src` */
+QSIM_API int qsim_state_init(qsim_state *s, int kind, uint64_t basis, const void *src);
+/* Copy all 2^n amplitudes (state precision) to host memory `dst`; synchronous. */
+QSIM_API int qsim_state_copy_to_host(qsim_state *s, void *dst);
+/* Block until all work queued on the state's stream has finished; returns
+ * QSIM_ECUDA if a kernel failed and QSIM_ETIMEOUT if a bounded wait expired. */
+QSIM_API int qsim_synchronize(qsim_state *s);
+
+/* ---------------------------------------------------------------- Eq. (1) */
+/* Apply one gate in place.  matrix: 2^k x 2^k row-major complex128 host array
+ * (targets[0] = most significant matrix bit); targets: k distinct qubits,
+ * 1 <= k <= QSIM_MAX_TARGETS; controls: c distinct qubits not among the
+ * targets (may be NULL when c == 0).  The library classifies the matrix
+ * (Sec. 2: dense, diagonal, permutation-with-phases; a block that leaves a
+ * target untouched when it is 0 becomes a control) and launches one sweep.
+ * Citation: Eq. (1), Sec. 1; single-qubit kernel listing and the
+ * multi-target / controlled / Pauli / SWAP operators, Sec. 2. */
+QSIM_API int qsim_apply_gate(qsim_state *s, const double *matrix, const int *targets, int k,
+                    const int *controls, int c);
+/* Apply a named gate (QSIM_GATE_*; params as listed above, may be NULL). */
+QSIM_API int qsim_apply_named(qsim_state *s, int kind, const int *targets, int k, const int *controls,
+                     int c, const double *params);
+
+/* ---------------------------------------------------------------- circuits */
+typedef struct qsim_circuit qsim_circuit;
+
+QSIM_API int qsim_circuit_create(int n, qsim_circuit **out);
+QSIM_API int qsim_circuit_destroy(qsim_circuit *c);
+/* Append a gate.  params: up to 4 doubles (angle, or the SU2 quaternion);
+ * param_index >= 0 marks an RX/RY/RZ angle as trainable parameter number
+ * param_index (used by qsim_adjoint_grad, which substitutes its own values);
+ * matrix: for QSIM_GATE_MATRIX only, 2^k x 2^k row-major complex128. */
+QSIM_API int qsim_circuit_add(qsim_circuit *c, int kind, const int *targets, int k, const int *controls,
+                     int nc, const double *params, int param_index, const double *matrix);
+QSIM_API int qsim_circuit_info(const qsim_circuit *c, int *n, int *ngates, int *nparams);
+/* Plain execution: one sweep per gate, in order (the unfused baseline). */
+QSIM_API int qsim_run(qsim_state *s, const qsim_circuit *c);
+
+/* ---------------------------------------------------------------- fusion */
+typedef struct qsim_plan qsim_plan;
+
+/* Fusion modes.
+ *   QSIM_FUSE_GREEDY2  the paper's fusion (Sec. 3.2): greedily multiply 1- and
+ *                      2-qubit gates that act on the same targets; one sweep
+ *                      per fused gate.
+ *   QSIM_FUSE_STAGED   cache-blocked stages: each stage loads tiles of 2^m
+ *                      amplitudes spanning a chosen qubit set into shared
+ *                      memory, applies every gate of the stage there (gates on
+ *                      qubits outside the set only if diagonal, or through
+ *                      their controls), and writes the tile back: one HBM pass
+ *                      per stage.
+ *   QSIM_FUSE_TC       dense k-qubit blocks (kmax = 4..6) applied on the
+ *                      tensor cores as split-precision real GEMMs
+ *                      (complex64 states only), with the qubit order rotated
+ *                      by each pass so every block's targets are the low bits.
+ * kmax bounds the targets of a fused block (2..6).  The plan copies what it
+ * needs from the circuit; it does not depend on the circuit afterwards.
+ * Citation: Sec. 3.2 (gate fusion; fusing up to about five qubits may help). */
+#define QSIM_FUSE_GREEDY2 0
+#define QSIM_FUSE_STAGED 1
+#define QSIM_FUSE_TC 2
+QSIM_API int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out);
+QSIM_API int qsim_plan_destroy(qsim_plan *p);
+/* Number of sweeps (HBM passes) and of source gates the plan covers. */
+QSIM_API int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode);
+/* Fused matrix of block i for QSIM_FUSE_GREEDY2 / QSIM_FUSE_TC plans:
+ * writes k and the targets (targets[0] = MSB) and, if matrix_out is non-NULL,
+ * the 2^k x 2^k row-major complex128 matrix.  Host-only; no GPU needed. */
+QSIM_API int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *matrix_out);
+/* Execute a plan on a state of the circuit's width and precision. */
+QSIM_API int qsim_apply_fused(qsim_state *s, const qsim_plan *p);
+
+/* ---------------------------------------------------------------- measurement */
+/* Probabilities (Sec. 2, measurement operators).  m = 0 or qubits == NULL:
+ * out[x] = |psi(x)|^2 for all 2^n x.  Otherwise the marginal over qubits[0..m-1]
+ * (distinct, qubits[0] = most significant bit of the output index):
+ * out[y] = sum over x whose listed bits spell y of |psi(x)|^2, 2^m doubles.
+ * out is device memory if out_on_device, else host memory (then synchronous).
+ * |psi|^2 is formed as re*re + im*im in double with no fused multiply-add. */
+QSIM_API int qsim_probabilities(qsim_state *s, const int *qubits, int m, double *out, int out_on_device);
+/* Squared norm sum_x |psi(x)|^2, accumulated in double; synchronous. */
+QSIM_API int qsim_norm2(qsim_state *s, double *out);
+
+/* Shot sampling by inverse CDF over integer weights (replaces the paper's
+ * Metropolis sampler, Sec. 2, so that shots are reproducible bit for bit):
+ *   w(x) = floor(p(x) 2^62), p(x) = |psi(x)|^2;  CDF(x) = w(0) + ... + w(x)
+ *   shot s uses Philox4x32-10 (Salmon et al., SC'11) with counter
+ *   (lo32(counter0 + s), hi32(counter0 + s), 0, 0) and key (lo32(seed),
+ *   hi32(seed)); with outputs o0, o1: u = o1 * 2^32 + o0,
+ *   r = floor(u * CDF(N-1) / 2^64), and the shot is the smallest x with
+ *   CDF(x) > r.
+ * out: nshots uint64 bitstrings, device memory if out_on_device, else host
+ * (synchronous).  The library keeps a scratch array of N/2048 + 1 uint64 in
+ * the state.  Returns QSIM_EINVAL if sum p > 1.5 or the weights sum to 0. */
+QSIM_API int qsim_sample(qsim_state *s, uint64_t nshots, uint64_t seed, uint64_t counter0, uint64_t *out,
+                int out_on_device);
+/* The same sampler on caller-supplied probabilities: p_dev is device memory
+ * holding N doubles (N >= 1).  Runs on `cuda_stream` and allocates its scratch
+ * (N/2048 + 1 uint64) for the duration of the call. */
+QSIM_API int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
+                      uint64_t counter0, uint64_t *out, int out_on_device, void *cuda_stream);
+
+/* Pauli expectation <psi| sum_t coeff[t] P_t |psi> with P_t given by bit masks
+ * (bit q of xmask/zmask: X = (1,0), Y = (1,1), Z = (0,1) on qubit q):
+ *   P|y> = i^{#Y} (-1)^{popcount(y & zmask)} |y ^ xmask>.
+ * Terms sharing an xmask are evaluated in one pass; partial sums are
+ * accumulated in double.  Host arrays of nterms entries; *out (host) receives
+ * the real part; synchronous.  (TFIM-type Hamiltonians, Sec. 3.3.) */
+QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *xmask,
+                           const uint64_t *zmask, const double *coeff, double *out);
+
+/* ---------------------------------------------------------------- gradients */
+/* Adjoint-method gradient of E(theta) = <0|U(theta)^dag H U(theta)|0> for every
+ * trainable parameter of circuit c (RX/RY/RZ gates with param_index >= 0),
+ * for nsets parameter vectors: params is nsets x nparams (host, row-major).
+ * Writes grads (nsets x nparams, host) and energies (nsets, host; may be NULL).
+ * One forward sweep, then one reverse sweep that un-applies each gate to the
+ * state and to lambda = H psi and accumulates 2 Re<lambda|dU psi> in double.
+ * dtype: QSIM_C64 or QSIM_C128.  Allocates three states per set in flight.
+ * (The paper obtains gradients only through TensorFlow autodiff, Sec. 2.) */
+QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, const double *params,
+                      int nterms, const uint64_t *xmask, const uint64_t *zmask,
+                      const double *coeff, double *grads, double *energies, void *cuda_stream);
+
+/* ---------------------------------------------------------------- batches */
+typedef struct qsim_batch qsim_batch;
+
+/* A batch of many small circuits (2 <= n <= 20 qubits each, complex64 states)
+ * run by one persistent kernel: each CTA takes the next circuit from a device
+ * work counter (largest first), simulates it with its state resident in
+ * shared memory (n <= 14) or in a per-CTA global slot streamed through shared
+ * memory tiles (n > 14), and writes <sum_i Z_i Z_{i+1}> of its final state.
+ * The plan (gate tables) is uploaded once at creation. */
+QSIM_API int qsim_batch_create(int ncircuits, const qsim_circuit *const *circuits, qsim_batch **out);
+QSIM_API int qsim_batch_destroy(qsim_batch *b);
+/* Run every circuit from |0...0> on `cuda_stream`; out_dev: device array of
+ * ncircuits doubles receiving <sum_{i=0}^{n-2} Z_i Z_{i+1}> per circuit.
+ * Safe to capture in a CUDA graph (the work counter is reset by a memset
+ * node inside the captured sequence). */
+QSIM_API int qsim_batch_run(qsim_batch *b, double *out_dev, void *cuda_stream);
+/* Tuning knobs (threads per CTA, tile qubits); 0 = automatic. */
+QSIM_API int qsim_batch_set_config(qsim_batch *b, int threads, int tile_qubits);
+
+/* ---------------------------------------------------------------- profiling */
+/* Launch accounting for every kernel the library starts.  When enabled, each
+ * launch is bracketed by CUDA events on its own stream; qsim_profile_get
+ * synchronises those events and reports, per kernel name, the launches, the
+ * summed device time and the summed algorithmic bytes moved. */
+QSIM_API int qsim_profile_enable(int on);
+QSIM_API int qsim_profile_reset(void);
+QSIM_API int qsim_profile_count(int *nkinds);
+QSIM_API int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total_ms,
+                     double *total_bytes);
+/* Total kernel launches issued by the library since load (always counted). */
+QSIM_API uint64_t qsim_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

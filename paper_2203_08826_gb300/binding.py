@@ -1,0 +1,380 @@
+"""Thin ctypes binding of libqsim (argument marshalling only).
+
+Every function here forwards to the C ABI declared in ``include/qsim.h``;
+no simulation arithmetic happens in Python.  PyTorch supplies device memory
+(state tensors) and the CUDA stream (``torch.cuda.current_stream()``).
+The library must have been built (``paper_2203_08826_gb300.build.build()``);
+loading raises ``QsimError`` otherwise -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Sequence
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
+
+C64, C128 = 0, 1
+FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
+INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE = 0, 1, 2, 3
+GATE_KIND = {"matrix": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "t": 6, "rx": 7, "ry": 8,
+             "rz": 9, "phase": 10, "cz": 11, "swap": 12, "su2": 13}
+
+
+class QsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qsim error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+P, I, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+_SIGS = {
+    "qsim_last_error": ([], ctypes.c_char_p),
+    "qsim_version": ([], ctypes.c_char_p),
+    "qsim_state_create": ([I, I, P, P, P], I),
+    "qsim_state_destroy": ([P], I),
+    "qsim_state_set_stream": ([P, P], I),
+    "qsim_state_info": ([P, P, P, P], I),
+    "qsim_state_init": ([P, I, U64, P], I),
+    "qsim_state_copy_to_host": ([P, P], I),
+    "qsim_synchronize": ([P], I),
+    "qsim_apply_gate": ([P, P, P, I, P, I], I),
+    "qsim_apply_named": ([P, I, P, I, P, I, P], I),
+    "qsim_circuit_create": ([I, P], I),
+    "qsim_circuit_destroy": ([P], I),
+    "qsim_circuit_add": ([P, I, P, I, P, I, P, I, P], I),
+    "qsim_circuit_info": ([P, P, P, P], I),
+    "qsim_run": ([P, P], I),
+    "qsim_plan_build": ([P, I, I, P], I),
+    "qsim_plan_destroy": ([P], I),
+    "qsim_plan_info": ([P, P, P, P], I),
+    "qsim_plan_block": ([P, I, P, P, P], I),
+    "qsim_apply_fused": ([P, P], I),
+    "qsim_probabilities": ([P, P, I, P, I], I),
+    "qsim_norm2": ([P, P], I),
+    "qsim_sample": ([P, U64, U64, U64, P, I], I),
+    "qsim_sample_probs": ([P, U64, U64, U64, U64, P, I, P], I),
+    "qsim_expectation_pauli": ([P, I, P, P, P, P], I),
+    "qsim_adjoint_grad": ([P, I, I, P, I, P, P, P, P, P, P], I),
+    "qsim_batch_create": ([I, P, P], I),
+    "qsim_batch_destroy": ([P], I),
+    "qsim_batch_run": ([P, P, P], I),
+    "qsim_batch_set_config": ([P, I, I], I),
+    "qsim_profile_enable": ([I], I),
+    "qsim_profile_reset": ([], I),
+    "qsim_profile_count": ([P], I),
+    "qsim_profile_get": ([I, P, P, P, P], I),
+    "qsim_launch_count": ([], U64),
+}
+
+
+def lib():
+    """The loaded libqsim (raises QsimError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise QsimError(-5, f"{LIB_PATH} not built; run paper_2203_08826_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name, None)
+                if f is None:
+                    continue
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise QsimError(rc, lib().qsim_last_error().decode())
+
+
+def _arr(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ circuits
+class QCircuit:
+    """A circuit handle in the library, built from an ``inputs.Circuit``."""
+
+    def __init__(self, circuit: inputs.Circuit):
+        self.n = circuit.n
+        self.source = circuit
+        h = ctypes.c_void_p()
+        _check(lib().qsim_circuit_create(circuit.n, ctypes.byref(h)))
+        self.handle = h
+        for g in circuit.gates:
+            t = _arr(g.targets, np.int32)
+            c = _arr(g.controls if len(g.controls) else [0], np.int32)
+            prm = _arr(list(g.params) + [0.0] * (4 - len(g.params)) if g.name != "matrix" else [0.0] * 4,
+                       np.float64)
+            mat = None
+            if g.name == "matrix":
+                mat = _arr(np.asarray(g.matrix, dtype=np.complex128).view(np.float64), np.float64)
+            _check(lib().qsim_circuit_add(h, GATE_KIND[g.name], _p(t), len(g.targets),
+                                          _p(c) if len(g.controls) else None, len(g.controls),
+                                          _p(prm), g.pindex, _p(mat) if mat is not None else None))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsim_circuit_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def ngates(self) -> int:
+        n = ctypes.c_int(); g = ctypes.c_int(); p = ctypes.c_int()
+        _check(lib().qsim_circuit_info(self.handle, ctypes.byref(n), ctypes.byref(g), ctypes.byref(p)))
+        return g.value
+
+    @property
+    def nparams(self) -> int:
+        n = ctypes.c_int(); g = ctypes.c_int(); p = ctypes.c_int()
+        _check(lib().qsim_circuit_info(self.handle, ctypes.byref(n), ctypes.byref(g), ctypes.byref(p)))
+        return p.value
+
+
+class Plan:
+    """A fusion plan (QSIM_FUSE_GREEDY2 / STAGED / TC) built on the host."""
+
+    def __init__(self, circuit, kmax: int = 2, mode: int = FUSE_GREEDY2):
+        qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+        self.n = qc.n
+        h = ctypes.c_void_p()
+        _check(lib().qsim_plan_build(qc.handle, kmax, mode, ctypes.byref(h)))
+        self.handle = h
+        self.mode = mode
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsim_plan_destroy(self.handle)
+            self.handle = None
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().qsim_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"sweeps": a.value, "gates": b.value, "mode": c.value}
+
+    def block(self, i: int):
+        k = ctypes.c_int()
+        t = np.zeros(8, dtype=np.int32)
+        _check(lib().qsim_plan_block(self.handle, i, ctypes.byref(k), _p(t), None))
+        m = np.zeros((1 << k.value) ** 2 * 2, dtype=np.float64)
+        _check(lib().qsim_plan_block(self.handle, i, ctypes.byref(k), _p(t), _p(m)))
+        d = 1 << k.value
+        return tuple(int(v) for v in t[: k.value]), m.view(np.complex128).reshape(d, d)
+
+
+# ------------------------------------------------------------------ state
+class State:
+    """A 2^n-amplitude state in a torch CUDA tensor, driven through libqsim."""
+
+    def __init__(self, n: int, dtype: str = "c64", tensor=None, stream=None):
+        torch = _torch()
+        self.n = n
+        self.dtype = C64 if dtype in ("c64", "complex64", C64) else C128
+        tdt = torch.complex64 if self.dtype == C64 else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=tdt, device="cuda")
+        assert tensor.dtype == tdt and tensor.numel() == 1 << n and tensor.is_contiguous()
+        self.tensor = tensor
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib().qsim_state_create(n, self.dtype, ctypes.c_void_p(tensor.data_ptr()),
+                                       _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsim_state_destroy(self.handle)
+            self.handle = None
+
+    # -- initialisation / transfer
+    def init_zero(self):
+        _check(lib().qsim_state_init(self.handle, INIT_ZERO, 0, None)); return self
+
+    def init_basis(self, b: int):
+        _check(lib().qsim_state_init(self.handle, INIT_BASIS, b, None)); return self
+
+    def from_host(self, amps: np.ndarray):
+        a = _arr(amps, np.complex64 if self.dtype == C64 else np.complex128)
+        assert a.size == 1 << self.n
+        _check(lib().qsim_state_init(self.handle, INIT_HOST, 0, _p(a)))
+        self.synchronize()
+        return self
+
+    def from_host_async(self, pinned):
+        """Start a host->device copy from a pinned torch tensor (kept alive by the caller)."""
+        _check(lib().qsim_state_init(self.handle, INIT_HOST, 0, ctypes.c_void_p(pinned.data_ptr())))
+        return self
+
+    def to_host(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.complex64 if self.dtype == C64 else np.complex128)
+        _check(lib().qsim_state_copy_to_host(self.handle, _p(out)))
+        return out
+
+    def to_host_into(self, pinned):
+        _check(lib().qsim_state_copy_to_host(self.handle, ctypes.c_void_p(pinned.data_ptr())))
+
+    def synchronize(self):
+        _check(lib().qsim_synchronize(self.handle))
+
+    # -- gates
+    def apply_matrix(self, G, targets: Sequence[int], controls: Sequence[int] = ()):
+        m = _arr(np.asarray(G, dtype=np.complex128).view(np.float64), np.float64)
+        t = _arr(targets, np.int32)
+        c = _arr(controls if len(controls) else [0], np.int32)
+        _check(lib().qsim_apply_gate(self.handle, _p(m), _p(t), len(targets),
+                                     _p(c) if len(controls) else None, len(controls)))
+
+    def apply(self, g: inputs.Gate):
+        if g.name == "matrix":
+            return self.apply_matrix(g.matrix, g.targets, g.controls)
+        t = _arr(g.targets, np.int32)
+        c = _arr(g.controls if len(g.controls) else [0], np.int32)
+        prm = _arr(list(g.params) + [0.0] * (4 - len(g.params)), np.float64)
+        _check(lib().qsim_apply_named(self.handle, GATE_KIND[g.name], _p(t), len(g.targets),
+                                      _p(c) if len(g.controls) else None, len(g.controls), _p(prm)))
+
+    def run(self, circuit):
+        qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+        _check(lib().qsim_run(self.handle, qc.handle))
+        return qc
+
+    def run_fused(self, plan: Plan):
+        _check(lib().qsim_apply_fused(self.handle, plan.handle))
+
+    # -- measurement
+    def probabilities(self, qubits: Sequence[int] | None = None, out=None):
+        """Host numpy array, or fills the device tensor ``out`` (float64)."""
+        q = _arr(qubits if qubits else [0], np.int32)
+        m = len(qubits) if qubits else 0
+        size = 1 << (m if m else self.n)
+        if out is not None:
+            assert out.numel() == size and out.dtype == _torch().float64
+            _check(lib().qsim_probabilities(self.handle, _p(q) if m else None, m,
+                                            ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        host = np.zeros(size, dtype=np.float64)
+        _check(lib().qsim_probabilities(self.handle, _p(q) if m else None, m, _p(host), 0))
+        return host
+
+    def norm2(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().qsim_norm2(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def sample(self, nshots: int, seed: int, counter0: int = 0, out=None):
+        if out is not None:
+            _check(lib().qsim_sample(self.handle, nshots, seed, counter0, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        host = np.zeros(max(nshots, 1), dtype=np.uint64)
+        _check(lib().qsim_sample(self.handle, nshots, seed & (2**64 - 1), counter0 & (2**64 - 1),
+                                 _p(host), 0))
+        return host[:nshots]
+
+    def expectation(self, ham: inputs.PauliSum) -> float:
+        xm, zm, c = _arr(ham.xmask, np.uint64), _arr(ham.zmask, np.uint64), _arr(ham.coeff, np.float64)
+        v = ctypes.c_double()
+        _check(lib().qsim_expectation_pauli(self.handle, len(c), _p(xm), _p(zm), _p(c), ctypes.byref(v)))
+        return v.value
+
+
+def sample_probs(p_dev, nshots: int, seed: int, counter0: int = 0, stream=None) -> np.ndarray:
+    """Sampler on a device float64 tensor of probabilities (host result)."""
+    host = np.zeros(max(nshots, 1), dtype=np.uint64)
+    _check(lib().qsim_sample_probs(ctypes.c_void_p(p_dev.data_ptr()), p_dev.numel(), nshots,
+                                   seed & (2**64 - 1), counter0 & (2**64 - 1), _p(host), 0,
+                                   _stream_ptr(stream)))
+    return host[:nshots]
+
+
+# ------------------------------------------------------------------ gradients
+def adjoint_grad(circuit, ham: inputs.PauliSum, params: np.ndarray, dtype: str = "c64", stream=None):
+    """Gradients (nsets x nparams) and energies (nsets) by the adjoint method."""
+    qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+    params = _arr(np.atleast_2d(params), np.float64)
+    nsets, npar = params.shape
+    grads = np.zeros((nsets, npar), dtype=np.float64)
+    en = np.zeros(nsets, dtype=np.float64)
+    xm, zm, c = _arr(ham.xmask, np.uint64), _arr(ham.zmask, np.uint64), _arr(ham.coeff, np.float64)
+    _check(lib().qsim_adjoint_grad(qc.handle, C64 if dtype == "c64" else C128, nsets, _p(params), len(c),
+                                   _p(xm), _p(zm), _p(c), _p(grads), _p(en), _stream_ptr(stream)))
+    return grads, en
+
+
+# ------------------------------------------------------------------ batches
+class Batch:
+    def __init__(self, circuits: Iterable[inputs.Circuit]):
+        self.qcs = [c if isinstance(c, QCircuit) else QCircuit(c) for c in circuits]
+        arr = (ctypes.c_void_p * len(self.qcs))(*[q.handle.value for q in self.qcs])
+        h = ctypes.c_void_p()
+        _check(lib().qsim_batch_create(len(self.qcs), arr, ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsim_batch_destroy(self.handle)
+            self.handle = None
+
+    def set_config(self, threads: int = 0, tile_qubits: int = 0):
+        _check(lib().qsim_batch_set_config(self.handle, threads, tile_qubits))
+
+    def run(self, out, stream=None):
+        _check(lib().qsim_batch_run(self.handle, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+
+# ------------------------------------------------------------------ profiling
+def profile_enable(on: bool = True):
+    _check(lib().qsim_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib().qsim_profile_reset())
+
+
+def profile_read() -> dict:
+    n = ctypes.c_int()
+    _check(lib().qsim_profile_count(ctypes.byref(n)))
+    out = {}
+    for i in range(n.value):
+        name = ctypes.c_char_p(); l = ctypes.c_uint64(); ms = ctypes.c_double(); by = ctypes.c_double()
+        _check(lib().qsim_profile_get(i, ctypes.byref(name), ctypes.byref(l), ctypes.byref(ms),
+                                      ctypes.byref(by)))
+        if l.value:
+            out[name.value.decode()] = {"launches": l.value, "ms": ms.value, "bytes": by.value}
+    return out
+
+
+def launch_count() -> int:
+    return int(lib().qsim_launch_count())
+
+
+def version() -> str:
+    return lib().qsim_version().decode()

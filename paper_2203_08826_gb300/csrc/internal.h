@@ -1,0 +1,137 @@
+// Internal declarations shared by the translation units of libqsim.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+#define QSIM_CUDA_TRY(call, what)                                   \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::qsim::cuda_error(e_, what);  \
+    } while (0)
+#define QSIM_TRY(call)                 \
+    do {                               \
+        int rc_ = (call);              \
+        if (rc_ != QSIM_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------ profiling
+// Kernel families; names are what profiling reports.
+enum KernelKind {
+    K_INIT = 0,
+    K_DENSE1,
+    K_DENSEK,
+    K_DIAG,
+    K_MONO,
+    K_PROBS,
+    K_MARGINAL,
+    K_REDUCE,
+    K_EXPECT,
+    K_SAMPLE_CHUNK,
+    K_SAMPLE_SCAN,
+    K_SAMPLE_DRAW,
+    K_STAGE,
+    K_TC_BLOCK,
+    K_BATCH,
+    K_ADJ_STEP,
+    K_HAPPLY,
+    K_COPY,
+    K_NUM_KINDS
+};
+const char *kernel_name(int kind);
+
+// RAII bracket around one launch: counts it and, when profiling is on,
+// records CUDA events on `stream` before and after.
+struct LaunchScope {
+    LaunchScope(int kind, cudaStream_t stream, double bytes);
+    ~LaunchScope();
+    int kind;
+    cudaStream_t stream;
+    int slot;
+};
+
+// ------------------------------------------------------------------ index maps
+// Expansion of a compact group index g into an amplitude index: a zero bit is
+// inserted at every listed position (ascending), then `set` is ORed in.
+constexpr int MAX_INS = QSIM_MAX_TARGETS + QSIM_MAX_CONTROLS;
+struct IndexMap {
+    int nins;
+    int ins[MAX_INS];
+    uint64_t set;
+};
+IndexMap make_index_map(const int *zero_bits, int nz, const int *one_bits, int no);
+// Offsets of the 2^k amplitudes of a group (matrix index j, targets[0] = MSB).
+struct Offsets {
+    uint64_t o[1 << QSIM_MAX_TARGETS];
+};
+
+// ------------------------------------------------------------------ gate ops
+// One launchable sweep after classification of a gate.
+struct Op {
+    enum Type { IDENTITY, DENSE, DIAG, MONO } type = IDENTITY;
+    int k = 0;                       // targets (matrix MSB first)
+    int targets[QSIM_MAX_TARGETS] = {};
+    int c = 0;                       // controls (all must be 1)
+    int controls[QSIM_MAX_CONTROLS + QSIM_MAX_TARGETS] = {};
+    std::vector<cd> m;               // DENSE: 2^k x 2^k; DIAG: 2^k entries
+    std::vector<int> perm;           // MONO: row r takes column perm[r]
+    std::vector<cd> phase;           // MONO: coefficient of row r
+};
+
+// Build a named gate's matrix (the library's own definitions).
+int gate_matrix(int kind, int k, const double *params, const double *matrix, std::vector<cd> &out);
+// Classify (dense / diagonal / monomial) and turn block-identity targets into controls.
+int classify(const std::vector<cd> &m, const int *targets, int k, const int *controls, int c,
+             Op &op);
+int validate_qubits(int n, const int *targets, int k, const int *controls, int c);
+
+// ------------------------------------------------------------------ launchers
+// All launchers are asynchronous on `st` and return QSIM_OK or an error code.
+int launch_op(void *psi, int n, int dtype, const Op &op, cudaStream_t st, void *mat_dev);
+int launch_init(void *psi, int n, int dtype, uint64_t basis, cudaStream_t st);
+int launch_probs(const void *psi, int n, int dtype, double *out, cudaStream_t st);
+int launch_marginal(const void *psi, int n, int dtype, const int *qubits, int m, double *out,
+                    double *scratch, size_t scratch_doubles, cudaStream_t st);
+size_t marginal_scratch_doubles(int n, int m);
+int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result,
+                 cudaStream_t st);
+size_t reduce_partials_needed(int n);
+int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t *xmask,
+                  const uint64_t *zmask, const double *coeff, double *partials,
+                  size_t npartials, double *result, cudaStream_t st);
+size_t sample_scratch_u64(uint64_t N);
+int launch_sample(const void *src, int src_kind, uint64_t N, uint64_t nshots, uint64_t seed,
+                  uint64_t counter0, uint64_t *out_dev, uint64_t *scratch, double *psum_dev,
+                  cudaStream_t st);
+enum { SRC_C64 = 0, SRC_C128 = 1, SRC_PROBS = 2 };
+
+}  // namespace qsim
+
+// ------------------------------------------------------------------ state
+struct qsim_state {
+    int n = 0;
+    int dtype = QSIM_C64;
+    void *amps = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // grow-only scratch owned by the state (reductions, sampler, matrices)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int ensure_scratch(size_t bytes);
+    size_t amp_bytes() const { return dtype == QSIM_C64 ? 8 : 16; }
+    uint64_t size() const { return uint64_t(1) << n; }
+};

@@ -1,0 +1,506 @@
+// Measurement kernels: probabilities, marginals, squared norm, Pauli
+// expectations (double accumulation, warp-shuffle trees) and the inverse-CDF
+// shot sampler with Philox4x32-10 (measurement operators, Sec. 2).
+#include "internal.h"
+
+namespace qsim {
+
+// |psi|^2 in double without contraction into an FMA, so that the result does
+// not depend on how the compiler schedules the two products.
+__device__ __forceinline__ double prob_of(float2 a) {
+    const double re = a.x, im = a.y;
+    return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+}
+__device__ __forceinline__ double prob_of(double2 a) {
+    return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum, result valid in thread 0.  blockDim.x must be a multiple of 32.
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = 0;
+    if (w == 0) {
+        v = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ probabilities
+template <typename C>
+__global__ void k_probs(const C *__restrict__ psi, uint64_t N, double *__restrict__ out) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = prob_of(psi[i]);
+}
+
+int launch_probs(const void *psi, int n, int dtype, double *out, cudaStream_t st) {
+    const uint64_t N = uint64_t(1) << n;
+    const int T = 256;
+    const int blocks = int(std::min<uint64_t>((N + T - 1) / T, uint64_t(sm_count()) * 16));
+    LaunchScope ls(K_PROBS, st, double(N) * ((dtype == QSIM_C64 ? 8 : 16) + 8));
+    if (dtype == QSIM_C64)
+        k_probs<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, out);
+    else
+        k_probs<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), N, out);
+    QSIM_CUDA_TRY(cudaGetLastError(), "probabilities launch");
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ marginals
+// Output bit (m-1-i) of y is amplitude bit qubits[i].
+struct MargParams {
+    int m;
+    int q[64];
+};
+
+__device__ __forceinline__ uint64_t gather_bits(uint64_t x, const MargParams &p) {
+    uint64_t y = 0;
+    for (int i = 0; i < p.m; ++i) y = (y << 1) | ((x >> p.q[i]) & 1);
+    return y;
+}
+
+// few bins: per-CTA shared-memory histogram, then per-CTA rows in scratch
+template <typename C>
+__global__ void k_marg_hist(const C *__restrict__ psi, uint64_t N, MargParams p, double *__restrict__ rows) {
+    extern __shared__ double hist[];
+    const int nb = 1 << p.m;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride)
+        atomicAdd(&hist[gather_bits(x, p)], prob_of(psi[x]));
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) rows[uint64_t(blockIdx.x) * nb + i] = hist[i];
+}
+
+__global__ void k_marg_rows(const double *__restrict__ rows, int nrows, int nb, double *__restrict__ out) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= nb) return;
+    double s = 0;
+    for (int r = 0; r < nrows; ++r) s += rows[uint64_t(r) * nb + y];
+    out[y] = s;
+}
+
+// many bins: one thread per output, summing over the complementary bits
+template <typename C>
+__global__ void k_marg_many(const C *__restrict__ psi, uint64_t nout, uint64_t nrest, MargParams p,
+                            IndexMap zero_at_listed, double *__restrict__ out) {
+    const uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (y >= nout) return;
+    uint64_t ybits = 0;
+    for (int i = 0; i < p.m; ++i)
+        if ((y >> (p.m - 1 - i)) & 1) ybits |= uint64_t(1) << p.q[i];
+    double s = 0;
+    for (uint64_t z = 0; z < nrest; ++z) {
+        uint64_t x = z;
+        for (int i = 0; i < zero_at_listed.nins; ++i) {
+            const uint64_t low = x & ((uint64_t(1) << zero_at_listed.ins[i]) - 1);
+            x = ((x ^ low) << 1) | low;
+        }
+        s += prob_of(psi[x | ybits]);
+    }
+    out[y] = s;
+}
+
+static int marg_blocks() { return sm_count() * 2; }
+
+size_t marginal_scratch_doubles(int n, int m) {
+    (void)n;
+    return m <= 12 ? size_t(marg_blocks()) << m : 0;
+}
+
+int launch_marginal(const void *psi, int n, int dtype, const int *qubits, int m, double *out,
+                    double *scratch, size_t scratch_doubles, cudaStream_t st) {
+    if (m > 62) return set_error(QSIM_EINVAL, "too many qubits");
+    MargParams p{};
+    p.m = m;
+    for (int i = 0; i < m; ++i) p.q[i] = qubits[i];
+    const uint64_t N = uint64_t(1) << n;
+    const double bytes = double(N) * (dtype == QSIM_C64 ? 8 : 16);
+    if (m <= 12) {
+        const int blocks = marg_blocks(), T = 256, nb = 1 << m;
+        if (scratch_doubles < size_t(blocks) * nb) return set_error(QSIM_EINVAL, "marginal scratch too small");
+        {
+            LaunchScope ls(K_MARGINAL, st, bytes);
+            if (dtype == QSIM_C64)
+                k_marg_hist<<<blocks, T, nb * sizeof(double), st>>>(static_cast<const float2 *>(psi), N, p, scratch);
+            else
+                k_marg_hist<<<blocks, T, nb * sizeof(double), st>>>(static_cast<const double2 *>(psi), N, p, scratch);
+            QSIM_CUDA_TRY(cudaGetLastError(), "marginal launch");
+        }
+        LaunchScope ls(K_REDUCE, st, double(blocks) * nb * 8);
+        k_marg_rows<<<(nb + 255) / 256, 256, 0, st>>>(scratch, blocks, nb, out);
+        QSIM_CUDA_TRY(cudaGetLastError(), "marginal rows launch");
+        return QSIM_OK;
+    }
+    int sorted[64];
+    for (int i = 0; i < m; ++i) sorted[i] = qubits[i];
+    if (m > MAX_INS) {
+        // more listed qubits than an IndexMap holds: fall back to a wider map
+        return set_error(QSIM_EUNSUPPORTED, "marginals over more than %d qubits with m > 12", MAX_INS);
+    }
+    const IndexMap zmap = make_index_map(sorted, m, nullptr, 0);
+    const uint64_t nout = uint64_t(1) << m, nrest = uint64_t(1) << (n - m);
+    LaunchScope ls(K_MARGINAL, st, bytes);
+    if (dtype == QSIM_C64)
+        k_marg_many<<<unsigned((nout + 255) / 256), 256, 0, st>>>(static_cast<const float2 *>(psi), nout, nrest, p,
+                                                                   zmap, out);
+    else
+        k_marg_many<<<unsigned((nout + 255) / 256), 256, 0, st>>>(static_cast<const double2 *>(psi), nout, nrest, p,
+                                                                   zmap, out);
+    QSIM_CUDA_TRY(cudaGetLastError(), "marginal launch");
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ reductions
+static int reduce_blocks() { return sm_count() * 4; }
+size_t reduce_partials_needed(int n) {
+    (void)n;
+    return size_t(reduce_blocks());
+}
+
+// Squared norm, accumulated in double per thread, per warp and per block.
+template <typename C>
+__global__ void __launch_bounds__(256) k_norm2(const C *__restrict__ psi, uint64_t N, double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const C a = psi[i];
+        acc += double(a.x) * double(a.x) + double(a.y) * double(a.y);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// result (+)= sum of partials, in a fixed order (one block)
+__global__ void k_sum_partials(const double *__restrict__ partials, int np, double *__restrict__ result,
+                               int accumulate) {
+    double acc = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *result = accumulate ? *result + acc : acc;
+}
+
+int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result, cudaStream_t st) {
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = reduce_blocks(), T = 256;
+    {
+        LaunchScope ls(K_REDUCE, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
+        if (dtype == QSIM_C64)
+            k_norm2<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, partials);
+        else
+            k_norm2<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), N, partials);
+        QSIM_CUDA_TRY(cudaGetLastError(), "norm launch");
+    }
+    LaunchScope ls(K_REDUCE, st, blocks * 8.0);
+    k_sum_partials<<<1, 256, 0, st>>>(partials, blocks, result, 0);
+    QSIM_CUDA_TRY(cudaGetLastError(), "norm sum launch");
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ Pauli expectation
+// One pass per distinct xmask X.  With f(y) = sum_t c_t (-1)^{popcount(y & z_t)}
+// (c_t = coeff_t * i^{#Y_t}) the group contributes sum_y conj(psi[y ^ X]) f(y) psi[y].
+// For X != 0 the pass visits each pair {y, y ^ X} once (bit h = top bit of X is 0).
+constexpr int EXP_TERMS = 64;
+struct ExpParams {
+    uint64_t X;
+    int h;  // highest set bit of X, -1 for X == 0
+    int nt;
+    uint64_t z[EXP_TERMS];
+    double cr[EXP_TERMS];
+    double ci[EXP_TERMS];
+};
+
+__device__ __forceinline__ void f_of(uint64_t y, const ExpParams &p, double &fr, double &fi) {
+    fr = 0;
+    fi = 0;
+    for (int t = 0; t < p.nt; ++t) {
+        const double s = (__popcll(y & p.z[t]) & 1) ? -1.0 : 1.0;
+        fr += s * p.cr[t];
+        fi += s * p.ci[t];
+    }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_expect(const C *__restrict__ psi, uint64_t count, ExpParams p,
+                                                double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < count; g += stride) {
+        if (p.h < 0) {
+            const C a = psi[g];
+            double fr, fi;
+            f_of(g, p, fr, fi);
+            acc += (double(a.x) * a.x + double(a.y) * a.y) * fr;
+        } else {
+            const uint64_t low = g & ((uint64_t(1) << p.h) - 1);
+            const uint64_t y = ((g ^ low) << 1) | low;  // bit h of y is 0
+            const uint64_t y2 = y ^ p.X;
+            const C a = psi[y], b = psi[y2];
+            double fr, fi, gr, gi;
+            f_of(y, p, fr, fi);
+            f_of(y2, p, gr, gi);
+            // Re[conj(b) f(y) a + conj(a) f(y2) b]
+            const double bar = double(b.x) * a.x + double(b.y) * a.y;   // Re(conj(b) a)
+            const double bai = double(b.x) * a.y - double(b.y) * a.x;   // Im(conj(b) a)
+            acc += fr * bar - fi * bai;
+            acc += gr * bar + gi * bai;  // conj(a) b = conj(conj(b) a)
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t *xmask, const uint64_t *zmask,
+                  const double *coeff, double *partials, size_t npartials, double *result, cudaStream_t st) {
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = reduce_blocks(), T = 256;
+    if (npartials < size_t(blocks)) return set_error(QSIM_EINVAL, "expectation scratch too small");
+    QSIM_CUDA_TRY(cudaMemsetAsync(result, 0, sizeof(double), st), "expectation zero");
+    std::vector<bool> done(nterms, false);
+    for (int t0 = 0; t0 < nterms; ++t0) {
+        if (done[t0]) continue;
+        ExpParams p{};
+        p.X = xmask[t0];
+        p.h = p.X ? 63 - __builtin_clzll(p.X) : -1;
+        for (int t = t0; t < nterms && p.nt < EXP_TERMS; ++t) {
+            if (done[t] || xmask[t] != p.X) continue;
+            done[t] = true;
+            const int ny = __builtin_popcountll(xmask[t] & zmask[t]);
+            // i^{#Y}: 1, i, -1, -i
+            const double re[4] = {1, 0, -1, 0}, im[4] = {0, 1, 0, -1};
+            p.z[p.nt] = zmask[t];
+            p.cr[p.nt] = coeff[t] * re[ny & 3];
+            p.ci[p.nt] = coeff[t] * im[ny & 3];
+            ++p.nt;
+        }
+        const uint64_t count = p.h < 0 ? N : N / 2;
+        {
+            LaunchScope ls(K_EXPECT, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
+            if (dtype == QSIM_C64)
+                k_expect<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), count, p, partials);
+            else
+                k_expect<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), count, p, partials);
+            QSIM_CUDA_TRY(cudaGetLastError(), "expectation launch");
+        }
+        LaunchScope ls(K_REDUCE, st, blocks * 8.0);
+        k_sum_partials<<<1, 256, 0, st>>>(partials, blocks, result, 1);
+        QSIM_CUDA_TRY(cudaGetLastError(), "expectation sum launch");
+        // terms beyond EXP_TERMS with this xmask stay !done and start their own pass
+    }
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ sampler
+// Philox4x32-10, Salmon et al., SC'11: ten rounds of the 4x32 S-box
+// (multipliers 0xD2511F53, 0xCD9E8D57), key bumped by 0x9E3779B9 / 0xBB67AE85
+// between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+constexpr int CHUNK = 2048;  // amplitudes per first-level CDF entry
+
+__device__ __forceinline__ uint64_t weight_of(double p) {
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return uint64_t(1) << 62;
+    return uint64_t(p * 4611686018427387904.0);  // floor(p * 2^62); the scaling is exact
+}
+
+template <int SRC>
+__device__ __forceinline__ double src_prob(const void *src, uint64_t x) {
+    if (SRC == SRC_C64) return prob_of(static_cast<const float2 *>(src)[x]);
+    if (SRC == SRC_C128) return prob_of(static_cast<const double2 *>(src)[x]);
+    return static_cast<const double *>(src)[x];
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// chunk sums of the integer weights (one CTA of 256 threads per chunk)
+template <int SRC>
+__global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ src, uint64_t N,
+                                                      uint64_t *__restrict__ sums, double *__restrict__ psum) {
+    __shared__ uint64_t ws[8];
+    __shared__ double ps[8];
+    const uint64_t c0 = uint64_t(blockIdx.x) * CHUNK;
+    uint64_t w = 0;
+    double pp = 0;
+    for (int i = threadIdx.x; i < CHUNK; i += blockDim.x) {
+        const uint64_t x = c0 + i;
+        if (x < N) {
+            const double p = src_prob<SRC>(src, x);
+            w += weight_of(p);
+            pp += p > 0.0 ? p : 0.0;
+        }
+    }
+    w = warp_sum_u64(w);
+    pp = warp_sum(pp);
+    if ((threadIdx.x & 31) == 0) {
+        ws[threadIdx.x >> 5] = w;
+        ps[threadIdx.x >> 5] = pp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        double q = 0;
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+            t += ws[i];
+            q += ps[i];
+        }
+        sums[blockIdx.x] = t;
+        atomicAdd(psum, q);
+    }
+}
+
+// inclusive prefix over the chunk sums in place; total -> sums[nchunks]
+__global__ void __launch_bounds__(1024) k_sample_scan(uint64_t *__restrict__ sums, uint64_t nchunks) {
+    __shared__ uint64_t part[1024];
+    const uint64_t per = (nchunks + blockDim.x - 1) / blockDim.x;
+    const uint64_t b = threadIdx.x * per, e = (b + per < nchunks) ? b + per : nchunks;
+    uint64_t s = 0;
+    for (uint64_t i = b; i < e; ++i) s += sums[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the per-thread totals
+    for (int off = 1; off < int(blockDim.x); off <<= 1) {
+        const uint64_t v = threadIdx.x >= unsigned(off) ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (uint64_t i = b; i < e; ++i) {
+        run += sums[i];
+        sums[i] = run;
+    }
+    if (threadIdx.x == blockDim.x - 1) sums[nchunks] = part[threadIdx.x];
+}
+
+// one warp per shot: binary search over the chunk prefix, then a warp scan
+// through the chunk in index order
+template <int SRC>
+__global__ void __launch_bounds__(256) k_sample_draw(const void *__restrict__ src, uint64_t N,
+                                                     const uint64_t *__restrict__ prefix, uint64_t nchunks,
+                                                     uint64_t nshots, uint64_t seed, uint64_t counter0,
+                                                     uint64_t *__restrict__ out) {
+    const uint64_t shot = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (shot >= nshots) return;
+    const uint64_t T = prefix[nchunks];
+    if (T == 0) {
+        if (lane == 0) out[shot] = 0;
+        return;
+    }
+    const uint64_t cs = counter0 + shot;
+    const uint4 o = philox4x32_10(make_uint4(unsigned(cs), unsigned(cs >> 32), 0u, 0u),
+                                  make_uint2(unsigned(seed), unsigned(seed >> 32)));
+    const uint64_t u = (uint64_t(o.y) << 32) | o.x;
+    const uint64_t r = __umul64hi(u, T);
+    // smallest chunk c with prefix[c] > r
+    uint64_t lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (prefix[mid] > r) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint64_t c = lo;
+    uint64_t run = c ? prefix[c - 1] : 0;  // CDF just before the chunk
+    const uint64_t x0 = c * CHUNK;
+    uint64_t found = ((x0 + CHUNK < N) ? x0 + CHUNK : N) - 1;
+    for (int j = 0; j < CHUNK / 32; ++j) {
+        const uint64_t x = x0 + uint64_t(j) * 32 + lane;
+        uint64_t w = x < N ? weight_of(src_prob<SRC>(src, x)) : 0;
+        // inclusive warp scan
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t v = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += v;
+        }
+        const uint64_t cdf = run + w;
+        const unsigned hit = __ballot_sync(0xffffffffu, cdf > r);
+        if (hit) {
+            found = x0 + uint64_t(j) * 32 + (__ffs(hit) - 1);
+            break;
+        }
+        run += __shfl_sync(0xffffffffu, w, 31);
+    }
+    if (lane == 0) out[shot] = found;
+}
+
+size_t sample_scratch_u64(uint64_t N) { return size_t((N + CHUNK - 1) / CHUNK) + 1; }
+
+template <int SRC>
+static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_t seed, uint64_t counter0,
+                           uint64_t *out, uint64_t *scratch, double *psum, cudaStream_t st) {
+    const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
+    const double S = SRC == SRC_C64 ? 8 : 16;
+    QSIM_CUDA_TRY(cudaMemsetAsync(psum, 0, sizeof(double), st), "sampler zero");
+    {
+        LaunchScope ls(K_SAMPLE_CHUNK, st, double(N) * S);
+        k_sample_chunk<SRC><<<unsigned(nchunks), 256, 0, st>>>(src, N, scratch, psum);
+        QSIM_CUDA_TRY(cudaGetLastError(), "sampler chunk launch");
+    }
+    {
+        LaunchScope ls(K_SAMPLE_SCAN, st, double(nchunks) * 16);
+        k_sample_scan<<<1, 1024, 0, st>>>(scratch, nchunks);
+        QSIM_CUDA_TRY(cudaGetLastError(), "sampler scan launch");
+    }
+    if (nshots) {
+        const uint64_t threads = nshots * 32;
+        LaunchScope ls(K_SAMPLE_DRAW, st, double(nshots) * CHUNK * S);
+        k_sample_draw<SRC><<<unsigned((threads + 255) / 256), 256, 0, st>>>(src, N, scratch, nchunks, nshots, seed,
+                                                                             counter0, out);
+        QSIM_CUDA_TRY(cudaGetLastError(), "sampler draw launch");
+    }
+    return QSIM_OK;
+}
+
+int launch_sample(const void *src, int src_kind, uint64_t N, uint64_t nshots, uint64_t seed, uint64_t counter0,
+                  uint64_t *out_dev, uint64_t *scratch, double *psum_dev, cudaStream_t st) {
+    if (nshots > (uint64_t(1) << 30)) return set_error(QSIM_EINVAL, "at most 2^30 shots per call");
+    switch (src_kind) {
+        case SRC_C64: return launch_sample_t<SRC_C64>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
+        case SRC_C128: return launch_sample_t<SRC_C128>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
+        default: return launch_sample_t<SRC_PROBS>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
+    }
+}
+
+}  // namespace qsim

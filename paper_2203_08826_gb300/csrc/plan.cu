@@ -1,0 +1,248 @@
+// Fusion planning (Sec. 3.2) and plan execution.
+//
+// QSIM_FUSE_GREEDY2 is the paper's fusion: walk the gate list and multiply
+// each 1- or 2-qubit gate into the most recent fused gate on its qubits when
+// the union stays within two qubits and no later fused gate on those qubits
+// would be overtaken.  The other modes live in their own translation units
+// and share the block bookkeeping defined here.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace qsim {
+
+// Matrix of a gate (targets + controls) on the ordered qubit list `qs`
+// (qs[0] = most significant bit of the result's index).
+std::vector<cd> embed_gate(const GateRec &g, const std::vector<int> &qs) {
+    const int b = int(qs.size());
+    const size_t D = size_t(1) << b;
+    auto pos = [&](int q) {
+        for (int i = 0; i < b; ++i)
+            if (qs[i] == q) return b - 1 - i;  // bit position within the block index
+        return -1;
+    };
+    std::vector<int> tpos(g.k), cpos(g.nc);
+    for (int i = 0; i < g.k; ++i) tpos[i] = pos(g.targets[i]);
+    for (int i = 0; i < g.nc; ++i) cpos[i] = pos(g.controls[i]);
+    const size_t d = size_t(1) << g.k;
+    std::vector<cd> out(D * D, cd(0.0));
+    for (size_t col = 0; col < D; ++col) {
+        bool active = true;
+        for (int i = 0; i < g.nc; ++i)
+            if (!((col >> cpos[i]) & 1)) active = false;
+        if (!active) {
+            out[col * D + col] = 1.0;
+            continue;
+        }
+        size_t jc = 0;  // gate column index read from the block column
+        for (int i = 0; i < g.k; ++i) jc = (jc << 1) | ((col >> tpos[i]) & 1);
+        size_t rest = col;
+        for (int i = 0; i < g.k; ++i) rest &= ~(size_t(1) << tpos[i]);
+        for (size_t jr = 0; jr < d; ++jr) {
+            size_t row = rest;
+            for (int i = 0; i < g.k; ++i)
+                if ((jr >> (g.k - 1 - i)) & 1) row |= size_t(1) << tpos[i];
+            out[row * D + col] += g.m[jr * d + jc];
+        }
+    }
+    return out;
+}
+
+// C = A * B for D x D row-major matrices
+std::vector<cd> matmul(const std::vector<cd> &A, const std::vector<cd> &B, size_t D) {
+    std::vector<cd> C(D * D, cd(0.0));
+    for (size_t i = 0; i < D; ++i)
+        for (size_t k = 0; k < D; ++k) {
+            const cd a = A[i * D + k];
+            if (a == cd(0.0)) continue;
+            for (size_t j = 0; j < D; ++j) C[i * D + j] += a * B[k * D + j];
+        }
+    return C;
+}
+
+// Re-express a block matrix on a larger ordered qubit list.
+std::vector<cd> widen(const std::vector<cd> &m, const std::vector<int> &from, const std::vector<int> &to) {
+    GateRec g;
+    g.k = int(from.size());
+    g.nc = 0;
+    for (int i = 0; i < g.k; ++i) g.targets[i] = from[i];
+    g.m = m;
+    return embed_gate(g, to);
+}
+
+static int build_greedy2(const qsim_circuit &c, qsim_plan &p) {
+    std::vector<int> last(c.n, -1);  // index of the latest block touching each qubit
+    for (size_t gi = 0; gi < c.gates.size(); ++gi) {
+        const GateRec &g = c.gates[gi];
+        std::vector<int> gq;
+        for (int i = 0; i < g.k; ++i) gq.push_back(g.targets[i]);
+        for (int i = 0; i < g.nc; ++i) gq.push_back(g.controls[i]);
+        int F = -1;
+        for (int q : gq) F = std::max(F, last[q]);
+        bool merged = false;
+        if (F >= 0 && gq.size() <= 2) {
+            Block &B = p.blocks[F];
+            std::vector<int> uni = B.qubits;
+            for (int q : gq)
+                if (std::find(uni.begin(), uni.end(), q) == uni.end()) uni.push_back(q);
+            if (uni.size() <= 2) {
+                // the qubits the gate adds must not have a block after F
+                bool ok = true;
+                for (int q : gq)
+                    if (last[q] > F) ok = false;
+                if (ok) {
+                    std::sort(uni.begin(), uni.end(), std::greater<int>());
+                    const size_t D = size_t(1) << uni.size();
+                    std::vector<cd> bm = widen(B.m, B.qubits, uni);
+                    B.m = matmul(embed_gate(g, uni), bm, D);
+                    B.qubits = uni;
+                    B.gates.push_back(int(gi));
+                    // qubits of B outside the gate may already have later blocks
+                    for (int q : gq) last[q] = F;
+                    merged = true;
+                }
+            }
+        }
+        if (!merged) {
+            Block B;
+            B.qubits = gq;
+            std::sort(B.qubits.begin(), B.qubits.end(), std::greater<int>());
+            B.m = embed_gate(g, B.qubits);
+            B.gates.push_back(int(gi));
+            p.blocks.push_back(std::move(B));
+            for (int q : gq) last[q] = int(p.blocks.size()) - 1;
+        }
+    }
+    return QSIM_OK;
+}
+
+// Per-dtype device copies of the dense matrices of a block-list plan.
+static int prepare_ops(qsim_plan &p, int dtype, cudaStream_t st) {
+    PlanDev &dv = p.dev[dtype];
+    if (dv.ready) return QSIM_OK;
+    dv.ops.clear();
+    dv.mat_off.clear();
+    std::vector<unsigned char> host;
+    const size_t eb = dtype == QSIM_C64 ? 8 : 16;
+    for (const Block &B : p.blocks) {
+        Op op;
+        std::vector<int> t(B.qubits.begin(), B.qubits.end());
+        QSIM_TRY(classify(B.m, t.data(), int(t.size()), nullptr, 0, op));
+        size_t off = size_t(-1);
+        if (op.type == Op::DENSE && op.k >= 2) {
+            off = host.size();
+            const size_t d = size_t(1) << op.k;
+            host.resize(off + d * d * eb);
+            for (size_t i = 0; i < d * d; ++i) {
+                if (dtype == QSIM_C64) {
+                    float v[2] = {float(op.m[i].real()), float(op.m[i].imag())};
+                    memcpy(&host[off + i * eb], v, 8);
+                } else {
+                    double v[2] = {op.m[i].real(), op.m[i].imag()};
+                    memcpy(&host[off + i * eb], v, 16);
+                }
+            }
+        }
+        dv.ops.push_back(std::move(op));
+        dv.mat_off.push_back(off);
+    }
+    if (!host.empty()) {
+        QSIM_CUDA_TRY(cudaMalloc(&dv.mats, host.size()), "plan matrices");
+        QSIM_CUDA_TRY(cudaMemcpyAsync(dv.mats, host.data(), host.size(), cudaMemcpyHostToDevice, st),
+                      "plan matrices upload");
+        QSIM_CUDA_TRY(cudaStreamSynchronize(st), "plan upload sync");
+    }
+    dv.ready = true;
+    return QSIM_OK;
+}
+
+int run_block_plan(qsim_state *s, qsim_plan &p) {
+    QSIM_TRY(prepare_ops(p, s->dtype, s->stream));
+    PlanDev &dv = p.dev[s->dtype];
+    for (size_t i = 0; i < dv.ops.size(); ++i) {
+        void *mat = dv.mat_off[i] == size_t(-1) ? nullptr : static_cast<char *>(dv.mats) + dv.mat_off[i];
+        QSIM_TRY(launch_op(s->amps, s->n, s->dtype, dv.ops[i], s->stream, mat));
+    }
+    return QSIM_OK;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+qsim_plan::~qsim_plan() {
+    for (PlanDev &d : dev)
+        if (d.mats) cudaFree(d.mats);
+    release_staged();
+    release_tc();
+}
+
+extern "C" {
+
+int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out) {
+    if (!c || !out) return set_error(QSIM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (kmax < 1 || kmax > QSIM_MAX_TARGETS) return set_error(QSIM_EINVAL, "kmax=%d outside 1..6", kmax);
+    qsim_plan *p = new qsim_plan();
+    p->n = c->n;
+    p->mode = mode;
+    p->kmax = kmax;
+    p->ngates = int(c->gates.size());
+    int rc = QSIM_OK;
+    switch (mode) {
+        case QSIM_FUSE_GREEDY2: rc = build_greedy2(*c, *p); break;
+        case QSIM_FUSE_STAGED: rc = build_staged(*c, *p); break;
+        case QSIM_FUSE_TC: rc = build_tc(*c, *p); break;
+        default: rc = set_error(QSIM_EINVAL, "unknown fusion mode %d", mode);
+    }
+    if (rc != QSIM_OK) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return QSIM_OK;
+}
+
+int qsim_plan_destroy(qsim_plan *p) {
+    delete p;
+    return QSIM_OK;
+}
+
+int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode) {
+    if (!p) return set_error(QSIM_EINVAL, "plan is NULL");
+    if (nsweeps) *nsweeps = p->nsweeps();
+    if (ngates) *ngates = p->ngates;
+    if (mode) *mode = p->mode;
+    return QSIM_OK;
+}
+
+int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *matrix_out) {
+    if (!p) return set_error(QSIM_EINVAL, "plan is NULL");
+    if (i < 0 || i >= int(p->blocks.size())) return set_error(QSIM_EINVAL, "block %d outside the plan", i);
+    const Block &B = p->blocks[i];
+    if (k) *k = int(B.qubits.size());
+    if (targets)
+        for (size_t j = 0; j < B.qubits.size(); ++j) targets[j] = B.qubits[j];
+    if (matrix_out)
+        for (size_t j = 0; j < B.m.size(); ++j) {
+            matrix_out[2 * j] = B.m[j].real();
+            matrix_out[2 * j + 1] = B.m[j].imag();
+        }
+    return QSIM_OK;
+}
+
+int qsim_apply_fused(qsim_state *s, const qsim_plan *pc) {
+    if (!s || !pc) return set_error(QSIM_EINVAL, "NULL argument");
+    qsim_plan *p = const_cast<qsim_plan *>(pc);
+    if (p->n != s->n) return set_error(QSIM_EINVAL, "plan has %d qubits, state %d", p->n, s->n);
+    switch (p->mode) {
+        case QSIM_FUSE_GREEDY2: return run_block_plan(s, *p);
+        case QSIM_FUSE_STAGED: return run_staged(s, *p);
+        case QSIM_FUSE_TC: return run_tc(s, *p);
+    }
+    return set_error(QSIM_EINVAL, "bad plan mode");
+}
+
+}  // extern "C"

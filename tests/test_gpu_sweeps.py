@@ -1,0 +1,225 @@
+"""GPU parity of the plain gate sweeps, probabilities, norms, expectations and
+the sampler against the CPU oracle (same seeded inputs, element by element).
+
+Tolerances: max-abs amplitude error 1e-12 for complex128 and 1e-5 for
+complex64 (the stated bar); reductions in double are held to a relative
+1e-12 (complex128) / 1e-6 (complex64, whose amplitudes carry ~6e-8 relative
+rounding); shots must match bit for bit on identical probabilities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2203_08826_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_08826_gb300 import build, binding
+    build.build()
+    return binding
+
+
+def new_state(q, n, dtype, psi0=None):
+    s = q.State(n, dtype)
+    if psi0 is None:
+        s.init_zero()
+    else:
+        s.from_host(psi0)
+    return s
+
+
+def check(got, want, dtype, what=""):
+    err = np.max(np.abs(got.astype(np.complex128) - want)) if want.size else 0.0
+    assert err <= TOL[dtype], f"{what}: max-abs error {err:.3e} > {TOL[dtype]:g}"
+    return err
+
+
+def random_gate(rng, n, kind, k, c):
+    qs = [int(v) for v in rng.permutation(n)[: k + c]]
+    t, ctl = tuple(qs[:k]), tuple(qs[k:])
+    if kind == "dense":
+        m = inputs.random_dense_gate(rng, k)
+    elif kind == "diag":
+        m = np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << k)))
+    else:  # monomial: permutation with phases
+        perm = rng.permutation(1 << k)
+        m = np.zeros((1 << k, 1 << k), dtype=complex)
+        m[np.arange(1 << k), perm] = np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << k))
+    return inputs.Gate("matrix", t, ctl, (), -1, m)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 13])
+def test_random_gates_each_kind(q, orc, dtype, n):
+    rng = np.random.default_rng(1000 + n)
+    psi0 = inputs.gaussian_state(n, seed=n)
+    s = new_state(q, n, dtype, psi0)
+    ref = psi0.copy()
+    cases = []
+    for kind in ("dense", "diag", "mono"):
+        for k in range(1, min(n, 6) + 1):
+            for c in (0, 1, 3):
+                if k + c <= n and not (kind == "mono" and k > 3):
+                    cases.append((kind, k, c))
+    for kind, k, c in cases:
+        g = random_gate(rng, n, kind, k, c)
+        s.apply(g)
+        orc.apply_gate(ref, g)
+        check(s.to_host(), ref, dtype, f"{kind} k={k} c={c} n={n}")
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_named_gates_and_classification(q, orc, dtype):
+    """Named gates (including those the classifier turns into controls,
+    diagonals and permutations) on every target of a 12-qubit state."""
+    n = 12
+    rng = np.random.default_rng(5)
+    psi0 = inputs.gaussian_state(n, seed=2)
+    s = new_state(q, n, dtype, psi0)
+    ref = psi0.copy()
+    for t in range(n):
+        o = (t + 5) % n
+        gates = [inputs.Gate("h", (t,)), inputs.Gate("x", (t,)), inputs.Gate("y", (t,)),
+                 inputs.Gate("z", (t,)), inputs.Gate("s", (t,)), inputs.Gate("t", (t,)),
+                 inputs.Gate("rx", (t,), (), (rng.uniform(0, 6),)),
+                 inputs.Gate("ry", (t,), (), (rng.uniform(0, 6),)),
+                 inputs.Gate("rz", (t,), (), (rng.uniform(0, 6),)),
+                 inputs.Gate("phase", (t,), (o,), (rng.uniform(0, 6),)),
+                 inputs.Gate("cz", (t, o)), inputs.Gate("swap", (o, t)),
+                 inputs.Gate("x", (t,), (o, (t + 3) % n)),
+                 inputs.Gate("su2", (t,), (), inputs.haar_su2_quaternion(rng))]
+        for g in gates:
+            s.apply(g)
+            orc.apply_gate(ref, g)
+    check(s.to_host(), ref, dtype, "named gates")
+
+
+def test_qft10_complex128_matches_oracle_and_dft(q, orc):
+    """10-qubit QFT, complex128, Gaussian initial state (seed 1)."""
+    n = 10
+    psi0 = inputs.gaussian_state(n, seed=1)
+    s = new_state(q, n, "c128", psi0)
+    s.run(inputs.qft(n))
+    got = s.to_host()
+    check(got, orc.simulate(inputs.qft(n), psi0), "c128", "qft10 vs oracle")
+    check(got, math.sqrt(1 << n) * np.fft.ifft(psi0), "c128", "qft10 vs DFT")
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("maker", ["random", "variational", "qft", "ghz"])
+def test_circuits_plain_and_greedy2(q, orc, dtype, maker):
+    circ = {"random": lambda: inputs.random_circuit(14, 6, seed=3),
+            "variational": lambda: inputs.variational(13, 4, seed=4),
+            "qft": lambda: inputs.qft(13),
+            "ghz": lambda: inputs.ghz(15)}[maker]()
+    psi0 = inputs.gaussian_state(circ.n, seed=7) if maker != "ghz" else None
+    want = orc.simulate(circ, psi0)
+    s = new_state(q, circ.n, dtype, psi0)
+    s.run(circ)
+    check(s.to_host(), want, dtype, f"{maker} plain")
+    s2 = new_state(q, circ.n, dtype, psi0)
+    s2.run_fused(q.Plan(circ, kmax=2, mode=q.FUSE_GREEDY2))
+    check(s2.to_host(), want, dtype, f"{maker} greedy2")
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_probabilities_and_norm(q, orc, dtype):
+    n = 14
+    psi0 = inputs.gaussian_state(n, seed=11)
+    s = new_state(q, n, dtype, psi0)
+    s.run(inputs.random_circuit(n, 2, seed=12))
+    amps = s.to_host().astype(np.complex128)
+    rtol = 1e-13 if dtype == "c128" else 1e-12
+    np.testing.assert_allclose(s.probabilities(), orc.probabilities(amps), rtol=rtol, atol=0)
+    for qubits in [(0,), (13,), (3, 9), (9, 3, 0), tuple(range(12)), (1, 5, 7, 11, 13, 0, 2, 4, 6, 8, 10, 12, 3)]:
+        np.testing.assert_allclose(s.probabilities(qubits), orc.probabilities(amps, qubits),
+                                   rtol=1e-11, atol=1e-15)
+    assert abs(s.norm2() - np.sum(np.abs(amps) ** 2)) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_pauli_expectation(q, orc, dtype):
+    n = 12
+    psi0 = inputs.gaussian_state(n, seed=21)
+    s = new_state(q, n, dtype, psi0)
+    amps = s.to_host().astype(np.complex128)
+    for ham in (inputs.random_pauli_sum(n, 40, seed=22), inputs.tfim(n), inputs.zz_chain(n)):
+        want = orc.expectation(amps, ham)
+        got = s.expectation(ham)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (got, want)
+
+
+def test_expectation_many_terms_same_xmask(q, orc):
+    """More terms share one xmask than one pass holds."""
+    n = 10
+    rng = np.random.default_rng(3)
+    z = rng.integers(0, 1 << n, size=150).astype(np.uint64)
+    x = np.full(150, 0b1010, dtype=np.uint64)
+    ham = inputs.PauliSum(x, z, rng.standard_normal(150))
+    s = new_state(q, n, "c128", inputs.gaussian_state(n, seed=1))
+    want = orc.expectation(s.to_host(), ham)
+    assert abs(s.expectation(ham) - want) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [3, 11, 16])
+def test_sampler_bit_exact(q, orc, dtype, n):
+    import torch
+    psi0 = inputs.gaussian_state(n, seed=31 + n)
+    s = new_state(q, n, dtype, psi0)
+    shots = 20000
+    seed, c0 = 0xDEADBEEF12345, 2**32 - 100
+    got = s.sample(shots, seed, c0)
+    # (a) GPU probabilities copied back, sampled by the oracle
+    p_gpu = s.probabilities()
+    np.testing.assert_array_equal(got, orc.sample(p_gpu, shots, seed, c0))
+    # (b) the oracle's probabilities (of the same stored amplitudes) on the GPU sampler
+    p_orc = orc.probabilities(s.to_host().astype(np.complex128))
+    dev = torch.from_numpy(p_orc).cuda()
+    from paper_2203_08826_gb300 import binding
+    np.testing.assert_array_equal(binding.sample_probs(dev, shots, seed, c0), orc.sample(p_orc, shots, seed, c0))
+
+
+@pytest.mark.parametrize("N", [1, 7, 2048, 2049, 5000, 1 << 15])
+def test_sampler_ragged_sizes(q, orc, N):
+    import torch
+    from paper_2203_08826_gb300 import binding
+    rng = np.random.default_rng(N)
+    p = rng.dirichlet(np.full(N, 0.5)) if N > 1 else np.ones(1)
+    p[rng.random(N) < 0.2] = 0.0
+    if p.sum() == 0:
+        p[0] = 1.0
+    p /= p.sum()
+    got = binding.sample_probs(torch.from_numpy(p).cuda(), 5000, seed=N, counter0=3)
+    np.testing.assert_array_equal(got, orc.sample(p, 5000, seed=N, counter0=3))
+
+
+def test_sampler_rejects_bad_probabilities(q):
+    import torch
+    from paper_2203_08826_gb300 import binding
+    with pytest.raises(binding.QsimError):
+        binding.sample_probs(torch.zeros(64, dtype=torch.float64, device="cuda"), 10, seed=1)
+    with pytest.raises(binding.QsimError):
+        binding.sample_probs(torch.full((64,), 0.5, dtype=torch.float64, device="cuda"), 10, seed=1)
+
+
+def test_argument_errors_do_not_launch(q):
+    from paper_2203_08826_gb300 import binding
+    s = new_state(q, 5, "c64")
+    before = binding.launch_count()
+    with pytest.raises(binding.QsimError):
+        s.apply_matrix(np.eye(2), (5,))
+    with pytest.raises(binding.QsimError):
+        s.apply_matrix(np.eye(4), (1, 1))
+    with pytest.raises(binding.QsimError):
+        s.apply_matrix(np.eye(2), (1,), (1,))
+    assert binding.launch_count() == before

@@ -1,0 +1,116 @@
+"""Host-side checks of libqsim that need no GPU: the C ABI loads and exports
+every declared symbol, argument validation, and the fusion planner."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2203_08826_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2203_08826_gb300 import build, binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"QSIM_API\s+[\w\s\*]*?\b(qsim_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(q):
+    names = declared_symbols()
+    assert len(names) >= 30
+    lib = q.lib()
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert "sm_103a" in q.version()
+
+
+def test_binding_covers_declared_symbols(q):
+    assert declared_symbols() <= set(q._SIGS)
+
+
+def test_circuit_validation(q):
+    lib = q.lib()
+    h = ctypes.c_void_p()
+    assert lib.qsim_circuit_create(4, ctypes.byref(h)) == 0
+    t = (ctypes.c_int * 2)(1, 1)
+    rc = lib.qsim_circuit_add(h, q.GATE_KIND["cz"], t, 2, None, 0, None, -1, None)
+    assert rc == -1 and b"twice" in lib.qsim_last_error()
+    t = (ctypes.c_int * 1)(4)
+    rc = lib.qsim_circuit_add(h, q.GATE_KIND["h"], t, 1, None, 0, None, -1, None)
+    assert rc == -1 and b"outside" in lib.qsim_last_error()
+    t = (ctypes.c_int * 1)(0)
+    rc = lib.qsim_circuit_add(h, q.GATE_KIND["cz"], t, 1, None, 0, None, -1, None)
+    assert rc == -1
+    # only rotation angles can be trainable
+    rc = lib.qsim_circuit_add(h, q.GATE_KIND["h"], t, 1, None, 0, None, 3, None)
+    assert rc == -1
+    assert lib.qsim_circuit_destroy(h) == 0
+    assert lib.qsim_circuit_create(0, ctypes.byref(h)) == -1
+
+
+def test_qcircuit_counts(q):
+    c = inputs.variational(6, 3, seed=1)
+    qc = q.QCircuit(c)
+    assert qc.ngates == len(c) and qc.nparams == c.nparams == 36
+
+
+def _asap_depth(n, qubit_sets):
+    level = [0] * n
+    for qs in qubit_sets:
+        l = 1 + max(level[x] for x in qs)
+        for x in qs:
+            level[x] = l
+    return max(level)
+
+
+def test_greedy2_fusion_reproduces_paper_qft_counts(q):
+    """Sec. 3.2 fusion on the 30-qubit QFT gives the fused size of the paper's
+    benchmark-circuit table (450 gates, depth 58)."""
+    row = [l.split() for l in open(os.path.join(GOLDEN, "benchmark_circuits_table.txt"))
+           if l.strip() and not l.startswith("#")][0]
+    n, fdepth, fgates = int(row[1]), int(row[4]), int(row[5])
+    plan = q.Plan(inputs.qft(n), kmax=2, mode=q.FUSE_GREEDY2)
+    info = plan.info()
+    assert info["sweeps"] == fgates and info["gates"] == 480
+    sets = [plan.block(i)[0] for i in range(info["sweeps"])]
+    assert _asap_depth(n, sets) == fdepth
+
+
+def test_greedy2_blocks_equal_product_of_oracle_gates(q, orc):
+    """Each fused matrix equals the product of its source gates' matrices, as
+    built by the oracle and embedded by Kronecker products (independent of the
+    planner's own embedding)."""
+    from tests.test_oracle_pins import kron_operator
+    circ = inputs.random_circuit(5, 3, seed=4)
+    plan = q.Plan(circ, kmax=2, mode=q.FUSE_GREEDY2)
+    n = circ.n
+    U_plan = np.eye(1 << n, dtype=complex)
+    for i in range(plan.info()["sweeps"]):
+        t, m = plan.block(i)
+        U_plan = kron_operator(n, m, t) @ U_plan
+    U_ref = np.eye(1 << n, dtype=complex)
+    for g in circ.gates:
+        U_ref = kron_operator(n, orc.gate_matrix(g), g.targets, g.controls) @ U_ref
+    np.testing.assert_allclose(U_plan, U_ref, atol=1e-13)
+    assert plan.info()["sweeps"] < len(circ)
+
+
+def test_plan_rejects_bad_mode(q):
+    with pytest.raises(q.QsimError):
+        q.Plan(inputs.qft(4), kmax=2, mode=7)
