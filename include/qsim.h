@@ -207,6 +207,24 @@ QSIM_API int qsim_sample(qsim_state *s, uint64_t nshots, uint64_t seed, uint64_t
 QSIM_API int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
                       uint64_t counter0, uint64_t *out, int out_on_device, void *cuda_stream);
 
+/* The sampler of qsim_sample_probs for callers that may not allocate device
+ * memory (a framework whose allocator owns the device pool, a service with a
+ * memory budget fixed at start-up, a loop that cannot take the device
+ * synchronisation cudaMalloc/cudaFree can cause).  The paper has no
+ * counterpart; this is a deployment variant.  It calls no allocator: its
+ * scratch is a 512.25 KiB array in the library's device image that every GPU
+ * loading the library holds until exit, so N is limited to 1 <= N <= 2^27
+ * (larger N returns QSIM_EINVAL without launching).  p_dev: N doubles on the
+ * device; out_dev: nshots uint64 on the device (required); the call runs on
+ * `cuda_stream` and synchronises it before returning (it reads back the
+ * total weight to validate the probabilities).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
+                                      uint64_t counter0, uint64_t *out_dev, void *cuda_stream);
+
 /* Pauli expectation <psi| sum_t coeff[t] P_t |psi> with P_t given by bit masks
  * (bit q of xmask/zmask: X = (1,0), Y = (1,1), Z = (0,1) on qubit q):
  *   P|y> = i^{#Y} (-1)^{popcount(y & zmask)} |y ^ xmask>.

@@ -63,6 +63,7 @@ _SIGS = {
     "qsim_norm2": ([P, P], I),
     "qsim_sample": ([P, U64, U64, U64, P, I], I),
     "qsim_sample_probs": ([P, U64, U64, U64, U64, P, I, P], I),
+    "qsim_sample_probs_static": ([P, U64, U64, U64, U64, P, P], I),
     "qsim_expectation_pauli": ([P, I, P, P, P, P], I),
     "qsim_adjoint_grad": ([P, I, I, P, I, P, P, P, P, P, P], I),
     "qsim_batch_create": ([I, P, P], I),

@@ -504,3 +504,73 @@ int launch_sample(const void *src, int src_kind, uint64_t N, uint64_t nshots, ui
 }
 
 }  // namespace qsim
+
+// ------------------------------------------------------------------ sampler without allocation
+// Some callers may not allocate device memory at all: a framework whose
+// caching allocator owns the whole device pool, a service that fixes its
+// memory budget at start-up, or a latency-sensitive loop that cannot afford
+// the implicit device synchronisation cudaMalloc and cudaFree may bring.
+// qsim_sample_probs_static serves them: its scratch (the chunk prefix sums,
+// the total weight and the probability sum) lives in this file-scope device
+// array, which every GPU that loads the library holds until the process exits.
+#include <mutex>
+
+namespace qsim {
+
+constexpr uint64_t STATIC_SAMPLE_MAX_N = uint64_t(1) << 27;         // probabilities
+constexpr size_t STATIC_SAMPLE_CHUNKS = size_t(STATIC_SAMPLE_MAX_N / CHUNK);
+// [0, chunks]: inclusive chunk prefix + total; [chunks + 1]: probability sum
+constexpr size_t STATIC_SAMPLE_WORDS = (STATIC_SAMPLE_CHUNKS + 2 + 31) / 32 * 32;  // 512.25 KiB
+
+static __device__ __align__(256) uint64_t g_sample_scratch[STATIC_SAMPLE_WORDS];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int MAX_DEVICES = 256;
+uint64_t *g_static_ptr[MAX_DEVICES] = {};
+
+// Device address of g_sample_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with that device current.
+int static_scratch(uint64_t **out) {
+    int dev = 0;
+    QSIM_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= MAX_DEVICES) return set_error(QSIM_EUNSUPPORTED, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        QSIM_CUDA_TRY(cudaGetSymbolAddress(&p, g_sample_scratch), "cudaGetSymbolAddress(sampler scratch)");
+        g_static_ptr[dev] = static_cast<uint64_t *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return QSIM_OK;
+}
+}  // namespace
+
+}  // namespace qsim
+
+extern "C" QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
+                                                 uint64_t counter0, uint64_t *out_dev, void *cuda_stream) {
+    using namespace qsim;
+    if (!p_dev || (nshots && !out_dev)) return set_error(QSIM_EINVAL, "NULL argument");
+    if (N == 0 || N > STATIC_SAMPLE_MAX_N)
+        return set_error(QSIM_EINVAL, "N=%llu outside 1..2^27, the capacity of the static sampler scratch",
+                         (unsigned long long)N);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    uint64_t *scratch = nullptr;
+    QSIM_TRY(static_scratch(&scratch));
+    const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
+    double *psum = reinterpret_cast<double *>(scratch + STATIC_SAMPLE_CHUNKS + 1);
+    // the chunk kernel overwrites every prefix entry it uses; the probability
+    // sum is accumulated and is cleared by the launcher's memset
+    QSIM_TRY(launch_sample(p_dev, SRC_PROBS, N, nshots, seed, counter0, out_dev, scratch, psum, st));
+    double hp = 0.0;
+    uint64_t total = 0;
+    QSIM_CUDA_TRY(cudaMemcpyAsync(&hp, psum, sizeof(double), cudaMemcpyDeviceToHost, st), "psum copy");
+    QSIM_CUDA_TRY(cudaMemcpyAsync(&total, scratch + nchunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st),
+                  "total copy");
+    QSIM_CUDA_TRY(cudaStreamSynchronize(st), "static sampler sync");
+    if (!(hp <= 1.5) || total == 0)
+        return set_error(QSIM_EINVAL, "probabilities must sum to a value in (0, 1.5] (got %g)", hp);
+    return QSIM_OK;
+}
