@@ -151,11 +151,14 @@ typedef struct qsim_plan qsim_plan;
  *                      2-qubit gates that act on the same targets; one sweep
  *                      per fused gate.
  *   QSIM_FUSE_STAGED   cache-blocked stages: each stage loads tiles of 2^m
- *                      amplitudes spanning a chosen qubit set into shared
- *                      memory, applies every gate of the stage there (gates on
- *                      qubits outside the set only if diagonal, or through
- *                      their controls), and writes the tile back: one HBM pass
- *                      per stage.
+ *                      amplitudes spanning a chosen qubit set into registers
+ *                      (qubits 0..4 across the lanes of a warp, 4 qubits per
+ *                      thread, min(kmax, 4) qubits across warps, with shared
+ *                      memory to re-assign them), applies every gate of the
+ *                      stage there (gates on qubits outside the set only if
+ *                      diagonal, or through their controls), and writes the
+ *                      tile back: one HBM pass per stage.  Needs n >= 9;
+ *                      smaller circuits get a QSIM_FUSE_GREEDY2 plan.
  *   QSIM_FUSE_TC       dense k-qubit blocks (kmax = 4..6) applied on the
  *                      tensor cores as split-precision real GEMMs
  *                      (complex64 states only), with the qubit order rotated
@@ -174,6 +177,9 @@ QSIM_API int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *
  * writes k and the targets (targets[0] = MSB) and, if matrix_out is non-NULL,
  * the 2^k x 2^k row-major complex128 matrix.  Host-only; no GPU needed. */
 QSIM_API int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *matrix_out);
+/* Human-readable summary of a plan (stages, tile qubits, op counts),
+ * NUL-terminated and truncated to len bytes.  Host-only. */
+QSIM_API int qsim_plan_describe(const qsim_plan *p, char *buf, size_t len);
 /* Execute a plan on a state of the circuit's width and precision. */
 QSIM_API int qsim_apply_fused(qsim_state *s, const qsim_plan *p);
 

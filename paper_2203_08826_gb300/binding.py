@@ -58,6 +58,7 @@ _SIGS = {
     "qsim_plan_destroy": ([P], I),
     "qsim_plan_info": ([P, P, P, P], I),
     "qsim_plan_block": ([P, I, P, P, P], I),
+    "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
     "qsim_apply_fused": ([P, P], I),
     "qsim_probabilities": ([P, P, I, P, I], I),
     "qsim_norm2": ([P, P], I),
@@ -180,6 +181,11 @@ class Plan:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().qsim_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"sweeps": a.value, "gates": b.value, "mode": c.value}
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 20)
+        _check(lib().qsim_plan_describe(self.handle, buf, len(buf)))
+        return buf.value.decode()
 
     def block(self, i: int):
         k = ctypes.c_int()

@@ -72,7 +72,7 @@ std::vector<cd> widen(const std::vector<cd> &m, const std::vector<int> &from, co
     return embed_gate(g, to);
 }
 
-static int build_greedy2(const qsim_circuit &c, qsim_plan &p) {
+int build_greedy2(const qsim_circuit &c, qsim_plan &p) {
     std::vector<int> last(c.n, -1);  // index of the latest block touching each qubit
     for (size_t gi = 0; gi < c.gates.size(); ++gi) {
         const GateRec &g = c.gates[gi];
@@ -215,6 +215,27 @@ int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode) {
     if (nsweeps) *nsweeps = p->nsweeps();
     if (ngates) *ngates = p->ngates;
     if (mode) *mode = p->mode;
+    return QSIM_OK;
+}
+
+int qsim_plan_describe(const qsim_plan *p, char *buf, size_t len) {
+    if (!p || !buf || len == 0) return set_error(QSIM_EINVAL, "NULL argument");
+    std::string out;
+    if (p->mode == QSIM_FUSE_STAGED) {
+        staged_describe(*p, out);
+    } else if (p->mode == QSIM_FUSE_TC) {
+        tc_describe(*p, out);
+    } else {
+        out = "greedy2 plan: " + std::to_string(p->blocks.size()) + " fused gates\n";
+        for (size_t i = 0; i < p->blocks.size(); ++i) {
+            out += "  " + std::to_string(i) + " [";
+            for (int q : p->blocks[i].qubits) out += std::to_string(q) + " ";
+            out += "] gates=" + std::to_string(p->blocks[i].gates.size()) + "\n";
+        }
+    }
+    const size_t n = std::min(len - 1, out.size());
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
     return QSIM_OK;
 }
 

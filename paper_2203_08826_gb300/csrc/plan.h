@@ -1,6 +1,7 @@
 // Host-side circuit records and fusion plans.
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -64,9 +65,12 @@ struct qsim_plan {
 };
 
 namespace qsim {
+int build_greedy2(const qsim_circuit &c, qsim_plan &p);
 int build_staged(const qsim_circuit &c, qsim_plan &p);
 int run_staged(qsim_state *s, qsim_plan &p);
 int staged_nsweeps(const qsim_plan &p);
+void staged_describe(const qsim_plan &p, std::string &out);
+void tc_describe(const qsim_plan &p, std::string &out);
 int build_tc(const qsim_circuit &c, qsim_plan &p);
 int run_tc(qsim_state *s, qsim_plan &p);
 int tc_nsweeps(const qsim_plan &p);
