@@ -1,13 +1,655 @@
-// Tensor-core fused k-qubit blocks (QSIM_FUSE_TC).
+// Tensor-core fused k-qubit blocks (QSIM_FUSE_TC), complex64 states.
+//
+// A dense k-qubit block on the k lowest bits of the index is the contraction
+// of Eq. (1) for every row of the (2^(n-k) x 2^k) matrix view of the state:
+// psi'[r, c] = sum_c' G[c, c'] psi[r, c'].  With amplitudes interleaved
+// (re, im) a row is 2^(k+1) reals and the complex product becomes one real
+// GEMM  D = A * B^T  with A = rows (M = 128 per tile, K = 2^(k+1)) and the
+// real-ified gate B[N = 2^(k+1), K]:
+//   B[2c  ][2c'] =  Re G[c,c'],  B[2c  ][2c'+1] = -Im G[c,c'],
+//   B[2c+1][2c'] =  Im G[c,c'],  B[2c+1][2c'+1] =  Re G[c,c'].
+// The fp32 state is split into two low-precision parts a = a_hi + a_lo and
+// the product is taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (the a_lo b_lo term
+// is below fp32 rounding of the result's scale), on the 5th-generation tensor
+// cores: tcgen05.mma with operands in shared memory (128-byte swizzled K-major
+// layout), the fp32 accumulator in tensor memory, completion signalled through
+// an mbarrier.  Two splits are built: BF16x3 (kind::f16) and 3xTF32
+// (kind::tf32).
+//
+// Each pass writes its output with the index rotated right by k bits,
+// out[(c << (n-k)) | r] = D[r, c], into a second buffer: the next pass then
+// finds the next k qubits in the low bits, and the warp that owns 32
+// consecutive rows stores 32 consecutive amplitudes per column.  A plan is a
+// sequence of such passes whose widths add up to a multiple of n, so the
+// final index order is the natural one.  Diagonal gates whose qubits straddle
+// the block are applied to the output in the epilogue, where the full index of
+// every element is known.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
 #include "internal.h"
 #include "plan.h"
 
 namespace qsim {
-struct TcPlan {};
-int build_tc(const qsim_circuit &, qsim_plan &) { return set_error(QSIM_EUNSUPPORTED, "tensor-core fusion not built yet"); }
-int run_tc(qsim_state *, qsim_plan &) { return set_error(QSIM_EUNSUPPORTED, "tensor-core fusion not built yet"); }
-int tc_nsweeps(const qsim_plan &) { return 0; }
-void tc_describe(const qsim_plan &, std::string &) {}
+
+namespace {
+
+constexpr int TC_M = 128;          // rows per tile (tcgen05 M)
+constexpr int TC_THREADS = 128;    // 4 warps: one TMEM lane quarter each
+constexpr int MAX_EPI = 48;        // epilogue diagonal ops per pass
+constexpr int MAX_EPI_POOL = 256;  // their complex entries
+constexpr unsigned long long WAIT_LIMIT = 1ull << 26;  // bounded mbarrier waits
+
+enum TcPrec { TC_BF16X3 = 0, TC_TF32X3 = 1 };
+
+struct EpiOp {
+    uint64_t cmask;  // control bits (current index) that must all be 1
+    int k;           // selector bits
+    int sel[QSIM_MAX_TARGETS];  // current-index bit of selector t (t = 0 is the MSB)
+    int moff;        // entries in the pool (2^k complex)
+    int neg;         // 1: k == 0 and the factor is exactly -1
+};
+
+struct TcParams {
+    const float2 *in;
+    float2 *out;
+    const uint4 *bimg;   // shared-memory image of B_hi then B_lo
+    int *err;            // set to 1 when a bounded wait expires
+    uint64_t ntiles;     // 2^(n-k) / 128
+    int n;
+    int nepi;
+    EpiOp epi[MAX_EPI];
+    float2 pool[MAX_EPI_POOL];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFF) >> 4);
+    d |= uint64_t(1) << 16;             // leading byte offset (unused with swizzle)
+    d |= uint64_t(1024 >> 4) << 32;     // stride byte offset
+    d |= uint64_t(1) << 46;             // version
+    d |= uint64_t(2) << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D fp32, A/B bf16 (1) or tf32 (2), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+template <int PREC>
+__host__ __device__ constexpr uint32_t tc_idesc(int N, int M) {
+    return (1u << 4) | (uint32_t(PREC == TC_BF16X3 ? 1 : 2) << 7) | (uint32_t(PREC == TC_BF16X3 ? 1 : 2) << 10) |
+           (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// Byte offset of element (row m, k-element e) in a swizzled K-major operand
+// made of 128-byte-wide column blocks, each rows*128 bytes.
+template <int EB>
+__host__ __device__ inline uint32_t sw128_offset(int m, int e, int rows) {
+    const int per_row = 128 / EB;  // elements per 128-byte row of a column block
+    const int blk = e / per_row;
+    const uint32_t byte = uint32_t(e % per_row) * EB;
+    const uint32_t chunk = byte >> 4, within = byte & 15;
+    return uint32_t(blk) * uint32_t(rows) * 128u + uint32_t(m / 8) * 1024u + uint32_t(m % 8) * 128u +
+           ((chunk ^ uint32_t(m % 8)) << 4) + within;
+}
+
+template <int PREC> struct Elem;
+template <> struct Elem<TC_BF16X3> {
+    static constexpr int EB = 2;
+    __device__ static void split(float a, uint16_t &hi, uint16_t &lo) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(a);
+        const __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(l);
+    }
+};
+template <> struct Elem<TC_TF32X3> {
+    static constexpr int EB = 4;
+    __device__ static void split(float a, uint32_t &hi, uint32_t &lo) {
+        const uint32_t h = __float_as_uint(a) & 0xFFFFE000u;  // exactly representable in tf32
+        hi = h;
+        lo = __float_as_uint(a - __uint_as_float(h));
+    }
+};
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int K, int PREC>
+struct TcShape {
+    static constexpr int KR = 2 << K;                   // reals per row (GEMM K and N)
+    static constexpr int EB = Elem<PREC>::EB;
+    static constexpr int OPND = TC_M * KR * EB;         // bytes of one A split
+    static constexpr int BOPND = KR * KR * EB;          // bytes of one B split
+    static constexpr int SMEM = 2 * OPND + 2 * BOPND + 1024 + 64;
+    static constexpr int TCOLS = KR < 32 ? 32 : KR;     // TMEM columns (power of 2 >= 32)
+    static constexpr int KSTEP = 32 / EB;               // K elements per MMA
+};
+
+template <int K, int PREC>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__ TcParams p) {
+    using S = TcShape<K, PREC>;
+    extern __shared__ __align__(1024) unsigned char smem_dyn[];
+    // 1024-byte alignment for the swizzle atoms
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    unsigned char *a_hi = sm;
+    unsigned char *a_lo = sm + S::OPND;
+    unsigned char *b_hi = sm + 2 * S::OPND;
+    unsigned char *b_lo = b_hi + S::BOPND;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(b_lo + S::BOPND);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // B (both splits) into shared memory; the host built the swizzled image
+    {
+        const uint4 *src = p.bimg;
+        uint4 *dst = reinterpret_cast<uint4 *>(b_hi);
+        for (int i = tid; i < 2 * S::BOPND / 16; i += TC_THREADS) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(S::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t mb = smem_u32(mbar);
+    uint32_t phase = 0;
+    bool failed = false;
+    constexpr uint32_t IDESC = tc_idesc<PREC>(S::KR, TC_M);
+    const int n = p.n;
+    const uint64_t rows_total = uint64_t(1) << (n - K);
+
+    for (uint64_t tile = blockIdx.x; tile < p.ntiles && !failed; tile += gridDim.x) {
+        // ---- A: 128 rows of KR floats (contiguous) -> split -> swizzled smem
+        const float4 *src = reinterpret_cast<const float4 *>(p.in + tile * TC_M * (S::KR / 2));
+        constexpr int NV = TC_M * S::KR / 4;  // float4 per tile
+#pragma unroll 4
+        for (int i = tid; i < NV; i += TC_THREADS) {
+            const float4 v = src[i];
+            const int m = (i * 4) / S::KR, e = (i * 4) % S::KR;
+            if (PREC == TC_BF16X3) {
+                uint16_t h[4], l[4];
+                Elem<TC_BF16X3>::split(v.x, h[0], l[0]);
+                Elem<TC_BF16X3>::split(v.y, h[1], l[1]);
+                Elem<TC_BF16X3>::split(v.z, h[2], l[2]);
+                Elem<TC_BF16X3>::split(v.w, h[3], l[3]);
+                const uint32_t off = sw128_offset<2>(m, e, TC_M);  // 8 bytes, inside one 16-byte chunk
+                *reinterpret_cast<uint2 *>(a_hi + off) = make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
+                *reinterpret_cast<uint2 *>(a_lo + off) = make_uint2(l[0] | (uint32_t(l[1]) << 16), l[2] | (uint32_t(l[3]) << 16));
+            } else {
+                uint32_t h[4], l[4];
+                Elem<TC_TF32X3>::split(v.x, h[0], l[0]);
+                Elem<TC_TF32X3>::split(v.y, h[1], l[1]);
+                Elem<TC_TF32X3>::split(v.z, h[2], l[2]);
+                Elem<TC_TF32X3>::split(v.w, h[3], l[3]);
+                const uint32_t off = sw128_offset<4>(m, e, TC_M);  // one 16-byte chunk
+                *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        // generic-proxy writes must be visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+            constexpr int PER = 128 / S::EB;  // elements per 128-byte column block
+            int acc = 0;
+#pragma unroll
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t A = pass == 2 ? al : ah;
+                const uint32_t B = pass == 1 ? bl : bh;
+#pragma unroll
+                for (int ks = 0; ks < S::KR / S::KSTEP; ++ks) {
+                    const int e = ks * S::KSTEP;
+                    const uint32_t aoff = uint32_t(e / PER) * TC_M * 128 + uint32_t(e % PER) * S::EB;
+                    const uint32_t boff = uint32_t(e / PER) * S::KR * 128 + uint32_t(e % PER) * S::EB;
+                    const uint64_t ad = sw128_desc(A + aoff), bd = sw128_desc(B + boff);
+                    if (PREC == TC_BF16X3)
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                    else
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        __syncwarp();
+        // every thread waits with a bound; the CTA leaves together if any gave up
+        const bool ok = __syncthreads_and(mbar_wait(mb, phase)) != 0;
+        if (!ok) {
+            failed = true;
+            if (tid == 0) atomicExch(p.err, 1);
+            // wait (bounded) for the MMAs in flight before the TMEM is freed
+            mbar_wait(mb, phase);
+            break;
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // ---- epilogue: row m = TMEM lane m; store rotated
+        const int m = warp * 32 + lane;
+        const uint64_t R = tile * TC_M + m;  // row index (bits k.. of the current index)
+        const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < S::KR; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(trow + uint32_t(c0)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 / 2 + j;  // complex column = low K bits of the current index
+                float2 v = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+                const uint64_t x = (R << K) | uint64_t(c);  // current index of this element
+                for (int e = 0; e < p.nepi; ++e) {
+                    const EpiOp &op = p.epi[e];
+                    if ((x & op.cmask) != op.cmask) continue;
+                    if (op.neg) {
+                        v.x = -v.x;
+                        v.y = -v.y;
+                        continue;
+                    }
+                    int s = 0;
+                    for (int t = 0; t < op.k; ++t) s = (s << 1) | int((x >> op.sel[t]) & 1);
+                    const float2 f = p.pool[op.moff + s];
+                    v = make_float2(f.x * v.x - f.y * v.y, f.x * v.y + f.y * v.x);
+                }
+                p.out[(uint64_t(c) << (n - K)) | R] = v;
+            }
+        }
+        // the next tile overwrites the A buffers and the accumulator
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        (void)rows_total;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+struct TcPass {
+    int k = 6;
+    int off = 0;                 // original qubit held by bit 0 of the current index
+    std::vector<cd> block;       // 2^k x 2^k on the window (index bit i = qubit off + i)
+    struct Diag {
+        std::vector<int> targets;  // original qubits (targets[0] = MSB of the entry index)
+        std::vector<int> controls;
+        std::vector<cd> d;
+    };
+    std::vector<Diag> epi;
+    int ngates = 0;
+};
+
+struct TcPlan {
+    int prec = TC_BF16X3;
+    std::vector<TcPass> passes;
+    struct Dev {
+        bool ready = false;
+        void *bimg = nullptr;
+        std::vector<size_t> boff;
+        std::vector<TcParams> params;
+        int *err = nullptr;
+    } dev;
+    ~TcPlan() {
+        if (dev.bimg) cudaFree(dev.bimg);
+        if (dev.err) cudaFree(dev.err);
+    }
+};
+
+namespace {
+
+// widths of consecutive passes: 6s and 5s (every total >= 20 is a sum of them)
+bool split56(int total, std::vector<int> &out) {
+    for (int b = total / 6; b >= 0; --b) {
+        const int rest = total - 6 * b;
+        if (rest % 5 == 0) {
+            out.assign(b, 6);
+            out.insert(out.end(), rest / 5, 5);
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace
+
+int build_tc(const qsim_circuit &c, qsim_plan &p) {
+    const int n = c.n;
+    const int kw = p.kmax >= 6 ? 6 : 5;
+    // a tile is 128 rows of the (2^(n-k) x 2^k) view
+    if (n < kw + 7 || n > 34) return set_error(QSIM_EUNSUPPORTED, "tensor-core plans need %d <= n <= 34 qubits", kw + 7);
+    TcPlan *tp = new TcPlan();
+    p.tc = tp;
+    tp->prec = kw == 6 ? TC_BF16X3 : TC_TF32X3;
+    // classify gates
+    std::vector<Op> ops(c.gates.size());
+    std::vector<bool> diag(c.gates.size());
+    for (size_t i = 0; i < c.gates.size(); ++i) {
+        const GateRec &g = c.gates[i];
+        QSIM_TRY(classify(g.m, g.targets, g.k, g.controls, g.nc, ops[i]));
+        diag[i] = ops[i].type == Op::DIAG || ops[i].type == Op::IDENTITY;
+        if (ops[i].type == Op::MONO) {
+            const size_t d = size_t(1) << ops[i].k;
+            ops[i].m.assign(d * d, cd(0.0));
+            for (size_t r = 0; r < d; ++r) ops[i].m[r * d + ops[i].perm[r]] = ops[i].phase[r];
+            ops[i].type = Op::DENSE;
+        }
+    }
+    std::vector<int> remaining(c.gates.size());
+    for (size_t i = 0; i < remaining.size(); ++i) remaining[i] = int(i);
+    int off = 0, rotated = 0;
+    int stall = 0;
+    while (!remaining.empty()) {
+        const int k = kw;
+        TcPass ps;
+        ps.k = k;
+        ps.off = off;
+        std::vector<int> win(k);
+        uint64_t wmask = 0;
+        for (int i = 0; i < k; ++i) {
+            win[i] = (off + i) % n;
+            wmask |= uint64_t(1) << win[i];
+        }
+        std::vector<int> qs(k);  // embedding order: MSB first
+        for (int i = 0; i < k; ++i) qs[i] = win[k - 1 - i];
+        ps.block.assign(size_t(1) << (2 * k), cd(0.0));
+        for (size_t i = 0; i < (size_t(1) << k); ++i) ps.block[i * ((size_t(1) << k) + 1)] = 1.0;
+        uint64_t blocked = 0;
+        std::vector<int> rest;
+        for (int gi : remaining) {
+            const Op &op = ops[gi];
+            uint64_t q = 0;
+            for (int t = 0; t < op.k; ++t) q |= uint64_t(1) << op.targets[t];
+            for (int t = 0; t < op.c; ++t) q |= uint64_t(1) << op.controls[t];
+            if (q & blocked) {
+                blocked |= q;
+                rest.push_back(gi);
+                continue;
+            }
+            if ((q & ~wmask) == 0) {
+                // inside the window: multiply into the block (later gates on the left)
+                GateRec gr;
+                gr.k = op.k;
+                gr.nc = op.c;
+                for (int t = 0; t < op.k; ++t) gr.targets[t] = op.targets[t];
+                for (int t = 0; t < op.c; ++t) gr.controls[t] = op.controls[t];
+                if (op.type == Op::DENSE) {
+                    gr.m = op.m;
+                } else if (op.type == Op::DIAG) {
+                    const size_t d = size_t(1) << op.k;
+                    gr.m.assign(d * d, cd(0.0));
+                    for (size_t r = 0; r < d; ++r) gr.m[r * d + r] = op.m[r];
+                } else {
+                    ps.ngates++;
+                    continue;  // identity
+                }
+                ps.block = matmul(embed_gate(gr, qs), ps.block, size_t(1) << k);
+                ps.ngates++;
+                continue;
+            }
+            if (diag[gi] && ops[gi].type != Op::IDENTITY) {
+                if (int(ps.epi.size()) >= MAX_EPI) {
+                    blocked |= q;
+                    rest.push_back(gi);
+                    continue;
+                }
+                // straddles the window: applied after the block, so the
+                // window qubits it touches take no further block gates
+                TcPass::Diag dg;
+                dg.targets.assign(op.targets, op.targets + op.k);
+                dg.controls.assign(op.controls, op.controls + op.c);
+                dg.d = op.m;
+                ps.epi.push_back(dg);
+                ps.ngates++;
+                blocked |= q & wmask;
+                continue;
+            }
+            if (ops[gi].type == Op::IDENTITY) {
+                ps.ngates++;
+                continue;
+            }
+            blocked |= q;
+            rest.push_back(gi);
+        }
+        stall = ps.ngates ? 0 : stall + 1;
+        if (stall > 2 * n) return set_error(QSIM_EUNSUPPORTED, "tensor-core planner: a gate wider than %d qubits", k);
+        tp->passes.push_back(std::move(ps));
+        remaining.swap(rest);
+        off = (off + k) % n;
+        rotated += k;
+    }
+    // close the rotation: extra identity passes until the total is a multiple
+    // of n (3xTF32 plans use width 5 only: width 6 does not fit shared memory)
+    for (int extra = (n - rotated % n) % n;; extra += n) {
+        std::vector<int> widths;
+        if (extra == 0) break;
+        const bool fits = kw == 5 ? (extra % 5 == 0 && (widths.assign(extra / 5, 5), true)) : split56(extra, widths);
+        if (fits) {
+            for (int w : widths) {
+                TcPass ps;
+                ps.k = w;
+                ps.off = off;
+                ps.block.assign(size_t(1) << (2 * w), cd(0.0));
+                for (size_t i = 0; i < (size_t(1) << w); ++i) ps.block[i * ((size_t(1) << w) + 1)] = 1.0;
+                tp->passes.push_back(std::move(ps));
+                off = (off + w) % n;
+            }
+            break;
+        }
+    }
+    return QSIM_OK;
+}
+
+namespace {
+
+template <int EB>
+void build_bimage(const std::vector<cd> &G, int k, std::vector<unsigned char> &img, int prec) {
+    const int KR = 2 << k;
+    const int d = 1 << k;
+    const size_t opnd = size_t(KR) * KR * EB;
+    img.assign(2 * opnd, 0);
+    for (int nn = 0; nn < KR; ++nn)
+        for (int kk = 0; kk < KR; ++kk) {
+            const int c = nn >> 1, s = nn & 1, cp = kk >> 1, t = kk & 1;
+            const cd g = G[size_t(c) * d + cp];
+            const double v = s == 0 ? (t == 0 ? g.real() : -g.imag()) : (t == 0 ? g.imag() : g.real());
+            const uint32_t off = sw128_offset<EB>(nn, kk, KR);
+            const float f = float(v);
+            if (prec == TC_BF16X3) {
+                // round-to-nearest-even bf16 split of the fp32 value
+                auto bf = [](float x) {
+                    uint32_t u;
+                    memcpy(&u, &x, 4);
+                    const uint32_t lsb = (u >> 16) & 1;
+                    u += 0x7FFF + lsb;
+                    return uint16_t(u >> 16);
+                };
+                const uint16_t h = bf(f);
+                uint32_t hu = uint32_t(h) << 16;
+                float hf;
+                memcpy(&hf, &hu, 4);
+                const uint16_t l = bf(f - hf);
+                memcpy(&img[off], &h, 2);
+                memcpy(&img[opnd + off], &l, 2);
+            } else {
+                uint32_t u;
+                memcpy(&u, &f, 4);
+                const uint32_t hu = u & 0xFFFFE000u;
+                float hf;
+                memcpy(&hf, &hu, 4);
+                const float lf = f - hf;
+                memcpy(&img[off], &hu, 4);
+                memcpy(&img[opnd + off], &lf, 4);
+            }
+        }
+}
+
+template <int K, int PREC> constexpr int smem_bytes() { return TcShape<K, PREC>::SMEM; }
+
+int prepare_tc(qsim_plan &p, int n) {
+    TcPlan &tp = *p.tc;
+    if (tp.dev.ready) return QSIM_OK;
+    std::vector<unsigned char> all, img;
+    tp.dev.boff.clear();
+    tp.dev.params.clear();
+    for (const TcPass &ps : tp.passes) {
+        if (tp.prec == TC_BF16X3) build_bimage<2>(ps.block, ps.k, img, tp.prec);
+        else build_bimage<4>(ps.block, ps.k, img, tp.prec);
+        tp.dev.boff.push_back(all.size());
+        all.insert(all.end(), img.begin(), img.end());
+        while (all.size() % 256) all.push_back(0);
+        TcParams prm;
+        memset(&prm, 0, sizeof prm);
+        prm.n = n;
+        prm.ntiles = (uint64_t(1) << (n - ps.k)) / TC_M;
+        int pool = 0;
+        for (const TcPass::Diag &dg : ps.epi) {
+            EpiOp &e = prm.epi[prm.nepi++];
+            auto cur = [&](int q) { return (q - ps.off + n) % n; };
+            e.cmask = 0;
+            for (int q : dg.controls) e.cmask |= uint64_t(1) << cur(q);
+            e.k = int(dg.targets.size());
+            for (int t = 0; t < e.k; ++t) e.sel[t] = cur(dg.targets[t]);
+            e.neg = (e.k == 0 && dg.d[0] == cd(-1.0)) ? 1 : 0;
+            e.moff = pool;
+            if (pool + int(dg.d.size()) > MAX_EPI_POOL) return set_error(QSIM_EUNSUPPORTED, "epilogue pool overflow");
+            for (const cd &v : dg.d) prm.pool[pool++] = make_float2(float(v.real()), float(v.imag()));
+        }
+        tp.dev.params.push_back(prm);
+    }
+    QSIM_CUDA_TRY(cudaMalloc(&tp.dev.bimg, all.size()), "tc B images");
+    QSIM_CUDA_TRY(cudaMemcpy(tp.dev.bimg, all.data(), all.size(), cudaMemcpyHostToDevice), "tc B upload");
+    QSIM_CUDA_TRY(cudaMalloc(&tp.dev.err, sizeof(int)), "tc error flag");
+    QSIM_CUDA_TRY(cudaMemset(tp.dev.err, 0, sizeof(int)), "tc error flag clear");
+    tp.dev.ready = true;
+    return QSIM_OK;
+}
+
+int sm_count_tc() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 148;
+    }
+    return v;
+}
+
+template <int K, int PREC>
+int launch_tc_k(const TcParams &prm, cudaStream_t st) {
+    constexpr int smem = TcShape<K, PREC>::SMEM;
+    static bool attr = false;
+    if (!attr) {
+        QSIM_CUDA_TRY(cudaFuncSetAttribute(k_tc_block<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "tc smem attribute");
+        attr = true;
+    }
+    const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
+    const uint64_t want = uint64_t(sm_count_tc()) * per_sm;
+    const unsigned grid = unsigned(std::min<uint64_t>(want, prm.ntiles));
+    LaunchScope ls(K_TC_BLOCK, st, 2.0 * double(prm.ntiles) * TC_M * (2 << K) * 4.0);
+    k_tc_block<K, PREC><<<grid, TC_THREADS, smem, st>>>(prm);
+    QSIM_CUDA_TRY(cudaGetLastError(), "tc launch");
+    return QSIM_OK;
+}
+
+}  // namespace
+
+int run_tc(qsim_state *s, qsim_plan &p) {
+    if (s->dtype != QSIM_C64) return set_error(QSIM_EUNSUPPORTED, "tensor-core plans run complex64 states");
+    QSIM_TRY(prepare_tc(p, s->n));
+    TcPlan &tp = *p.tc;
+    const size_t bytes = s->size() * s->amp_bytes();
+    // ping-pong partner buffer in the state's scratch (grow-only)
+    QSIM_TRY(s->ensure_scratch(bytes));
+    float2 *bufs[2] = {static_cast<float2 *>(s->amps), static_cast<float2 *>(s->scratch)};
+    int cur = 0;
+    for (size_t i = 0; i < tp.passes.size(); ++i) {
+        TcParams prm = tp.dev.params[i];
+        prm.in = bufs[cur];
+        prm.out = bufs[cur ^ 1];
+        prm.bimg = reinterpret_cast<const uint4 *>(static_cast<char *>(tp.dev.bimg) + tp.dev.boff[i]);
+        prm.err = tp.dev.err;
+        const int k = tp.passes[i].k;
+        int rc;
+        if (tp.prec == TC_BF16X3) rc = k == 6 ? launch_tc_k<6, TC_BF16X3>(prm, s->stream) : launch_tc_k<5, TC_BF16X3>(prm, s->stream);
+        else rc = k == 6 ? launch_tc_k<6, TC_TF32X3>(prm, s->stream) : launch_tc_k<5, TC_TF32X3>(prm, s->stream);
+        QSIM_TRY(rc);
+        cur ^= 1;
+    }
+    if (cur == 1) {
+        LaunchScope ls(K_COPY, s->stream, 2.0 * double(bytes));
+        QSIM_CUDA_TRY(cudaMemcpyAsync(s->amps, s->scratch, bytes, cudaMemcpyDeviceToDevice, s->stream), "tc result copy");
+    }
+    int err = 0;
+    QSIM_CUDA_TRY(cudaMemcpyAsync(&err, tp.dev.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "tc flag read");
+    QSIM_CUDA_TRY(cudaStreamSynchronize(s->stream), "tc sync");
+    if (err) {
+        cudaMemsetAsync(tp.dev.err, 0, sizeof(int), s->stream);
+        return set_error(QSIM_ETIMEOUT, "tensor-core pass: an mbarrier wait exceeded its bound");
+    }
+    return QSIM_OK;
+}
+
+int tc_nsweeps(const qsim_plan &p) { return p.tc ? int(p.tc->passes.size()) : 0; }
+
+void tc_describe(const qsim_plan &p, std::string &out) {
+    if (!p.tc) return;
+    char buf[256];
+    snprintf(buf, sizeof buf, "tensor-core plan: %zu passes, %s\n", p.tc->passes.size(),
+             p.tc->prec == TC_BF16X3 ? "BF16x3 (kind::f16)" : "3xTF32 (kind::tf32)");
+    out += buf;
+    for (size_t i = 0; i < p.tc->passes.size(); ++i) {
+        const TcPass &ps = p.tc->passes[i];
+        snprintf(buf, sizeof buf, "  %3zu k=%d qubits %d..%d (mod n) gates=%d epilogue=%zu\n", i, ps.k, ps.off,
+                 ps.off + ps.k - 1, ps.ngates, ps.epi.size());
+        out += buf;
+    }
+}
+
 }  // namespace qsim
 
 void qsim_plan::release_tc() {

@@ -87,3 +87,39 @@ def test_staged_covers_fewer_sweeps(q):
     c = inputs.random_circuit(30, 20, seed=2022)
     info = q.Plan(c, kmax=4, mode=q.FUSE_STAGED).info()
     assert info["gates"] == 900 and info["sweeps"] < 60
+
+
+@pytest.mark.parametrize("kmax", [5, 6])
+@pytest.mark.parametrize("maker", ["random", "variational", "local2q"])
+def test_tensor_core_blocks_match_oracle(q, orc, kmax, maker):
+    """Fused k-qubit blocks as split-precision real GEMMs on tcgen05
+    (kmax 6: BF16x3, kmax 5: 3xTF32), bit-rotating passes, complex64."""
+    n = {"random": 14, "variational": 15, "local2q": 13}[maker]
+    rng = np.random.default_rng(11)
+    if maker == "random":
+        circ = inputs.random_circuit(n, 5, seed=21)
+    elif maker == "variational":
+        circ = inputs.variational(n, 3, seed=22)
+    else:  # dense 2-qubit gates on neighbours plus controlled gates inside a window
+        gates = []
+        for layer in range(4):
+            for a in range(layer % 2, n - 1, 2):
+                gates.append(inputs.Gate("matrix", (a + 1, a), (), (), -1, inputs.random_dense_gate(rng, 2)))
+            gates.append(inputs.Gate("x", (3,), (1,)))
+            gates.append(inputs.Gate("cz", (0, n - 1)))
+        circ = inputs.Circuit(n, gates)
+    psi0 = inputs.gaussian_state(n, seed=23)
+    want = orc.simulate(circ, psi0)
+    got = run_plan(q, circ, "c64", psi0, q.FUSE_TC, kmax)
+    err = np.max(np.abs(got - want))
+    rel = err / np.max(np.abs(want))
+    assert err <= 1e-5, f"tc {maker} kmax={kmax}: max-abs {err:.3e} (relative {rel:.3e})"
+    # the split keeps ~16 (BF16x3) or ~21 (3xTF32) bits per operand
+    assert rel <= (2e-4 if kmax == 6 else 2e-5), f"relative error {rel:.3e}"
+
+
+def test_tensor_core_rejects_complex128(q):
+    circ = inputs.random_circuit(13, 2, seed=1)
+    s = q.State(13, "c128").init_zero()
+    with pytest.raises(q.QsimError):
+        s.run_fused(q.Plan(circ, kmax=6, mode=q.FUSE_TC))

@@ -114,3 +114,16 @@ def test_greedy2_blocks_equal_product_of_oracle_gates(q, orc):
 def test_plan_rejects_bad_mode(q):
     with pytest.raises(q.QsimError):
         q.Plan(inputs.qft(4), kmax=2, mode=7)
+
+
+def test_staged_and_tc_plans_describe(q):
+    c = inputs.random_circuit(30, 20, seed=2022)
+    st = q.Plan(c, kmax=4, mode=q.FUSE_STAGED)
+    assert st.info()["gates"] == 900 and "tile" in st.describe()
+    tc = q.Plan(c, kmax=6, mode=q.FUSE_TC)
+    info = tc.info()
+    assert info["gates"] == 900 and info["sweeps"] % 5 == 0  # 30 qubits = 5 windows of 6
+    assert "BF16x3" in tc.describe()
+    assert "3xTF32" in q.Plan(c, kmax=5, mode=q.FUSE_TC).describe()
+    with pytest.raises(q.QsimError):
+        q.Plan(inputs.random_circuit(10, 2, seed=1), kmax=6, mode=q.FUSE_TC)
