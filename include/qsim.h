@@ -256,7 +256,7 @@ QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, cons
 /* ---------------------------------------------------------------- batches */
 typedef struct qsim_batch qsim_batch;
 
-/* A batch of many small circuits (2 <= n <= 20 qubits each, complex64 states)
+/* A batch of many small circuits (9 <= n <= 20 qubits each, complex64 states)
  * run by one persistent kernel: each CTA takes the next circuit from a device
  * work counter (largest first), simulates it with its state resident in
  * shared memory (n <= 14) or in a per-CTA global slot streamed through shared
@@ -269,8 +269,15 @@ QSIM_API int qsim_batch_destroy(qsim_batch *b);
  * Safe to capture in a CUDA graph (the work counter is reset by a memset
  * node inside the captured sequence). */
 QSIM_API int qsim_batch_run(qsim_batch *b, double *out_dev, void *cuda_stream);
-/* Tuning knobs (threads per CTA, tile qubits); 0 = automatic. */
-QSIM_API int qsim_batch_set_config(qsim_batch *b, int threads, int tile_qubits);
+/* Tuning knobs: CTAs per SM (1..8) and tile width in qubits (9..12, at most
+ * the smallest circuit's width; threads per CTA = 2^(tile_qubits - 4));
+ * 0 = automatic. */
+QSIM_API int qsim_batch_set_config(qsim_batch *b, int ctas_per_sm, int tile_qubits);
+/* Autotuner: runs the batch (reps timed runs per candidate, CUDA events on
+ * `cuda_stream`) for every tile width / CTAs-per-SM candidate, keeps the
+ * fastest as the batch's configuration and reports it (outputs may be NULL). */
+QSIM_API int qsim_batch_autotune(qsim_batch *b, void *cuda_stream, int reps, int *best_tile_qubits,
+                                 int *best_ctas_per_sm, double *best_ms);
 
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each

@@ -71,6 +71,7 @@ _SIGS = {
     "qsim_batch_destroy": ([P], I),
     "qsim_batch_run": ([P, P, P], I),
     "qsim_batch_set_config": ([P, I, I], I),
+    "qsim_batch_autotune": ([P, P, I, P, P, P], I),
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),
@@ -349,8 +350,14 @@ class Batch:
             _lib.qsim_batch_destroy(self.handle)
             self.handle = None
 
-    def set_config(self, threads: int = 0, tile_qubits: int = 0):
-        _check(lib().qsim_batch_set_config(self.handle, threads, tile_qubits))
+    def set_config(self, ctas_per_sm: int = 0, tile_qubits: int = 0):
+        _check(lib().qsim_batch_set_config(self.handle, ctas_per_sm, tile_qubits))
+
+    def autotune(self, reps: int = 2, stream=None):
+        t, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().qsim_batch_autotune(self.handle, _stream_ptr(stream), reps, ctypes.byref(t), ctypes.byref(c),
+                                         ctypes.byref(ms)))
+        return {"tile_qubits": t.value, "ctas_per_sm": c.value, "ms": ms.value}
 
     def run(self, out, stream=None):
         _check(lib().qsim_batch_run(self.handle, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))

@@ -1,0 +1,314 @@
+// Register-tile stage interpreter shared by the staged fusion kernel and the
+// batched persistent kernel (see staged.cu for the scheme).
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace qsim {
+namespace stage {
+
+constexpr int LANE_BITS = 5;
+constexpr int REG_BITS = 4;  // amplitudes per thread = 16
+constexpr int MAX_WARP_BITS = 4;
+constexpr int MAX_SLOTS = REG_BITS + MAX_WARP_BITS;
+constexpr int MAX_OPS = 192;
+constexpr int MAX_PHASES = 24;
+constexpr int MAX_POOL = 768;
+
+enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3 };
+
+// Position codes: 0..4 lane bit, 8 + b register bit b, 32 + q bit q of the
+// thread's base index (lane, warp or tile qubit).
+constexpr int POS_REG = 8;
+constexpr int POS_BASE = 32;
+
+struct StageOp {
+    uint64_t tmask;  // control bits outside the registers: (base & tmask) == tmask
+    int32_t moff;    // offset of the matrix / diagonal in the pool (complex entries)
+    int8_t type;
+    int8_t a, b;     // U1: target position; U2: positions (a = MSB); EXCHANGE: a = phase
+    int8_t k;        // DIAG: number of selector qubits
+    int8_t rneed;    // control bits on register qubits: (j & rneed) == rneed
+    int8_t flags;    // DIAG k = 0: 1 when the factor is exactly -1
+    int8_t dq[QSIM_MAX_TARGETS];  // DIAG selectors (position codes), dq[0] = MSB
+};
+
+struct Phase {
+    int8_t rq[REG_BITS];       // global qubit of register bit b
+    int8_t wq[MAX_WARP_BITS];  // global qubit of warp bit b
+    int8_t rslot[REG_BITS];    // shared-memory bit (above the lane bits) of register bit b
+    int8_t wslot[MAX_WARP_BITS];
+};
+
+template <typename C> struct StageParams {
+    IndexMap outer;  // inserts zeros at the tile qubits (tile id -> base index)
+    int nops, phase0;
+    Phase phases[MAX_PHASES];
+    StageOp ops[MAX_OPS];
+    C pool[MAX_POOL];
+};
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cmad(C a, C b, C acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+
+__device__ __forceinline__ uint64_t expand(uint64_t g, const IndexMap &m) {
+#pragma unroll 1
+    for (int i = 0; i < m.nins; ++i) {
+        const uint64_t low = g & ((uint64_t(1) << m.ins[i]) - 1);
+        g = ((g ^ low) << 1) | low;
+    }
+    return g | m.set;
+}
+
+template <typename C, int JB, bool CTRL>
+__device__ __forceinline__ void u1_reg(C (&v)[1 << REG_BITS], C m00, C m01, C m10, C m11, int rneed) {
+#pragma unroll
+    for (int i = 0; i < (1 << REG_BITS); ++i) {
+        if (i & (1 << JB)) continue;
+        if (CTRL && (i & rneed) != rneed) continue;
+        const C a = v[i], b = v[i | (1 << JB)];
+        v[i] = cmad(m01, b, cmul(m00, a));
+        v[i | (1 << JB)] = cmad(m11, b, cmul(m10, a));
+    }
+}
+
+template <typename C, int JB>
+__device__ __forceinline__ void u1_reg_dispatch(C (&v)[1 << REG_BITS], C m00, C m01, C m10, C m11, int rneed) {
+    if (rneed) u1_reg<C, JB, true>(v, m00, m01, m10, m11, rneed);
+    else u1_reg<C, JB, false>(v, m00, m01, m10, m11, 0);
+}
+
+template <typename C, int JA, int JB>
+__device__ __forceinline__ void u2_reg(C (&v)[1 << REG_BITS], const C *m, int rneed) {
+    // matrix index bit 1 <-> register bit JA, bit 0 <-> register bit JB
+#pragma unroll
+    for (int i = 0; i < (1 << REG_BITS); ++i) {
+        if (i & ((1 << JA) | (1 << JB))) continue;
+        if ((i & rneed) != rneed) continue;
+        const int idx[4] = {i, i | (1 << JB), i | (1 << JA), i | (1 << JA) | (1 << JB)};
+        C x[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = v[idx[c]];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            C acc = cmul(m[r * 4], x[0]);
+#pragma unroll
+            for (int c = 1; c < 4; ++c) acc = cmad(m[r * 4 + c], x[c], acc);
+            v[idx[r]] = acc;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 shfl_c(float2 a, int mask) {
+    a.x = __shfl_xor_sync(0xffffffffu, a.x, mask);
+    a.y = __shfl_xor_sync(0xffffffffu, a.y, mask);
+    return a;
+}
+__device__ __forceinline__ double2 shfl_c(double2 a, int mask) {
+    a.x = __shfl_xor_sync(0xffffffffu, a.x, mask);
+    a.y = __shfl_xor_sync(0xffffffffu, a.y, mask);
+    return a;
+}
+
+// Global index of register 0 of this thread in phase P.
+template <int W>
+__device__ __forceinline__ uint64_t thread_base(const Phase &P, uint64_t tile_base, int lane, int warp) {
+    uint64_t b = tile_base | uint64_t(lane);
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if ((warp >> i) & 1) b |= uint64_t(1) << P.wq[i];
+    return b;
+}
+
+template <typename C, int W, bool STORE>
+__device__ __forceinline__ void tile_global(C *__restrict__ psi, C (&v)[1 << REG_BITS], const Phase &P,
+                                            uint64_t base) {
+    uint64_t rm[REG_BITS];
+#pragma unroll
+    for (int b = 0; b < REG_BITS; ++b) rm[b] = uint64_t(1) << P.rq[b];
+#pragma unroll
+    for (int j = 0; j < (1 << REG_BITS); ++j) {
+        uint64_t x = base;
+#pragma unroll
+        for (int b = 0; b < REG_BITS; ++b)
+            if ((j >> b) & 1) x |= rm[b];
+        if (STORE) psi[x] = v[j];
+        else v[j] = psi[x];
+    }
+}
+
+template <typename C, int W, bool STORE>
+__device__ __forceinline__ void tile_shared(C *tile, C (&v)[1 << REG_BITS], const Phase &P, int lane, int warp) {
+    uint32_t lb = uint32_t(lane), lm[REG_BITS];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        if ((warp >> i) & 1) lb |= uint32_t(1) << (LANE_BITS + P.wslot[i]);
+#pragma unroll
+    for (int b = 0; b < REG_BITS; ++b) lm[b] = uint32_t(1) << (LANE_BITS + P.rslot[b]);
+#pragma unroll
+    for (int j = 0; j < (1 << REG_BITS); ++j) {
+        uint32_t l = lb;
+#pragma unroll
+        for (int b = 0; b < REG_BITS; ++b)
+            if ((j >> b) & 1) l |= lm[b];
+        if (STORE) tile[l] = v[j];
+        else v[j] = tile[l];
+    }
+}
+
+
+// One pass of the op list over the tile held in v (16 amplitudes per thread).
+// Src supplies op(o), phase(i) and pool(i); ph / base are the current phase
+// and the thread's base index, updated by EXCHANGE ops.
+template <typename C, int W, typename Src>
+__device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 << REG_BITS], int &ph, uint64_t &base,
+                                           uint64_t tile_base, C *tile, int lane, int warp) {
+    constexpr int NR = 1 << REG_BITS;
+    for (int o = 0; o < nops; ++o) {
+        const StageOp &op = src.op(o);
+        const int type = op.type;
+        if (type == SOP_EXCHANGE) {
+            tile_shared<C, W, true>(tile, v, src.phase(ph), lane, warp);
+            __syncthreads();
+            ph = op.a;
+            base = thread_base<W>(src.phase(ph), tile_base, lane, warp);
+            tile_shared<C, W, false>(tile, v, src.phase(ph), lane, warp);
+            __syncthreads();
+            continue;
+        }
+        // controls on lane / warp / tile qubits: one test per thread (a lane
+        // gate still takes part in the shuffles when its controls are not met)
+        const bool tok = (base & op.tmask) == op.tmask;
+        if (!tok && !(type == SOP_U1 && op.a < POS_REG)) continue;
+        const int rneed = op.rneed;
+        if (type == SOP_U1) {
+            const C m00 = src.pool(op.moff), m01 = src.pool(op.moff + 1);
+            const C m10 = src.pool(op.moff + 2), m11 = src.pool(op.moff + 3);
+            if (op.a >= POS_REG) {
+                switch (op.a - POS_REG) {
+                    case 0: u1_reg_dispatch<C, 0>(v, m00, m01, m10, m11, rneed); break;
+                    case 1: u1_reg_dispatch<C, 1>(v, m00, m01, m10, m11, rneed); break;
+                    case 2: u1_reg_dispatch<C, 2>(v, m00, m01, m10, m11, rneed); break;
+                    default: u1_reg_dispatch<C, 3>(v, m00, m01, m10, m11, rneed); break;
+                }
+            } else {
+                const int bit = (lane >> op.a) & 1;
+                const C cs = bit ? m11 : m00, co = bit ? m10 : m01;
+                const int lm = 1 << op.a;
+                if (tok && rneed == 0) {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], lm), cmul(cs, v[j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) {
+                        const C other = shfl_c(v[j], lm);
+                        if (tok && (j & rneed) == rneed) v[j] = cmad(co, other, cmul(cs, v[j]));
+                    }
+                }
+            }
+        } else if (type == SOP_U2) {
+            C m[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) m[e] = src.pool(op.moff + e);
+            switch ((op.a - POS_REG) * 4 + (op.b - POS_REG)) {
+                case 1: u2_reg<C, 0, 1>(v, m, rneed); break;
+                case 2: u2_reg<C, 0, 2>(v, m, rneed); break;
+                case 3: u2_reg<C, 0, 3>(v, m, rneed); break;
+                case 4: u2_reg<C, 1, 0>(v, m, rneed); break;
+                case 6: u2_reg<C, 1, 2>(v, m, rneed); break;
+                case 7: u2_reg<C, 1, 3>(v, m, rneed); break;
+                case 8: u2_reg<C, 2, 0>(v, m, rneed); break;
+                case 9: u2_reg<C, 2, 1>(v, m, rneed); break;
+                case 11: u2_reg<C, 2, 3>(v, m, rneed); break;
+                case 12: u2_reg<C, 3, 0>(v, m, rneed); break;
+                case 13: u2_reg<C, 3, 1>(v, m, rneed); break;
+                default: u2_reg<C, 3, 2>(v, m, rneed); break;
+            }
+        } else if (op.k == 0) {  // SOP_DIAG, one factor on the control subspace
+            if (op.flags & 1) {
+                if (rneed == 0) {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) {
+                        v[j].x = -v[j].x;
+                        v[j].y = -v[j].y;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j)
+                        if ((j & rneed) == rneed) {
+                            v[j].x = -v[j].x;
+                            v[j].y = -v[j].y;
+                        }
+                }
+            } else {
+                const C f = src.pool(op.moff);
+#pragma unroll
+                for (int j = 0; j < NR; ++j)
+                    if ((j & rneed) == rneed) v[j] = cmul(f, v[j]);
+            }
+        } else {  // SOP_DIAG with selector qubits
+            int sel_t = 0, regsel[QSIM_MAX_TARGETS];
+            const int k = op.k;
+            for (int t = 0; t < k; ++t) {
+                const int code = op.dq[t];
+                const int sh = k - 1 - t;
+                if (code >= POS_BASE) {
+                    sel_t |= int((base >> (code - POS_BASE)) & 1) << sh;
+                    regsel[t] = 0;
+                } else {
+                    regsel[t] = code - POS_REG + 1;  // register bit + 1
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if ((j & rneed) != rneed) continue;
+                int sel = sel_t;
+                for (int t = 0; t < k; ++t)
+                    if (regsel[t]) sel |= ((j >> (regsel[t] - 1)) & 1) << (k - 1 - t);
+                v[j] = cmul(src.pool(op.moff + sel), v[j]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host planner
+struct GateClass {
+    enum { DIAG, DENSE1, DENSE2, OTHER } kind;
+    Op op;  // classified form (targets reduced, controls extended)
+};
+
+struct Stage {
+    bool plain = false;
+    Op op;                   // plain: one sweep
+    std::vector<int> slots;  // tile qubits outside the lanes (slot s <-> slots[s])
+    std::vector<StageOp> ops;
+    std::vector<Phase> phases;
+    std::vector<cd> pool;
+    int phase0 = 0;
+};
+
+// Split a circuit into stages for tiles of 2^(9 + W) amplitudes.  With
+// `limits` the op, phase and pool counts of a stage stay within one kernel
+// parameter block.
+int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out);
+
+}  // namespace stage
+}  // namespace qsim
