@@ -190,6 +190,41 @@ def run_reference(args, ws, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+PLAN_KMAX = {"greedy2": 2, "staged": 4, "tc": 6}
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz):
+    """Roofline object for the kernel with the largest share of device time."""
+    if not prof:
+        return None
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    avg_ms = d["ms"] / d["launches"]
+    gbs = d["bytes"] / d["launches"] / (avg_ms / 1e3) / 1e9
+    share = d["ms"] / sum(v["ms"] for v in prof.values())
+    common = {"kernel": name, "avg_launch_ms": avg_ms, "launch_share": round(share, 4),
+              "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+              "flops_per_launch": d.get("flops", 0.0) / d["launches"]}
+    if name == "stage":
+        # register-tile interpreter: bound by the FP32 pipe / issue, not HBM
+        tf = d["flops"] / d["launches"] / (avg_ms / 1e3) / 1e12
+        pk = fp32_peak_tflops(sm_max_mhz)
+        r = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
+             "frac": round(tf / pk, 4), "traffic": NCU_TRAFFIC_30Q_C64.get(name),
+             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+             "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
+    else:
+        r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_gbs, "unit": "GB/s",
+             "frac": round(gbs / peak_gbs, 4), "traffic": NCU_TRAFFIC_30Q_C64.get(name),
+             "peak_source": peak_src}
+    r.update(common)
+    return r
+
+
 def run_qsim(args, ws, rank, local):
     import torch
     from paper_2203_08826_gb300 import binding as q
@@ -205,6 +240,13 @@ def run_qsim(args, ws, rank, local):
         if pg:
             pg.barrier()
 
+    def max_over_ranks(x: float) -> float:
+        if not pg:
+            return x
+        t = torch.tensor([x], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
     n = args.qubits
     circ = inputs.random_circuit(n, DEPTH, seed=2022 + rank)
     ngates = len(circ)
@@ -212,32 +254,32 @@ def run_qsim(args, ws, rank, local):
     ham = inputs.zz_chain(n)
     st = torch.cuda.current_stream()
     state = q.State(n, args.dtype)
-
-    PLAN_MODES = {"greedy2": (q.FUSE_GREEDY2, 2), "staged": (q.FUSE_STAGED, 6), "tc": (q.FUSE_TC, 6)}
+    mode_ids = {"greedy2": q.FUSE_GREEDY2, "staged": q.FUSE_STAGED, "tc": q.FUSE_TC}
     plans = {}
-    for name, (mode, k) in PLAN_MODES.items():
+    for name, mode in mode_ids.items():
+        if name == "tc" and args.dtype != "c64":
+            continue
         try:
-            plans[name] = q.Plan(qc, kmax=k, mode=mode)
+            plans[name] = q.Plan(qc, kmax=PLAN_KMAX[name], mode=mode)
         except q.QsimError:
             pass
     chosen = args.mode
     if chosen == "auto":
-        chosen = "staged" if "staged" in plans else "plain"
+        # complex64: the staged tiles; complex128 is FP64-bound, plain sweeps touch the fewest amplitudes
+        chosen = "staged" if (args.dtype == "c64" and "staged" in plans) else "plain"
 
-    def step(mode_name, out=None):
+    def step(mode_name):
         state.init_zero()
         if mode_name == "plain":
             state.run(qc)
         else:
             state.run_fused(plans[mode_name])
-        e = state.expectation(ham)
-        shots = state.sample(SHOTS, seed=7, counter0=0)
-        if out is not None:
-            out.append((e, shots))
+        state.expectation(ham)
+        state.sample(SHOTS, seed=7, counter0=0)
 
-    def timed(mode_name, warmup, steps, profile=False, clocks=None):
+    def timed(fn, warmup, steps, profile=False):
         for _ in range(warmup):
-            step(mode_name)
+            fn()
         torch.cuda.synchronize()
         barrier()
         if profile:
@@ -246,95 +288,80 @@ def run_qsim(args, ws, rank, local):
         l0 = q.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         e0.record(st)
-        t0 = time.perf_counter()
         for _ in range(steps):
-            step(mode_name)
+            fn()
         e1.record(st)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
         launches = q.launch_count() - l0
         prof = None
         if profile:
             prof = q.profile_read()
             q.profile_enable(False)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if pg:
-            t = torch.tensor([ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, wall, launches, prof
+        return max_over_ranks(e0.elapsed_time(e1)), launches, prof
 
-    # ---- headline: chosen mode, profiled, clocks sampled
+    # ---- headline: chosen mode, profiled, clocks sampled during the timed steps
     with ClockSampler(local) as clk:
-        ms, wall, launches, prof = timed(chosen, args.warmup, args.steps, profile=True)
+        ms, launches, prof = timed(lambda: step(chosen), args.warmup, args.steps, profile=True)
     clocks = clk.summary()
-    total_gates = ngates * args.steps * ws
-    value = total_gates / (ms / 1e3)
-
-    # dominant kernel and its roofline
+    value = ngates * args.steps * ws / (ms / 1e3)
     peak, peak_src = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
-    roof = None
-    if dom:
-        name, d = dom
-        avg_ms = d["ms"] / d["launches"]
-        bytes_per_launch = d["bytes"] / d["launches"]
-        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": NCU_TRAFFIC_30Q_C64.get(name) if (n == 30 and args.dtype == "c64") else None,
-                "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                "launch_share": round(d["ms"] / sum(v["ms"] for v in prof.values()), 4)}
-        if args.dtype == "c128" and name in ("sweep_dense1",):
-            # complex128 dense sweeps run into the FP64 pipe before HBM
-            roof["note"] = "complex128 dense sweep: FP64-ALU bound (8 FMA per amplitude)"
+    roof = roofline_of(prof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0)
 
-    # ---- the other modes (informational, same circuit)
+    # ---- the same circuit through the other execution modes
     others = {}
-    for other in ([] if args.quick else ["plain"] + [m for m in plans if m != chosen]):
-        if other == chosen:
-            continue
-        oms, _, ol, _ = timed(other, 1, 1)
-        others[other] = {"s_per_circuit": oms / 1e3, "gates_per_s": ngates / (oms / 1e3), "launches": ol}
+    if not args.quick:
+        for other in ["plain"] + [m for m in plans if m != chosen]:
+            if other == chosen:
+                continue
+            oms, ol, oprof = timed(lambda: step(other), 1, 1, profile=True)
+            others[other] = {"s_per_circuit": oms / 1e3, "gates_per_s": ngates / (oms / 1e3), "launches": ol,
+                             "sweeps": plans[other].info()["sweeps"] if other in plans else ngates,
+                             "roofline": roofline_of(oprof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0)}
 
     # ---- end to end through the public API with host buffers
-    amp_bytes = (8 if args.dtype == "c64" else 16) << n
-    h_in = torch.zeros(1 << n, dtype=state.tensor.dtype, pin_memory=True)
-    h_in[0] = 1
-    h_out = torch.empty_like(h_in, pin_memory=True)
+    e2e = None
+    if not args.quick:
+        amp_bytes = (8 if args.dtype == "c64" else 16) << n
+        h_in = torch.zeros(1 << n, dtype=state.tensor.dtype).pin_memory()
+        h_in[0] = 1
+        h_out = torch.empty_like(h_in).pin_memory()
 
-    def e2e_step():
-        qc_e = q.QCircuit(circ)  # marshal the gate list (the user's call)
-        state.from_host_async(h_in)
-        if chosen == "plain":
-            state.run(qc_e)
-        else:
-            mode, k = PLAN_MODES[chosen]
-            state.run_fused(q.Plan(qc_e, kmax=k, mode=mode))
-        e = state.expectation(ham)
-        state.to_host_into(h_out)
-        return e
+        def e2e_step():
+            qc_e = q.QCircuit(circ)  # the gate list travels from the host every step
+            state.from_host_async(h_in)
+            if chosen == "plain":
+                state.run(qc_e)
+            else:
+                state.run_fused(q.Plan(qc_e, kmax=PLAN_KMAX[chosen], mode=mode_ids[chosen]))
+            e = state.expectation(ham)
+            state.to_host_into(h_out)
+            return e
 
-    e2e_steps = 0 if args.quick else max(1, min(args.steps, 3))
-    for _ in range(max(1, min(args.warmup, 3)) if e2e_steps else 0):
-        e2e_step()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ngates * e2e_steps * ws / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": amp_bytes,
-           "d2h_bytes_per_step": amp_bytes + 8} if e2e_steps else None
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(max(1, min(args.warmup, 3))):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": ngates * e2e_steps * ws / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": amp_bytes,
+               "d2h_bytes_per_step": amp_bytes + 8,
+               "includes": "gate-list marshalling + plan build, H2D of the initial state from pinned memory, "
+                           "circuit, expectation, D2H of the final state"}
+        del h_in, h_out
+    del state
+    plans.clear()
+    torch.cuda.empty_cache()
+
+    # ---- other workloads of the scope (rank 0 only, informational)
+    extra = {}
+    if rank == 0 and not (args.quick or args.no_extra):
+        extra = other_workloads(q, torch, peak, peak_src)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
@@ -356,15 +383,116 @@ def run_qsim(args, ws, rank, local):
                                    f"CZ on a random perfect matching per layer), |0> start, "
                                    f"<sum Z_i Z_i+1> + {SHOTS} shots per step",
                        "qubits": n, "depth": DEPTH, "gates": ngates, "state": args.dtype, "mode": chosen,
-                       "state_bytes": amp_bytes, "l2": "inputs larger than L2 (state 8+ GiB vs 129 MB L2)"},
+                       "l2": "inputs larger than L2 (state >= 8 GiB vs 129 MB L2)"},
             "s_per_circuit": ms / 1e3 / args.steps,
             "gpu_launches": launches,
             "roofline": roof, "kernels": prof, "other_modes": others, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": clocks,
+            "clocks": clocks, "other_workloads": extra,
         }
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def other_workloads(q, torch, peak, peak_src):
+    """The scope's other workloads, each timed with CUDA events (W warm-up, K timed)."""
+    out = {}
+    st = torch.cuda.current_stream()
+
+    def ev_time(fn, warmup, steps, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if profile:
+            q.profile_reset()
+            q.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = q.profile_read()
+            q.profile_enable(False)
+        return e0.elapsed_time(e1) / steps, prof
+
+    # QFT, 30 qubits
+    c = inputs.qft(30)
+    qc = q.QCircuit(c)
+    for dt in ("c64", "c128"):
+        s = q.State(30, dt).init_zero()
+        res = {}
+        if dt == "c64":
+            p = q.Plan(qc, kmax=4, mode=q.FUSE_STAGED)
+            ms, _ = ev_time(lambda: s.run_fused(p), 3, 3)
+            res["staged"] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3)}
+        ms, _ = ev_time(lambda: s.run(qc), 1 if dt == "c128" else 3, 1 if dt == "c128" else 3)
+        res["plain"] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3)}
+        out[f"qft30_{dt}"] = res
+        del s
+        torch.cuda.empty_cache()
+    # random circuit in complex128 (FP64-bound plain sweeps)
+    c = inputs.random_circuit(30, DEPTH, seed=2022)
+    qc = q.QCircuit(c)
+    s = q.State(30, "c128").init_zero()
+    ms, prof = ev_time(lambda: s.run(qc), 1, 1, profile=True)
+    d = prof.get("sweep_dense1")
+    fp64 = None
+    if d:
+        fp64 = {"kernel": "sweep_dense1", "bound": "alu (FP64)", "unit": "TFLOP/s",
+                "achieved": round(d["flops"] / (d["ms"] / 1e3) / 1e12, 3),
+                "peak": 1.21, "peak_source": "FP64 FMA rate probe on this pool (1.21 TFLOP/s)",
+                "hbm_gbs": round(d["bytes"] / (d["ms"] / 1e3) / 1e9, 1)}
+        fp64["frac"] = round(fp64["achieved"] / fp64["peak"], 4)
+    out["random30_c128_plain"] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3), "roofline": fp64}
+    del s
+    torch.cuda.empty_cache()
+    # variational ansatz, 32 qubits, 20 layers, complex64
+    c = inputs.variational(32, 20, seed=1)
+    qc = q.QCircuit(c)
+    s = q.State(32, "c64").init_zero()
+    res = {}
+    for label, mode, k in (("staged", q.FUSE_STAGED, 4), ("tc_bf16x3_k6", q.FUSE_TC, 6)):
+        p = q.Plan(qc, kmax=k, mode=mode)
+        ms, prof = ev_time(lambda: s.run_fused(p), 1, 1, profile=True)
+        res[label] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3), "sweeps": p.info()["sweeps"],
+                      "roofline": roofline_of(prof, peak, peak_src, 2070.0)}
+    out["variational32_c64"] = res
+    del s
+    torch.cuda.empty_cache()
+    # batch of 4096 small circuits, one persistent launch replayed from a CUDA graph
+    circs = inputs.batch_circuits(4096, seed=2024)
+    b = q.Batch(circs)
+    cfg = b.autotune(reps=1)
+    o = torch.zeros(len(circs), dtype=torch.float64, device="cuda")
+    b.run(o)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run(o)
+    ms, _ = ev_time(g.replay, 3, 5)
+    upd = sum((1 << cc.n) * len(cc.gates) for cc in circs)
+    out["batch4096_c64"] = {"s_per_batch": ms / 1e3, "circuits_per_s": len(circs) / (ms / 1e3),
+                            "amp_gate_updates_per_s": upd / (ms / 1e3), "config": cfg,
+                            "workload": "4096 variational circuits, n ~ U{12..20}, 4..12 layers, <sum Z_i Z_i+1>"}
+    del b, g
+    torch.cuda.empty_cache()
+    # adjoint gradient, 24 qubits, 10 layers (480 parameters)
+    c = inputs.variational(24, 10, seed=5)
+    qc = q.QCircuit(c)
+    ham = inputs.tfim(24)
+    th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(4, c.nparams))
+    q.adjoint_grad(qc, ham, th[:1], "c64")
+    t0 = time.perf_counter()
+    q.adjoint_grad(qc, ham, th, "c64")
+    dt = (time.perf_counter() - t0) / len(th)
+    out["adjoint24_c64"] = {"s_per_parameter_set": dt, "gradients_per_s": c.nparams / dt,
+                            "workload": "24 qubits, 10 layers RY/RZ + CZ ladder, 480 parameters, "
+                                        "H = sum(Z_i Z_i+1 + 0.5 X_i), 4 parameter sets"}
+    return out
 
 
 def main():
@@ -378,6 +506,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--quick", action="store_true",
                     help="headline mode only (no other modes, end-to-end or CPU legs): for profiling runs")
     args = ap.parse_args()

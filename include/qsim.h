@@ -283,12 +283,14 @@ QSIM_API int qsim_batch_autotune(qsim_batch *b, void *cuda_stream, int reps, int
 /* Launch accounting for every kernel the library starts.  When enabled, each
  * launch is bracketed by CUDA events on its own stream; qsim_profile_get
  * synchronises those events and reports, per kernel name, the launches, the
- * summed device time and the summed algorithmic bytes moved. */
+ * summed device time, the summed algorithmic HBM bytes and the summed useful
+ * floating-point operations (a complex multiply-add counts 8; tensor-core
+ * passes count the complex flops of the gate they apply, not the split). */
 QSIM_API int qsim_profile_enable(int on);
 QSIM_API int qsim_profile_reset(void);
 QSIM_API int qsim_profile_count(int *nkinds);
 QSIM_API int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total_ms,
-                     double *total_bytes);
+                     double *total_bytes, double *total_flops);
 /* Total kernel launches issued by the library since load (always counted). */
 QSIM_API uint64_t qsim_launch_count(void);
 

@@ -75,7 +75,7 @@ _SIGS = {
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),
-    "qsim_profile_get": ([I, P, P, P, P], I),
+    "qsim_profile_get": ([I, P, P, P, P, P], I),
     "qsim_launch_count": ([], U64),
 }
 
@@ -336,6 +336,28 @@ def adjoint_grad(circuit, ham: inputs.PauliSum, params: np.ndarray, dtype: str =
     return grads, en
 
 
+def adjoint_energy(circuit, ham: inputs.PauliSum, dtype: str = "c64"):
+    """A torch.autograd.Function computing <H> for a batch of parameter sets
+    (tensor nsets x nparams, float64) whose backward returns the adjoint-method
+    gradients computed by the library in the same call."""
+    torch = _torch()
+    qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+
+    class _AdjointEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta):
+            grads, en = adjoint_grad(qc, ham, theta.detach().cpu().numpy(), dtype)
+            ctx.save_for_backward(torch.from_numpy(grads).to(theta.device))
+            return torch.from_numpy(en).to(theta.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grads,) = ctx.saved_tensors
+            return gout[:, None] * grads
+
+    return _AdjointEnergy.apply
+
+
 # ------------------------------------------------------------------ batches
 class Batch:
     def __init__(self, circuits: Iterable[inputs.Circuit]):
@@ -379,10 +401,12 @@ def profile_read() -> dict:
     out = {}
     for i in range(n.value):
         name = ctypes.c_char_p(); l = ctypes.c_uint64(); ms = ctypes.c_double(); by = ctypes.c_double()
+        fl = ctypes.c_double()
         _check(lib().qsim_profile_get(i, ctypes.byref(name), ctypes.byref(l), ctypes.byref(ms),
-                                      ctypes.byref(by)))
+                                      ctypes.byref(by), ctypes.byref(fl)))
         if l.value:
-            out[name.value.decode()] = {"launches": l.value, "ms": ms.value, "bytes": by.value}
+            out[name.value.decode()] = {"launches": l.value, "ms": ms.value, "bytes": by.value,
+                                        "flops": fl.value}
     return out
 
 

@@ -1,9 +1,365 @@
 // Adjoint-method gradients (qsim_adjoint_grad).
+//
+// For E(theta) = <psi_L| H |psi_L> with psi_l = U_l psi_{l-1}, psi_0 = |0>, and
+// lambda_l = U_{l+1}^dag ... U_L^dag H psi_L, every parametrised rotation
+// U_l = exp(-i theta P / 2) contributes
+//     dE/dtheta = 2 Re <lambda_l| dU_l/dtheta psi_{l-1}> = Im <lambda_l| P |psi_l>
+// (dU/dtheta = (-i/2) P U).  One forward sweep builds psi_L, one pass forms
+// lambda = H psi_L, and one reverse sweep walks the gates from the last to the
+// first: at a rotation it accumulates Im<lambda|P|psi> (double, per block) and
+// un-applies U_l to both states in the same pass; any other gate is
+// un-applied to both states with the plain sweeps.  The paper differentiates
+// only through TensorFlow's automatic differentiation (Sec. 2); this is the
+// GPU-native replacement.
+#include <cstring>
+
 #include "internal.h"
 #include "plan.h"
 
+namespace qsim {
+namespace {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+constexpr int ADJ_BLOCKS_PER_SM = 4;
+constexpr int HAPPLY_GROUPS = 64;
+constexpr int HAPPLY_TERMS = 128;
+
+int sm_count_a() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 148;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = 0;
+    if (w == 0) {
+        v = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+template <typename C> struct M2 {
+    C m00, m01, m10, m11;
+};
+
+template <typename C> __device__ __forceinline__ C mul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C add(C a, C b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+
+// One rotation of the reverse sweep: g += Im(<lambda|P|psi>) over the pairs
+// of qubit q (partials per block), then psi <- U^dag psi, lambda <- U^dag lambda.
+// P: 0 = X, 1 = Y, 2 = Z.
+template <typename C>
+__global__ void __launch_bounds__(256) k_adj_rot(C *__restrict__ psi, C *__restrict__ lam, uint64_t npairs, int q,
+                                                 int P, M2<C> u, double *__restrict__ partial) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t bit = uint64_t(1) << q;
+    double acc = 0;
+    for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < npairs; g += stride) {
+        const uint64_t low = g & (bit - 1);
+        const uint64_t i0 = ((g ^ low) << 1) | low, i1 = i0 | bit;
+        const C a0 = psi[i0], a1 = psi[i1], l0 = lam[i0], l1 = lam[i1];
+        C p0, p1;
+        if (P == 0) {
+            p0 = a1;
+            p1 = a0;
+        } else if (P == 1) {  // Y|0> = i|1>, Y|1> = -i|0>:  (P psi)_0 = -i a1, (P psi)_1 = i a0
+            p0.x = a1.y;
+            p0.y = -a1.x;
+            p1.x = -a0.y;
+            p1.y = a0.x;
+        } else {
+            p0 = a0;
+            p1.x = -a1.x;
+            p1.y = -a1.y;
+        }
+        // Im(conj(l) p) = l.x p.y - l.y p.x
+        acc += double(l0.x) * p0.y - double(l0.y) * p0.x + double(l1.x) * p1.y - double(l1.y) * p1.x;
+        psi[i0] = add(mul(u.m00, a0), mul(u.m01, a1));
+        psi[i1] = add(mul(u.m10, a0), mul(u.m11, a1));
+        lam[i0] = add(mul(u.m00, l0), mul(u.m01, l1));
+        lam[i1] = add(mul(u.m10, l0), mul(u.m11, l1));
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// lambda[y] = sum_groups f_g(y ^ X_g) psi[y ^ X_g],
+// f_g(x) = sum_{t in g} c_t (-1)^{popcount(x & Z_t)},  c_t = coeff_t i^{#Y_t}
+struct HParams {
+    int ngroups;
+    uint64_t X[HAPPLY_GROUPS];
+    int t0[HAPPLY_GROUPS + 1];
+    uint64_t Z[HAPPLY_TERMS];
+    double cr[HAPPLY_TERMS], ci[HAPPLY_TERMS];
+};
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__restrict__ lam, uint64_t N,
+                                                const __grid_constant__ HParams h) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
+        double sr = 0, si = 0;
+        for (int g = 0; g < h.ngroups; ++g) {
+            const uint64_t x = y ^ h.X[g];
+            const C a = psi[x];
+            double fr = 0, fi = 0;
+            for (int t = h.t0[g]; t < h.t0[g + 1]; ++t) {
+                const double s = (__popcll(x & h.Z[t]) & 1) ? -1.0 : 1.0;
+                fr += s * h.cr[t];
+                fi += s * h.ci[t];
+            }
+            sr += fr * a.x - fi * a.y;
+            si += fr * a.y + fi * a.x;
+        }
+        C o;
+        o.x = sr;
+        o.y = si;
+        lam[y] = o;
+    }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_dot_re(const C *__restrict__ a, const C *__restrict__ b, uint64_t N,
+                                                double *__restrict__ partial) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    double acc = 0;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+        acc += double(a[i].x) * b[i].x + double(a[i].y) * b[i].y;
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// out[r] = sum of row r of partial (rows of `cols` entries), fixed order
+__global__ void k_rows(const double *__restrict__ partial, int rows, int cols, double *__restrict__ out) {
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        double acc = 0;
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) acc += partial[size_t(r) * cols + c];
+        acc = block_sum(acc);
+        if (threadIdx.x == 0) out[r] = acc;
+    }
+}
+
+struct AdjGate {
+    bool param = false;
+    int P = 0;       // generator for rotations
+    int q = 0;
+    int pindex = -1;
+    Op fwd, inv;     // forward and inverse sweeps (non-parametrised gates)
+    std::vector<cd> mfwd;
+};
+
+int rotation_matrix(int kind, double th, std::vector<cd> &m) { return gate_matrix(kind, 1, &th, nullptr, m); }
+
+template <typename R>
+int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HParams &hp, double *grads,
+              double *energies, cudaStream_t st) {
+    using C = typename CT<R>::T;
+    const int n = c.n;
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = sm_count_a() * ADJ_BLOCKS_PER_SM;
+    int nrot = 0;
+    std::vector<int> rot_of_gate(c.gates.size(), -1);
+    for (size_t i = 0; i < c.gates.size(); ++i) {
+        const GateRec &g = c.gates[i];
+        if (g.pindex < 0) continue;
+        if (g.nc != 0 || g.k != 1) return set_error(QSIM_EUNSUPPORTED, "trainable rotations must be uncontrolled 1-qubit gates");
+        rot_of_gate[i] = nrot++;
+    }
+    // device buffers: psi, lambda, one row of partials per rotation, reductions
+    C *psi = nullptr, *lam = nullptr;
+    double *partial = nullptr, *rows = nullptr;
+    const size_t prow = size_t(blocks);
+    cudaError_t e = cudaMalloc(&psi, N * sizeof(C));
+    if (e == cudaSuccess) e = cudaMalloc(&lam, N * sizeof(C));
+    if (e == cudaSuccess) e = cudaMalloc(&partial, (size_t(nrot) + 1) * prow * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    struct Guard {
+        void *p[4];
+        ~Guard() {
+            for (void *x : p)
+                if (x) cudaFree(x);
+        }
+    } guard{{psi, lam, partial, rows}};
+    if (e != cudaSuccess) return cuda_error(e, "adjoint buffers");
+    std::vector<double> host_rows(size_t(nrot) + 1);
+    std::vector<void *> mats;  // dense k >= 2 matrices (uploaded per set)
+    for (int set = 0; set < nsets; ++set) {
+        const double *th = params + size_t(set) * size_t(c.nparams);
+        // forward and inverse ops with this set's angles
+        std::vector<AdjGate> gs(c.gates.size());
+        std::vector<unsigned char> matbuf;
+        std::vector<size_t> moff_f(c.gates.size(), size_t(-1)), moff_i(c.gates.size(), size_t(-1));
+        const size_t eb = sizeof(C);
+        auto stash = [&](const Op &op) -> size_t {
+            if (op.type != Op::DENSE || op.k < 2) return size_t(-1);
+            const size_t d = size_t(1) << op.k, off = matbuf.size();
+            matbuf.resize(off + d * d * eb);
+            for (size_t i = 0; i < d * d; ++i) {
+                R v[2] = {R(op.m[i].real()), R(op.m[i].imag())};
+                memcpy(&matbuf[off + i * eb], v, eb);
+            }
+            return off;
+        };
+        for (size_t i = 0; i < c.gates.size(); ++i) {
+            const GateRec &g = c.gates[i];
+            AdjGate &a = gs[i];
+            std::vector<cd> m = g.m;
+            if (g.pindex >= 0) {
+                QSIM_TRY(rotation_matrix(g.kind, th[g.pindex], m));
+                a.param = true;
+                a.P = g.kind == QSIM_GATE_RX ? 0 : g.kind == QSIM_GATE_RY ? 1 : 2;
+                a.q = g.targets[0];
+                a.pindex = g.pindex;
+            }
+            a.mfwd = m;
+            QSIM_TRY(classify(m, g.targets, g.k, g.controls, g.nc, a.fwd));
+            const size_t d = size_t(1) << g.k;
+            std::vector<cd> mi(d * d);
+            for (size_t r = 0; r < d; ++r)
+                for (size_t col = 0; col < d; ++col) mi[col * d + r] = std::conj(m[r * d + col]);
+            if (a.param) a.mfwd = mi;  // the reverse sweep needs U^dag
+            QSIM_TRY(classify(mi, g.targets, g.k, g.controls, g.nc, a.inv));
+            moff_f[i] = stash(a.fwd);
+            moff_i[i] = stash(a.inv);
+        }
+        void *dmats = nullptr;
+        if (!matbuf.empty()) {
+            QSIM_CUDA_TRY(cudaMalloc(&dmats, matbuf.size()), "adjoint matrices");
+            QSIM_CUDA_TRY(cudaMemcpyAsync(dmats, matbuf.data(), matbuf.size(), cudaMemcpyHostToDevice, st),
+                          "adjoint matrix upload");
+            mats.push_back(dmats);
+        }
+        auto mptr = [&](size_t off) -> void * {
+            return off == size_t(-1) ? nullptr : static_cast<char *>(dmats) + off;
+        };
+        // forward sweep from |0>
+        QSIM_TRY(launch_init(psi, n, sizeof(R) == 4 ? QSIM_C64 : QSIM_C128, 0, st));
+        const int dtype = sizeof(R) == 4 ? QSIM_C64 : QSIM_C128;
+        for (size_t i = 0; i < gs.size(); ++i)
+            QSIM_TRY(launch_op(psi, n, dtype, gs[i].fwd, st, mptr(moff_f[i])));
+        // lambda = H psi, energy = Re <psi|lambda>
+        {
+            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(C) * (hp.ngroups + 1));
+            k_happly<C><<<blocks, 256, 0, st>>>(psi, lam, N, hp);
+            QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+        }
+        double *prow_e = partial + size_t(nrot) * prow;
+        {
+            LaunchScope ls(K_REDUCE, st, 2.0 * double(N) * sizeof(C));
+            k_dot_re<C><<<blocks, 256, 0, st>>>(psi, lam, N, prow_e);
+            QSIM_CUDA_TRY(cudaGetLastError(), "energy launch");
+        }
+        // reverse sweep
+        for (size_t ii = gs.size(); ii-- > 0;) {
+            const AdjGate &a = gs[ii];
+            if (a.param) {
+                M2<C> u;
+                auto tc = [](const cd &z) {
+                    C r;
+                    r.x = R(z.real());
+                    r.y = R(z.imag());
+                    return r;
+                };
+                u.m00 = tc(a.mfwd[0]);
+                u.m01 = tc(a.mfwd[1]);
+                u.m10 = tc(a.mfwd[2]);
+                u.m11 = tc(a.mfwd[3]);
+                LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(C));
+                k_adj_rot<C><<<blocks, 256, 0, st>>>(psi, lam, N / 2, a.q, a.P, u,
+                                                     partial + size_t(rot_of_gate[ii]) * prow);
+                QSIM_CUDA_TRY(cudaGetLastError(), "adjoint step launch");
+            } else {
+                QSIM_TRY(launch_op(psi, n, dtype, a.inv, st, mptr(moff_i[ii])));
+                QSIM_TRY(launch_op(lam, n, dtype, a.inv, st, mptr(moff_i[ii])));
+            }
+        }
+        {
+            LaunchScope ls(K_REDUCE, st, double(nrot + 1) * prow * 8.0);
+            k_rows<<<std::min(nrot + 1, 1024), 256, 0, st>>>(partial, nrot + 1, int(prow), rows);
+            QSIM_CUDA_TRY(cudaGetLastError(), "adjoint reduce launch");
+        }
+        QSIM_CUDA_TRY(cudaMemcpyAsync(host_rows.data(), rows, host_rows.size() * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st),
+                      "adjoint result copy");
+        QSIM_CUDA_TRY(cudaStreamSynchronize(st), "adjoint sync");
+        for (void *m : mats) cudaFree(m);
+        mats.clear();
+        double *gset = grads + size_t(set) * size_t(c.nparams);
+        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
+        for (size_t i = 0; i < c.gates.size(); ++i)
+            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += host_rows[rot_of_gate[i]];
+        if (energies) energies[set] = host_rows[nrot];
+    }
+    return QSIM_OK;
+}
+
+}  // namespace
+}  // namespace qsim
+
 using namespace qsim;
-extern "C" int qsim_adjoint_grad(const qsim_circuit *, int, int, const double *, int, const uint64_t *,
-                                 const uint64_t *, const double *, double *, double *, void *) {
-    return set_error(QSIM_EUNSUPPORTED, "adjoint gradient not built yet");
+
+extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, const double *params, int nterms,
+                                 const uint64_t *xmask, const uint64_t *zmask, const double *coeff, double *grads,
+                                 double *energies, void *cuda_stream) {
+    if (!c || !grads || nsets < 1 || (c->nparams > 0 && !params)) return set_error(QSIM_EINVAL, "bad arguments");
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) return set_error(QSIM_EINVAL, "bad dtype");
+    if (nterms < 1 || !xmask || !zmask || !coeff) return set_error(QSIM_EINVAL, "empty Hamiltonian");
+    const uint64_t full = (uint64_t(1) << c->n) - 1;
+    HParams hp;
+    memset(&hp, 0, sizeof hp);
+    std::vector<bool> done(nterms, false);
+    int nt = 0;
+    for (int t0 = 0; t0 < nterms; ++t0) {
+        if (done[t0]) continue;
+        if ((xmask[t0] | zmask[t0]) & ~full) return set_error(QSIM_EINVAL, "term %d acts outside the state", t0);
+        if (hp.ngroups >= HAPPLY_GROUPS) return set_error(QSIM_EUNSUPPORTED, "more than %d distinct X masks", HAPPLY_GROUPS);
+        hp.X[hp.ngroups] = xmask[t0];
+        hp.t0[hp.ngroups] = nt;
+        for (int t = t0; t < nterms; ++t) {
+            if (done[t] || xmask[t] != xmask[t0]) continue;
+            if (nt >= HAPPLY_TERMS) return set_error(QSIM_EUNSUPPORTED, "more than %d Pauli terms", HAPPLY_TERMS);
+            done[t] = true;
+            const int ny = __builtin_popcountll(xmask[t] & zmask[t]);
+            const double re[4] = {1, 0, -1, 0}, im[4] = {0, 1, 0, -1};
+            hp.Z[nt] = zmask[t];
+            hp.cr[nt] = coeff[t] * re[ny & 3];
+            hp.ci[nt] = coeff[t] * im[ny & 3];
+            ++nt;
+        }
+        ++hp.ngroups;
+        hp.t0[hp.ngroups] = nt;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return dtype == QSIM_C64 ? adjoint_t<float>(*c, nsets, params, hp, grads, energies, st)
+                             : adjoint_t<double>(*c, nsets, params, hp, grads, energies, st);
 }

@@ -45,7 +45,7 @@ namespace {
 struct ProfSlot {
     int kind;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, flops;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -55,6 +55,7 @@ std::atomic<uint64_t> g_launches{0};
 uint64_t g_kind_launches[K_NUM_KINDS];
 double g_kind_ms[K_NUM_KINDS];
 double g_kind_bytes[K_NUM_KINDS];
+double g_kind_flops[K_NUM_KINDS];
 
 int prof_collect() {
     // caller holds g_prof_mu
@@ -66,13 +67,14 @@ int prof_collect() {
         g_kind_launches[s.kind] += 1;
         g_kind_ms[s.kind] += ms;
         g_kind_bytes[s.kind] += s.bytes;
+        g_kind_flops[s.kind] += s.flops;
     }
     g_used = 0;
     return QSIM_OK;
 }
 }  // namespace
 
-LaunchScope::LaunchScope(int kind_, cudaStream_t stream_, double bytes)
+LaunchScope::LaunchScope(int kind_, cudaStream_t stream_, double bytes, double flops)
     : kind(kind_), stream(stream_), slot(-1) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_prof_on) return;
@@ -85,6 +87,7 @@ LaunchScope::LaunchScope(int kind_, cudaStream_t stream_, double bytes)
     slot = int(g_used++);
     g_slots[slot].kind = kind;
     g_slots[slot].bytes = bytes;
+    g_slots[slot].flops = flops;
     cudaEventRecord(g_slots[slot].a, stream);
 }
 
@@ -627,6 +630,7 @@ int qsim_profile_reset(void) {
         g_kind_launches[i] = 0;
         g_kind_ms[i] = 0;
         g_kind_bytes[i] = 0;
+        g_kind_flops[i] = 0;
     }
     return QSIM_OK;
 }
@@ -637,7 +641,8 @@ int qsim_profile_count(int *nkinds) {
     return QSIM_OK;
 }
 
-int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total_ms, double *total_bytes) {
+int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total_ms, double *total_bytes,
+                     double *total_flops) {
     if (i < 0 || i >= K_NUM_KINDS) return set_error(QSIM_EINVAL, "kind index %d", i);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     QSIM_TRY(prof_collect());
@@ -645,6 +650,7 @@ int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total
     if (launches) *launches = g_kind_launches[i];
     if (total_ms) *total_ms = g_kind_ms[i];
     if (total_bytes) *total_bytes = g_kind_bytes[i];
+    if (total_flops) *total_flops = g_kind_flops[i];
     return QSIM_OK;
 }
 

@@ -56,7 +56,8 @@ const char *kernel_name(int kind);
 // RAII bracket around one launch: counts it and, when profiling is on,
 // records CUDA events on `stream` before and after.
 struct LaunchScope {
-    LaunchScope(int kind, cudaStream_t stream, double bytes);
+    // bytes: algorithmic HBM bytes of the launch; flops: useful arithmetic
+    LaunchScope(int kind, cudaStream_t stream, double bytes, double flops = 0.0);
     ~LaunchScope();
     int kind;
     cudaStream_t stream;

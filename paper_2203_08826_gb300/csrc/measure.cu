@@ -228,14 +228,26 @@ int launch_norm2(const void *psi, int n, int dtype, double *partials, double *re
 constexpr int EXP_TERMS = 64;
 struct ExpParams {
     uint64_t X;
-    int h;  // highest set bit of X, -1 for X == 0
+    int h;        // highest set bit of X, -1 for X == 0
     int nt;
+    int uniform;  // every term of the pass has the same coefficient (ur, ui)
+    double ur, ui;
     uint64_t z[EXP_TERMS];
     double cr[EXP_TERMS];
     double ci[EXP_TERMS];
 };
 
+// f(y) = sum_t c_t (-1)^{popcount(y & z_t)}.  With one shared coefficient the
+// signs are counted in integers: f = c (nt - 2 * #odd).
 __device__ __forceinline__ void f_of(uint64_t y, const ExpParams &p, double &fr, double &fi) {
+    if (p.uniform) {
+        int odd = 0;
+        for (int t = 0; t < p.nt; ++t) odd += __popcll(y & p.z[t]) & 1;
+        const double s = double(p.nt - 2 * odd);
+        fr = s * p.ur;
+        fi = s * p.ui;
+        return;
+    }
     fr = 0;
     fi = 0;
     for (int t = 0; t < p.nt; ++t) {
@@ -299,6 +311,11 @@ int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t 
             ++p.nt;
         }
         const uint64_t count = p.h < 0 ? N : N / 2;
+        p.uniform = 1;
+        p.ur = p.cr[0];
+        p.ui = p.ci[0];
+        for (int t = 1; t < p.nt; ++t)
+            if (p.cr[t] != p.ur || p.ci[t] != p.ui) p.uniform = 0;
         {
             LaunchScope ls(K_EXPECT, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
             if (dtype == QSIM_C64)
@@ -335,10 +352,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 constexpr int CHUNK = 2048;  // amplitudes per first-level CDF entry
 
+// floor(p * 2^62) for 0 < p < 1, read off the binary representation: with
+// p = m 2^(e-52) (m the 53-bit significand) the weight is m shifted by e + 10.
 __device__ __forceinline__ uint64_t weight_of(double p) {
     if (!(p > 0.0)) return 0;
     if (p >= 1.0) return uint64_t(1) << 62;
-    return uint64_t(p * 4611686018427387904.0);  // floor(p * 2^62); the scaling is exact
+    const uint64_t bits = uint64_t(__double_as_longlong(p));
+    const int ex = int((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;  // subnormal: far below 2^-62
+    const uint64_t m = (bits & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
+    const int sh = ex - 1023 + 10;  // <= 9 because p < 1
+    return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0);
 }
 
 template <int SRC>

@@ -362,6 +362,7 @@ struct StagedPlan {
         std::vector<unsigned char> params;  // packed StageParams per tile stage
         std::vector<size_t> param_off;
     } dev[2];
+    std::vector<double> flops_per_amp;  // useful flops per amplitude of each stage
     ~StagedPlan() {
         for (Dev &d : dev)
             for (void *m : d.plain_mats)
@@ -380,7 +381,23 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
     p.staged = sp;
     // kmax selects the tile: 2^(9 + W) amplitudes with W = min(kmax, 4) warp qubits
     sp->W = std::min(std::min(p.kmax, MAX_WARP_BITS), n - LANE_BITS - REG_BITS);
-    return plan_stage_list(c, sp->W, true, sp->stages);
+    QSIM_TRY(plan_stage_list(c, sp->W, true, sp->stages));
+    // useful flops per amplitude: a complex multiply-add is 8 flops
+    for (const Stage &st : sp->stages) {
+        double f = 0;
+        if (st.plain) {
+            f = st.op.type == Op::DENSE ? 8.0 * double(1 << st.op.k) / double(1ull << st.op.c) : 0.0;
+        } else {
+            for (const StageOp &o : st.ops) {
+                const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
+                if (o.type == SOP_U1) f += 16.0 * frac;
+                else if (o.type == SOP_U2) f += 32.0 * frac;
+                else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
+            }
+        }
+        sp->flops_per_amp.push_back(f);
+    }
+    return QSIM_OK;
 }
 
 template <typename C> static void make_params(const Stage &st, StageParams<C> &prm) {
@@ -441,7 +458,7 @@ static int prepare_staged(qsim_plan &p, int dtype) {
 }
 
 template <typename R, int W>
-static int launch_stage_w(void *psi, int n, const StageParams<typename CT<R>::T> &prm, cudaStream_t s) {
+static int launch_stage_w(void *psi, int n, const StageParams<typename CT<R>::T> &prm, cudaStream_t s, double fpa) {
     using C = typename CT<R>::T;
     const int nt = LANE_BITS + REG_BITS + W;
     const uint64_t ntiles = uint64_t(1) << (n - nt);
@@ -452,22 +469,22 @@ static int launch_stage_w(void *psi, int n, const StageParams<typename CT<R>::T>
                       "stage smem attribute");
         attr_set = true;
     }
-    LaunchScope ls(K_STAGE, s, 2.0 * double(uint64_t(1) << n) * sizeof(C));
+    LaunchScope ls(K_STAGE, s, 2.0 * double(uint64_t(1) << n) * sizeof(C), fpa * double(uint64_t(1) << n));
     k_stage<R, W><<<unsigned(ntiles), 32 << W, smem, s>>>(static_cast<C *>(psi), prm);
     QSIM_CUDA_TRY(cudaGetLastError(), "stage launch");
     return QSIM_OK;
 }
 
 template <typename R>
-static int launch_stage(void *psi, int n, int W, const void *params, cudaStream_t s) {
+static int launch_stage(void *psi, int n, int W, const void *params, cudaStream_t s, double fpa) {
     using C = typename CT<R>::T;
     const StageParams<C> &prm = *static_cast<const StageParams<C> *>(params);
     switch (W) {
-        case 0: return launch_stage_w<R, 0>(psi, n, prm, s);
-        case 1: return launch_stage_w<R, 1>(psi, n, prm, s);
-        case 2: return launch_stage_w<R, 2>(psi, n, prm, s);
-        case 3: return launch_stage_w<R, 3>(psi, n, prm, s);
-        default: return launch_stage_w<R, 4>(psi, n, prm, s);
+        case 0: return launch_stage_w<R, 0>(psi, n, prm, s, fpa);
+        case 1: return launch_stage_w<R, 1>(psi, n, prm, s, fpa);
+        case 2: return launch_stage_w<R, 2>(psi, n, prm, s, fpa);
+        case 3: return launch_stage_w<R, 3>(psi, n, prm, s, fpa);
+        default: return launch_stage_w<R, 4>(psi, n, prm, s, fpa);
     }
 }
 
@@ -484,9 +501,9 @@ int run_staged(qsim_state *s, qsim_plan &p) {
         }
         const void *prm = &d.params[d.param_off[i]];
         if (s->dtype == QSIM_C64)
-            QSIM_TRY(launch_stage<float>(s->amps, s->n, sp.W, prm, s->stream));
+            QSIM_TRY(launch_stage<float>(s->amps, s->n, sp.W, prm, s->stream, sp.flops_per_amp[i]));
         else
-            QSIM_TRY(launch_stage<double>(s->amps, s->n, sp.W, prm, s->stream));
+            QSIM_TRY(launch_stage<double>(s->amps, s->n, sp.W, prm, s->stream, sp.flops_per_amp[i]));
     }
     return QSIM_OK;
 }

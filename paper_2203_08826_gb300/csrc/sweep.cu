@@ -234,7 +234,7 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 Mat2<R> m{to_c<R>(op.m[0]), to_c<R>(op.m[1]), to_c<R>(op.m[2]), to_c<R>(op.m[3])};
                 constexpr int PER = 4, T = 256;
                 const uint64_t blocks = (ngroups + T * PER - 1) / (T * PER);
-                LaunchScope ls(K_DENSE1, st, bytes);
+                LaunchScope ls(K_DENSE1, st, bytes, 16.0 * double(ngroups << 1));
                 k_dense1<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, ngroups, map,
                                                                   uint64_t(1) << op.targets[0], m);
             } else {
@@ -244,7 +244,7 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 const C *mat = static_cast<const C *>(mat_dev);
                 constexpr int GPB = 32;
                 const uint64_t blocks = (ngroups + GPB - 1) / GPB;
-                LaunchScope ls(K_DENSEK, st, bytes);
+                LaunchScope ls(K_DENSEK, st, bytes, 8.0 * double(1 << k) * double(ngroups << k));
                 switch (k) {
                     case 2: k_densek<R, 2, GPB><<<unsigned(blocks), 128, 0, st>>>(psi, ngroups, map, mat, offs); break;
                     case 3: k_densek<R, 3, GPB><<<unsigned(blocks), 256, 0, st>>>(psi, ngroups, map, mat, offs); break;
@@ -265,7 +265,7 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
             for (int j = 0; j < (1 << k); ++j) p.d[j] = to_c<R>(op.m[j]);
             constexpr int PER = 4, T = 256;
             const uint64_t blocks = (count + T * PER - 1) / (T * PER);
-            LaunchScope ls(K_DIAG, st, 2.0 * S * double(count));
+            LaunchScope ls(K_DIAG, st, 2.0 * S * double(count), 6.0 * double(count));
             k_diag<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, count, map, p);
             break;
         }

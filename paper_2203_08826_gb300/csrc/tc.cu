@@ -590,7 +590,9 @@ int launch_tc_k(const TcParams &prm, cudaStream_t st) {
     const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
     const uint64_t want = uint64_t(sm_count_tc()) * per_sm;
     const unsigned grid = unsigned(std::min<uint64_t>(want, prm.ntiles));
-    LaunchScope ls(K_TC_BLOCK, st, 2.0 * double(prm.ntiles) * TC_M * (2 << K) * 4.0);
+    // useful flops: a dense k-qubit block is 2^k complex multiply-adds per amplitude
+    LaunchScope ls(K_TC_BLOCK, st, 2.0 * double(prm.ntiles) * TC_M * (2 << K) * 4.0,
+                   8.0 * double(1 << K) * double(prm.ntiles) * TC_M * double(1 << K));
     k_tc_block<K, PREC><<<grid, TC_THREADS, smem, st>>>(prm);
     QSIM_CUDA_TRY(cudaGetLastError(), "tc launch");
     return QSIM_OK;

@@ -1,0 +1,93 @@
+"""GPU parity of the adjoint-method gradient against the oracle's
+parameter-shift gradients (exact for exp(-i theta P / 2)) and central finite
+differences, energies against the oracle, and the autograd wrapper."""
+import numpy as np
+import pytest
+
+from paper_2203_08826_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_08826_gb300 import build, binding
+    build.build()
+    return binding
+
+
+def mixed_ansatz(n, layers, seed):
+    """RX / RY / RZ rotations (all three generators) with CZ and H in between."""
+    rng = np.random.default_rng(seed)
+    gates, p = [], 0
+    for _ in range(layers):
+        for q_ in range(n):
+            name = ("rx", "ry", "rz")[int(rng.integers(3))]
+            gates.append(inputs.Gate(name, (q_,), (), (float(rng.uniform(0, 6.28)),), p)); p += 1
+        for i in range(0, n - 1, 2):
+            gates.append(inputs.Gate("cz", (i, i + 1)))
+        gates.append(inputs.Gate("h", (int(rng.integers(n)),)))
+    return inputs.Circuit(n, gates)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 2e-4)])
+def test_adjoint_matches_parameter_shift(q, orc, dtype, tol):
+    circ = mixed_ansatz(6, 3, seed=1)
+    ham = inputs.tfim(6)
+    rng = np.random.default_rng(2)
+    thetas = rng.uniform(0, 2 * np.pi, size=(3, circ.nparams))
+    grads, en = q.adjoint_grad(circ, ham, thetas, dtype)
+    for s in range(3):
+        want = orc.parameter_shift_gradient(circ, ham, thetas[s])
+        np.testing.assert_allclose(grads[s], want, atol=tol)
+        assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < tol
+    fd = orc.finite_difference_gradient(circ, ham, thetas[0], h=1e-4)
+    np.testing.assert_allclose(grads[0], fd, atol=max(tol, 1e-6))
+
+
+def test_adjoint_variational_12q_all_parameters(q, orc):
+    """The benchmark ansatz (RY/RZ + CZ ladder) at 12 qubits, 4 layers,
+    H = sum_i (Z_i Z_{i+1} + 0.5 X_i), complex128: all 96 gradients."""
+    circ = inputs.variational(12, 4, seed=3)
+    ham = inputs.tfim(12)
+    th = circ.params()
+    grads, en = q.adjoint_grad(circ, ham, th[None, :], "c128")
+    np.testing.assert_allclose(grads[0], orc.parameter_shift_gradient(circ, ham, th), atol=1e-10)
+    assert abs(en[0] - orc.energy(circ, ham, th)) < 1e-10
+
+
+def test_autograd_function(q, orc):
+    import torch
+    circ = inputs.variational(5, 2, seed=4)
+    ham = inputs.tfim(5)
+    f = q.adjoint_energy(circ, ham, "c128")
+    theta = torch.tensor(np.stack([circ.params(), circ.params() + 0.1]), dtype=torch.float64, requires_grad=True)
+    e = f(theta)
+    (2.0 * e[0] + 3.0 * e[1]).backward()
+    g0 = orc.parameter_shift_gradient(circ, ham, circ.params())
+    g1 = orc.parameter_shift_gradient(circ, ham, circ.params() + 0.1)
+    np.testing.assert_allclose(theta.grad.numpy(), np.stack([2 * g0, 3 * g1]), atol=1e-10)
+
+
+def test_adjoint_24q_config_properties(q):
+    """The 24-qubit, 10-layer ansatz of the gradient workload (480 parameters):
+    a few gradient entries against central differences of the library's own
+    energies (h = 1e-4, complex128), and complex64 against complex128."""
+    circ = inputs.variational(24, 10, seed=5)
+    ham = inputs.tfim(24)
+    th = circ.params()
+    g64, e64 = q.adjoint_grad(circ, ham, th[None, :], "c64")
+    g128, e128 = q.adjoint_grad(circ, ham, th[None, :], "c128")
+    assert abs(e64[0] - e128[0]) < 1e-4
+    np.testing.assert_allclose(g64[0], g128[0], atol=2e-3)
+    h = 1e-4
+    for p_ in (0, 237, 479):
+        tp, tm = th.copy(), th.copy()
+        tp[p_] += h
+        tm[p_] -= h
+        _, ep = q.adjoint_grad(circ, ham, tp[None, :], "c128")
+        _, em = q.adjoint_grad(circ, ham, tm[None, :], "c128")
+        assert abs((ep[0] - em[0]) / (2 * h) - g128[0, p_]) < 1e-6
