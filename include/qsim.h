@@ -231,11 +231,21 @@ QSIM_API int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots,
 QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
                                       uint64_t counter0, uint64_t *out_dev, void *cuda_stream);
 
+/* Measurement collapse (Sec. 2: the operator that collapses and re-normalises
+ * a state after a measurement): the outcome's m bits are read with
+ * qubits[0] as the most significant; P = sum of |psi(x)|^2 over the x whose
+ * listed bits spell the outcome (written to *prob_out if not NULL); those
+ * amplitudes are divided by sqrt(P) and all others set to 0.  Synchronous
+ * (reads P back); QSIM_EINVAL when P = 0 (the state is then left unchanged). */
+QSIM_API int qsim_collapse(qsim_state *s, const int *qubits, int m, uint64_t outcome, double *prob_out);
+
 /* Pauli expectation <psi| sum_t coeff[t] P_t |psi> with P_t given by bit masks
  * (bit q of xmask/zmask: X = (1,0), Y = (1,1), Z = (0,1) on qubit q):
  *   P|y> = i^{#Y} (-1)^{popcount(y & zmask)} |y ^ xmask>.
  * Terms sharing an xmask are evaluated in one pass; partial sums are
- * accumulated in double.  Host arrays of nterms entries; *out (host) receives
+ * accumulated in double (for a complex64 state and a diagonal pass with one
+ * real coefficient, |psi|^2 times the integer sign sum is formed in fp32 over
+ * 16 amplitudes per thread first).  Host arrays of nterms entries; *out (host) receives
  * the real part; synchronous.  (TFIM-type Hamiltonians, Sec. 3.3.) */
 QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *xmask,
                            const uint64_t *zmask, const double *coeff, double *out);

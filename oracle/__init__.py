@@ -258,6 +258,21 @@ def finite_difference_gradient(circuit, ham, theta: Sequence[float], h: float = 
     return grad
 
 
+def collapse(psi: np.ndarray, qubits: Sequence[int], outcome: int):
+    """Measurement collapse by definition: keep the amplitudes whose listed
+    bits (qubits[0] = most significant) spell `outcome`, renormalise.
+    Returns (new state, probability of the outcome)."""
+    m = len(qubits)
+    x = np.arange(psi.size)
+    spelled = np.zeros(psi.size, dtype=np.int64)
+    for q in qubits:
+        spelled = (spelled << 1) | ((x >> q) & 1)
+    keep = spelled == outcome
+    p = float(np.sum(np.abs(psi[keep]) ** 2))
+    out = np.where(keep, psi, 0).astype(np.complex128)
+    return out / np.sqrt(p), p
+
+
 # ---------------------------------------------------------------- sampling
 
 def philox4x32_10(counter: Sequence[int], key: Sequence[int]) -> np.ndarray:

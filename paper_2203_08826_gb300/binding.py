@@ -66,6 +66,7 @@ _SIGS = {
     "qsim_sample_probs": ([P, U64, U64, U64, U64, P, I, P], I),
     "qsim_sample_probs_static": ([P, U64, U64, U64, U64, P, P], I),
     "qsim_expectation_pauli": ([P, I, P, P, P, P], I),
+    "qsim_collapse": ([P, P, I, U64, P], I),
     "qsim_adjoint_grad": ([P, I, I, P, I, P, P, P, P, P, P], I),
     "qsim_batch_create": ([I, P, P], I),
     "qsim_batch_destroy": ([P], I),
@@ -305,6 +306,13 @@ class State:
         _check(lib().qsim_sample(self.handle, nshots, seed & (2**64 - 1), counter0 & (2**64 - 1),
                                  _p(host), 0))
         return host[:nshots]
+
+    def collapse(self, qubits: Sequence[int], outcome: int) -> float:
+        """Project on `outcome` of `qubits` (qubits[0] = MSB) and renormalise; returns P."""
+        q = _arr(qubits, np.int32)
+        p = ctypes.c_double()
+        _check(lib().qsim_collapse(self.handle, _p(q), len(q), outcome, ctypes.byref(p)))
+        return p.value
 
     def expectation(self, ham: inputs.PauliSum) -> float:
         xm, zm, c = _arr(ham.xmask, np.uint64), _arr(ham.zmask, np.uint64), _arr(ham.coeff, np.float64)

@@ -232,18 +232,31 @@ struct ExpParams {
     int nt;
     int uniform;  // every term of the pass has the same coefficient (ur, ui)
     double ur, ui;
+    // uniform 2-qubit Z parts: term (a, a + d) contributes bit a of (y ^ (y >> d)),
+    // so one popcount per distinct distance d counts the odd terms
+    int ndist;
+    int dist[EXP_TERMS];
+    uint64_t dmask[EXP_TERMS];
     uint64_t z[EXP_TERMS];
     double cr[EXP_TERMS];
     double ci[EXP_TERMS];
 };
 
+__device__ __forceinline__ int odd_terms(uint64_t y, const ExpParams &p) {
+    int odd = 0;
+    if (p.ndist > 0) {
+        for (int i = 0; i < p.ndist; ++i) odd += __popcll((y ^ (y >> p.dist[i])) & p.dmask[i]);
+    } else {
+        for (int t = 0; t < p.nt; ++t) odd += __popcll(y & p.z[t]) & 1;
+    }
+    return odd;
+}
+
 // f(y) = sum_t c_t (-1)^{popcount(y & z_t)}.  With one shared coefficient the
 // signs are counted in integers: f = c (nt - 2 * #odd).
 __device__ __forceinline__ void f_of(uint64_t y, const ExpParams &p, double &fr, double &fi) {
     if (p.uniform) {
-        int odd = 0;
-        for (int t = 0; t < p.nt; ++t) odd += __popcll(y & p.z[t]) & 1;
-        const double s = double(p.nt - 2 * odd);
+        const double s = double(p.nt - 2 * odd_terms(y, p));
         fr = s * p.ur;
         fi = s * p.ui;
         return;
@@ -255,6 +268,29 @@ __device__ __forceinline__ void f_of(uint64_t y, const ExpParams &p, double &fr,
         fr += s * p.cr[t];
         fi += s * p.ci[t];
     }
+}
+
+// Diagonal pass of a complex64 state with one real coefficient: |psi|^2 times
+// the integer sign sum is formed in fp32 for 16 amplitudes per thread (the
+// precision of the complex64 amplitudes themselves) and accumulated in double.
+__global__ void __launch_bounds__(256) k_expect_diag_c64(const float2 *__restrict__ psi, uint64_t N, ExpParams p,
+                                                         double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t g0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g0 < N; g0 += 16 * stride) {
+        float part = 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint64_t g = g0 + uint64_t(u) * stride;
+            if (g < N) {
+                const float2 a = psi[g];
+                part += (a.x * a.x + a.y * a.y) * float(p.nt - 2 * odd_terms(g, p));
+            }
+        }
+        acc += double(part);
+    }
+    acc = block_sum(acc * p.ur);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
 template <typename C>
@@ -316,9 +352,27 @@ int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t 
         p.ui = p.ci[0];
         for (int t = 1; t < p.nt; ++t)
             if (p.cr[t] != p.ur || p.ci[t] != p.ui) p.uniform = 0;
+        // two-bit Z parts grouped by distance (ZZ chains and couplings)
+        bool two_bit = p.uniform != 0;
+        for (int t = 0; t < p.nt && two_bit; ++t) two_bit = __builtin_popcountll(p.z[t]) == 2;
+        if (two_bit) {
+            for (int t = 0; t < p.nt; ++t) {
+                const int a = __builtin_ctzll(p.z[t]), b = 63 - __builtin_clzll(p.z[t]);
+                int i = 0;
+                while (i < p.ndist && p.dist[i] != b - a) ++i;
+                if (i == p.ndist) {
+                    p.dist[p.ndist] = b - a;
+                    p.dmask[p.ndist] = 0;
+                    ++p.ndist;
+                }
+                p.dmask[i] |= uint64_t(1) << a;
+            }
+        }
         {
             LaunchScope ls(K_EXPECT, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
-            if (dtype == QSIM_C64)
+            if (dtype == QSIM_C64 && p.h < 0 && p.uniform && p.ui == 0.0)
+                k_expect_diag_c64<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, p, partials);
+            else if (dtype == QSIM_C64)
                 k_expect<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), count, p, partials);
             else
                 k_expect<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), count, p, partials);
@@ -387,14 +441,17 @@ __global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ s
     const uint64_t c0 = uint64_t(blockIdx.x) * CHUNK;
     uint64_t w = 0;
     double pp = 0;
-    for (int i = threadIdx.x; i < CHUNK; i += blockDim.x) {
-        const uint64_t x = c0 + i;
+    float ppf = 0.f;  // the probability sum only guards against p summing above 1.5
+#pragma unroll
+    for (int i = 0; i < CHUNK / 256; ++i) {
+        const uint64_t x = c0 + uint64_t(i) * 256 + threadIdx.x;
         if (x < N) {
             const double p = src_prob<SRC>(src, x);
             w += weight_of(p);
-            pp += p > 0.0 ? p : 0.0;
+            ppf += p > 0.0 ? float(p) : 0.f;
         }
     }
+    pp = ppf;
     w = warp_sum_u64(w);
     pp = warp_sum(pp);
     if ((threadIdx.x & 31) == 0) {
@@ -596,5 +653,85 @@ extern "C" QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N
     QSIM_CUDA_TRY(cudaStreamSynchronize(st), "static sampler sync");
     if (!(hp <= 1.5) || total == 0)
         return set_error(QSIM_EINVAL, "probabilities must sum to a value in (0, 1.5] (got %g)", hp);
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ collapse
+// Measurement collapse (Sec. 2: the operator that collapses and
+// re-normalises a state): P = sum of |psi(x)|^2 over the x whose listed bits
+// spell the outcome; those amplitudes are divided by sqrt(P), the others set
+// to zero.
+namespace qsim {
+namespace {
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_outcome_prob(const C *__restrict__ psi, uint64_t N, uint64_t qmask,
+                                                      uint64_t omask, double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride)
+        if ((x & qmask) == omask) acc += double(psi[x].x) * psi[x].x + double(psi[x].y) * psi[x].y;
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_collapse(C *__restrict__ psi, uint64_t N, uint64_t qmask, uint64_t omask,
+                                                  const double *__restrict__ prob) {
+    const double inv = 1.0 / sqrt(*prob);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
+        C a = psi[x];
+        if ((x & qmask) == omask) {
+            a.x = a.x * inv;
+            a.y = a.y * inv;
+        } else {
+            a.x = 0;
+            a.y = 0;
+        }
+        psi[x] = a;
+    }
+}
+
+}  // namespace
+}  // namespace qsim
+
+extern "C" QSIM_API int qsim_collapse(qsim_state *s, const int *qubits, int m, uint64_t outcome, double *prob_out) {
+    using namespace qsim;
+    if (!s || (m > 0 && !qubits)) return set_error(QSIM_EINVAL, "NULL argument");
+    if (m < 1 || m > s->n) return set_error(QSIM_EINVAL, "m=%d outside 1..n", m);
+    if (outcome >> m) return set_error(QSIM_EINVAL, "outcome has more than %d bits", m);
+    uint64_t qmask = 0, omask = 0;
+    for (int i = 0; i < m; ++i) {
+        if (qubits[i] < 0 || qubits[i] >= s->n || (qmask >> qubits[i] & 1))
+            return set_error(QSIM_EINVAL, "bad or repeated qubit %d", qubits[i]);
+        qmask |= uint64_t(1) << qubits[i];
+        if ((outcome >> (m - 1 - i)) & 1) omask |= uint64_t(1) << qubits[i];  // qubits[0] = MSB
+    }
+    const int blocks = reduce_blocks();
+    QSIM_TRY(s->ensure_scratch((size_t(blocks) + 8) * sizeof(double)));
+    double *part = static_cast<double *>(s->scratch), *res = part + blocks;
+    const uint64_t N = s->size();
+    {
+        LaunchScope ls(K_REDUCE, s->stream, double(N) * s->amp_bytes());
+        if (s->dtype == QSIM_C64)
+            k_outcome_prob<<<blocks, 256, 0, s->stream>>>(static_cast<const float2 *>(s->amps), N, qmask, omask, part);
+        else
+            k_outcome_prob<<<blocks, 256, 0, s->stream>>>(static_cast<const double2 *>(s->amps), N, qmask, omask, part);
+        QSIM_CUDA_TRY(cudaGetLastError(), "collapse probability launch");
+        k_sum_partials<<<1, 256, 0, s->stream>>>(part, blocks, res, 0);
+        QSIM_CUDA_TRY(cudaGetLastError(), "collapse sum launch");
+    }
+    double p = 0;
+    QSIM_CUDA_TRY(cudaMemcpyAsync(&p, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream), "collapse copy");
+    QSIM_CUDA_TRY(cudaStreamSynchronize(s->stream), "collapse sync");
+    if (prob_out) *prob_out = p;
+    if (!(p > 0.0)) return set_error(QSIM_EINVAL, "the outcome has probability 0");
+    LaunchScope ls(K_REDUCE, s->stream, 2.0 * double(N) * s->amp_bytes());
+    if (s->dtype == QSIM_C64)
+        k_collapse<<<blocks, 256, 0, s->stream>>>(static_cast<float2 *>(s->amps), N, qmask, omask, res);
+    else
+        k_collapse<<<blocks, 256, 0, s->stream>>>(static_cast<double2 *>(s->amps), N, qmask, omask, res);
+    QSIM_CUDA_TRY(cudaGetLastError(), "collapse launch");
     return QSIM_OK;
 }

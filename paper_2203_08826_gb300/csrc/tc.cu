@@ -39,7 +39,7 @@ namespace qsim {
 namespace {
 
 constexpr int TC_M = 128;          // rows per tile (tcgen05 M)
-constexpr int TC_THREADS = 128;    // 4 warps: one TMEM lane quarter each
+constexpr int TC_THREADS = 256;    // 8 warps: each TMEM lane quarter is read by two warps
 constexpr int MAX_EPI = 48;        // epilogue diagonal ops per pass
 constexpr int MAX_EPI_POOL = 256;  // their complex entries
 constexpr unsigned long long WAIT_LIMIT = 1ull << 26;  // bounded mbarrier waits
@@ -121,6 +121,18 @@ template <> struct Elem<TC_TF32X3> {
     }
 };
 
+template <int K, int PREC>
+struct TcShape {
+    static constexpr int KR = 2 << K;                   // reals per row (GEMM K and N)
+    static constexpr int EB = Elem<PREC>::EB;
+    static constexpr int RAW = TC_M * KR * 4;           // bytes of one fp32 tile
+    static constexpr int OPND = TC_M * KR * EB;         // bytes of one A split
+    static constexpr int BOPND = KR * KR * EB;          // bytes of one B split
+    static constexpr int SMEM = RAW + 2 * OPND + 2 * BOPND + 1024 + 64;
+    static constexpr int TCOLS = KR < 32 ? 32 : KR;     // TMEM columns (power of 2 >= 32)
+    static constexpr int KSTEP = 32 / EB;               // K elements per MMA
+};
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
         uint32_t ok;
@@ -136,39 +148,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-template <int K, int PREC>
-struct TcShape {
-    static constexpr int KR = 2 << K;                   // reals per row (GEMM K and N)
-    static constexpr int EB = Elem<PREC>::EB;
-    static constexpr int OPND = TC_M * KR * EB;         // bytes of one A split
-    static constexpr int BOPND = KR * KR * EB;          // bytes of one B split
-    static constexpr int SMEM = 2 * OPND + 2 * BOPND + 1024 + 64;
-    static constexpr int TCOLS = KR < 32 ? 32 : KR;     // TMEM columns (power of 2 >= 32)
-    static constexpr int KSTEP = 32 / EB;               // K elements per MMA
-};
+// bulk copy global -> shared, completion counted in bytes on an mbarrier
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
 
+// Persistent CTA: while the tensor cores and the epilogue work on tile t, the
+// bulk copy of tile t + gridDim.x is already in flight.
 template <int K, int PREC>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__ TcParams p) {
     using S = TcShape<K, PREC>;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
-    // 1024-byte alignment for the swizzle atoms
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-    unsigned char *a_hi = sm;
+    unsigned char *a_hi = sm;                      // split operands (1024-aligned)
     unsigned char *a_lo = sm + S::OPND;
     unsigned char *b_hi = sm + 2 * S::OPND;
     unsigned char *b_lo = b_hi + S::BOPND;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(b_lo + S::BOPND);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    unsigned char *raw = b_lo + S::BOPND;          // fp32 tile landing buffer
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(raw + S::RAW);  // [0] MMA done, [1] tile loaded
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mb_mma = smem_u32(&mbar[0]), mb_load = smem_u32(&mbar[1]);
+    const uint32_t raw_s = smem_u32(raw);
 
-    // B (both splits) into shared memory; the host built the swizzled image
-    {
+    {  // B (both splits): the host built the swizzled image
         const uint4 *src = p.bimg;
         uint4 *dst = reinterpret_cast<uint4 *>(b_hi);
         for (int i = tid; i < 2 * S::BOPND / 16; i += TC_THREADS) dst[i] = src[i];
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_load));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -180,45 +193,62 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t mb = smem_u32(mbar);
-    uint32_t phase = 0;
-    bool failed = false;
+    uint32_t ph_mma = 0, ph_load = 0;
+    bool load_pending = false;
     constexpr uint32_t IDESC = tc_idesc<PREC>(S::KR, TC_M);
     const int n = p.n;
-    const uint64_t rows_total = uint64_t(1) << (n - K);
+    const size_t tile_bytes = size_t(S::RAW);
 
-    for (uint64_t tile = blockIdx.x; tile < p.ntiles && !failed; tile += gridDim.x) {
-        // ---- A: 128 rows of KR floats (contiguous) -> split -> swizzled smem
-        const float4 *src = reinterpret_cast<const float4 *>(p.in + tile * TC_M * (S::KR / 2));
-        constexpr int NV = TC_M * S::KR / 4;  // float4 per tile
+    uint64_t tile = blockIdx.x;
+    if (tile < p.ntiles && tid == 0) bulk_load(raw_s, reinterpret_cast<const char *>(p.in) + tile * tile_bytes, S::RAW, mb_load);
+    load_pending = tile < p.ntiles;
+    bool failed = false;
+    for (; tile < p.ntiles; tile += gridDim.x) {
+        // ---- tile landed?
+        if (!__syncthreads_and(mbar_wait(mb_load, ph_load))) {
+            failed = true;
+            break;
+        }
+        ph_load ^= 1;
+        load_pending = false;
+        // ---- split the fp32 tile into the swizzled K-major operands
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(raw);
+            constexpr int NV = TC_M * S::KR / 4;
 #pragma unroll 4
-        for (int i = tid; i < NV; i += TC_THREADS) {
-            const float4 v = src[i];
-            const int m = (i * 4) / S::KR, e = (i * 4) % S::KR;
-            if (PREC == TC_BF16X3) {
-                uint16_t h[4], l[4];
-                Elem<TC_BF16X3>::split(v.x, h[0], l[0]);
-                Elem<TC_BF16X3>::split(v.y, h[1], l[1]);
-                Elem<TC_BF16X3>::split(v.z, h[2], l[2]);
-                Elem<TC_BF16X3>::split(v.w, h[3], l[3]);
-                const uint32_t off = sw128_offset<2>(m, e, TC_M);  // 8 bytes, inside one 16-byte chunk
-                *reinterpret_cast<uint2 *>(a_hi + off) = make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
-                *reinterpret_cast<uint2 *>(a_lo + off) = make_uint2(l[0] | (uint32_t(l[1]) << 16), l[2] | (uint32_t(l[3]) << 16));
-            } else {
-                uint32_t h[4], l[4];
-                Elem<TC_TF32X3>::split(v.x, h[0], l[0]);
-                Elem<TC_TF32X3>::split(v.y, h[1], l[1]);
-                Elem<TC_TF32X3>::split(v.z, h[2], l[2]);
-                Elem<TC_TF32X3>::split(v.w, h[3], l[3]);
-                const uint32_t off = sw128_offset<4>(m, e, TC_M);  // one 16-byte chunk
-                *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            for (int i = tid; i < NV; i += TC_THREADS) {
+                const float4 v = src[i];
+                const int m = (i * 4) / S::KR, e = (i * 4) % S::KR;
+                if (PREC == TC_BF16X3) {
+                    uint16_t h[4], l[4];
+                    Elem<TC_BF16X3>::split(v.x, h[0], l[0]);
+                    Elem<TC_BF16X3>::split(v.y, h[1], l[1]);
+                    Elem<TC_BF16X3>::split(v.z, h[2], l[2]);
+                    Elem<TC_BF16X3>::split(v.w, h[3], l[3]);
+                    const uint32_t off = sw128_offset<2>(m, e, TC_M);
+                    *reinterpret_cast<uint2 *>(a_hi + off) = make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
+                    *reinterpret_cast<uint2 *>(a_lo + off) = make_uint2(l[0] | (uint32_t(l[1]) << 16), l[2] | (uint32_t(l[3]) << 16));
+                } else {
+                    uint32_t h[4], l[4];
+                    Elem<TC_TF32X3>::split(v.x, h[0], l[0]);
+                    Elem<TC_TF32X3>::split(v.y, h[1], l[1]);
+                    Elem<TC_TF32X3>::split(v.z, h[2], l[2]);
+                    Elem<TC_TF32X3>::split(v.w, h[3], l[3]);
+                    const uint32_t off = sw128_offset<4>(m, e, TC_M);
+                    *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
             }
         }
-        // generic-proxy writes must be visible to the tensor core (async proxy)
+        // generic-proxy writes -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
+            // the landing buffer is free again: fetch the next tile
+            const uint64_t next = tile + gridDim.x;
+            if (next < p.ntiles) {
+                bulk_load(raw_s, reinterpret_cast<const char *>(p.in) + next * tile_bytes, S::RAW, mb_load);
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
             constexpr int PER = 128 / S::EB;  // elements per 128-byte column block
@@ -246,27 +276,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__
                     acc = 1;
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma)
                          : "memory");
         }
+        load_pending = tile + gridDim.x < p.ntiles;
         __syncwarp();
-        // every thread waits with a bound; the CTA leaves together if any gave up
-        const bool ok = __syncthreads_and(mbar_wait(mb, phase)) != 0;
-        if (!ok) {
+        if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma))) {
             failed = true;
-            if (tid == 0) atomicExch(p.err, 1);
-            // wait (bounded) for the MMAs in flight before the TMEM is freed
-            mbar_wait(mb, phase);
+            mbar_wait(mb_mma, ph_mma);  // bounded: let the MMAs in flight drain
             break;
         }
-        phase ^= 1;
+        ph_mma ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: row m = TMEM lane m; store rotated
-        const int m = warp * 32 + lane;
-        const uint64_t R = tile * TC_M + m;  // row index (bits k.. of the current index)
-        const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
+        // ---- epilogue: TMEM lane = row; warps w and w + 4 split the columns
+        const int q4 = warp & 3, half = warp >> 2;
+        const int m = q4 * 32 + lane;
+        const uint64_t R = tile * TC_M + m;  // row index = bits K.. of the current index
+        const uint32_t trow = tmem + (uint32_t(q4 * 32) << 16);
+        constexpr int CPW = S::KR / 2;  // columns per warp half
 #pragma unroll 1
-        for (int c0 = 0; c0 < S::KR; c0 += 16) {
+        for (int c0 = half * CPW; c0 < (half + 1) * CPW; c0 += 16) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -278,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__
             for (int j = 0; j < 8; ++j) {
                 const int c = c0 / 2 + j;  // complex column = low K bits of the current index
                 float2 v = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-                const uint64_t x = (R << K) | uint64_t(c);  // current index of this element
+                const uint64_t x = (R << K) | uint64_t(c);
                 for (int e = 0; e < p.nepi; ++e) {
                     const EpiOp &op = p.epi[e];
                     if ((x & op.cmask) != op.cmask) continue;
@@ -295,10 +324,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__
                 p.out[(uint64_t(c) << (n - K)) | R] = v;
             }
         }
-        // the next tile overwrites the A buffers and the accumulator
+        // the next tile reuses the operands and the accumulator
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        (void)rows_total;
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(p.err, 1);
+        if (load_pending) mbar_wait(mb_load, ph_load);  // bounded: the copy in flight lands first
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -587,7 +619,7 @@ int launch_tc_k(const TcParams &prm, cudaStream_t st) {
                       "tc smem attribute");
         attr = true;
     }
-    const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
+    const int per_sm = std::max(1, std::min(2, (227 * 1024) / smem));
     const uint64_t want = uint64_t(sm_count_tc()) * per_sm;
     const unsigned grid = unsigned(std::min<uint64_t>(want, prm.ntiles));
     // useful flops: a dense k-qubit block is 2^k complex multiply-adds per amplitude

@@ -152,10 +152,12 @@ def test_pauli_expectation(q, orc, dtype):
     psi0 = inputs.gaussian_state(n, seed=21)
     s = new_state(q, n, dtype, psi0)
     amps = s.to_host().astype(np.complex128)
+    # complex64 diagonal passes form |psi|^2 x sign in fp32 over 16 amplitudes (relative 1e-6)
+    rtol = 1e-12 if dtype == "c128" else 1e-6
     for ham in (inputs.random_pauli_sum(n, 40, seed=22), inputs.tfim(n), inputs.zz_chain(n)):
         want = orc.expectation(amps, ham)
         got = s.expectation(ham)
-        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (got, want)
+        assert abs(got - want) <= rtol * max(1.0, abs(want)), (got, want)
 
 
 def test_expectation_many_terms_same_xmask(q, orc):
@@ -223,3 +225,19 @@ def test_argument_errors_do_not_launch(q):
     with pytest.raises(binding.QsimError):
         s.apply_matrix(np.eye(2), (1,), (1,))
     assert binding.launch_count() == before
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_collapse(q, orc, dtype):
+    n = 13
+    psi0 = inputs.gaussian_state(n, seed=41)
+    for qubits, outcome in (((0,), 1), ((12, 3), 2), ((7, 1, 9), 6)):
+        s = new_state(q, n, dtype, psi0)
+        p = s.collapse(qubits, outcome)
+        amps = psi0.astype(np.complex64).astype(np.complex128) if dtype == "c64" else psi0
+        want, pw = orc.collapse(amps, qubits, outcome)
+        assert abs(p - pw) <= (1e-13 if dtype == "c128" else 1e-7)
+        check(s.to_host(), want, dtype, f"collapse {qubits}={outcome}")
+    s = new_state(q, 4, dtype)
+    with pytest.raises(q.QsimError):
+        s.collapse((1,), 1)  # |0000>: outcome 1 has probability 0

@@ -1,0 +1,74 @@
+"""The multi-rank path on CPU: two gloo ranks split a batch of circuits by
+cost, simulate their share with the oracle, gather the results and take the
+maximum time -- the same host logic the benchmark runs with one GPU per rank."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2203_08826_gb300 import inputs, shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        circs = inputs.batch_circuits(12, seed=3, nmin=3, nmax=6, lmin=1, lmax=3)
+        costs = [(1 << c.n) * len(c.gates) for c in circs]
+        mine = shard.shard_by_cost(costs, rank, world)
+        local = [oracle.expectation(oracle.simulate(circs[i]), inputs.zz_chain(circs[i].n)) for i in mine]
+        allres = shard.gather_results(local, mine, len(circs))
+        tmax = shard.max_over_ranks(float(rank + 1))
+        q.put((rank, mine, allres.tolist(), tmax))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_split_helpers():
+    for n, w in ((10, 3), (2, 4), (4096, 8)):
+        ranges = [shard.shard_range(n, r, w) for r in range(w)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == n
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+        assert max(b - a for a, b in ranges) - min(b - a for a, b in ranges) <= 1
+    costs = np.random.default_rng(1).integers(1, 100, 50).tolist()
+    parts = [shard.shard_by_cost(costs, r, 4) for r in range(4)]
+    assert sorted(sum(parts, [])) == list(range(50))
+    loads = [sum(costs[i] for i in p) for p in parts]
+    assert max(loads) - min(loads) <= max(costs)
+    with pytest.raises(ValueError):
+        shard.shard_range(5, 3, 2)
+
+
+def test_two_gloo_ranks_split_and_gather():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=240) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res.sort()
+    import oracle
+    circs = inputs.batch_circuits(12, seed=3, nmin=3, nmax=6, lmin=1, lmax=3)
+    want = [oracle.expectation(oracle.simulate(c), inputs.zz_chain(c.n)) for c in circs]
+    mine0, mine1 = res[0][1], res[1][1]
+    assert sorted(mine0 + mine1) == list(range(12)) and not set(mine0) & set(mine1)
+    for r in res:
+        np.testing.assert_allclose(r[2], want, atol=1e-12)
+        assert r[3] == 2.0

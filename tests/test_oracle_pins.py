@@ -360,3 +360,19 @@ def test_sampler_rejects_bad_probabilities(orc):
         orc.sample(np.zeros(8), 10, seed=1)
     with pytest.raises(ValueError):
         orc.sample(np.full(8, 0.5), 10, seed=1)
+
+
+def test_collapse_of_ghz_and_bell(orc):
+    """GHZ: measuring any qubit gives 0 or 1 with probability 1/2 and leaves a
+    basis state; the marginal probability equals the oracle's marginal."""
+    n = 5
+    psi = orc.simulate(inputs.ghz(n))
+    out, p = orc.collapse(psi, (2,), 1)
+    assert abs(p - 0.5) < 1e-14
+    want = np.zeros(1 << n); want[-1] = 1
+    np.testing.assert_allclose(out, want, atol=1e-14)
+    st = inputs.gaussian_state(6, seed=3)
+    for qubits, o in (((0,), 1), ((4, 1), 2), ((5, 3, 0), 5)):
+        out, p = orc.collapse(st, qubits, o)
+        assert abs(p - orc.probabilities(st, qubits)[o]) < 1e-14
+        assert abs(np.linalg.norm(out) - 1) < 1e-14
