@@ -149,7 +149,8 @@ typedef struct qsim_plan qsim_plan;
 /* Fusion modes.
  *   QSIM_FUSE_GREEDY2  the paper's fusion (Sec. 3.2): greedily multiply 1- and
  *                      2-qubit gates that act on the same targets; one sweep
- *                      per fused gate.
+ *                      per fused gate (kmax = 1 merges only 1-qubit gates on
+ *                      the same qubit).
  *   QSIM_FUSE_STAGED   cache-blocked stages: each stage loads tiles of 2^m
  *                      amplitudes spanning a chosen qubit set into registers
  *                      (qubits 0..4 across the lanes of a warp, 4 qubits per
@@ -180,6 +181,15 @@ QSIM_API int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, do
 /* Human-readable summary of a plan (stages, tile qubits, op counts),
  * NUL-terminated and truncated to len bytes.  Host-only. */
 QSIM_API int qsim_plan_describe(const qsim_plan *p, char *buf, size_t len);
+/* Autotuner: builds the candidate plans (staged tiles of 2^12 and 2^13
+ * amplitudes; for complex64 also tensor-core blocks of 5 and 6 qubits, for
+ * complex128 one sweep per gate (greedy fusion with kmax = 1)), runs each on
+ * the scratch state `s` (its contents are overwritten) once to warm up and
+ * `reps` times under CUDA events on the state's stream, and returns the
+ * fastest plan in *out (the caller destroys it) with its mode, kmax and time
+ * per run.  Synchronous. */
+QSIM_API int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
+                                int *kmax_out, double *ms_out);
 /* Execute a plan on a state of the circuit's width and precision. */
 QSIM_API int qsim_apply_fused(qsim_state *s, const qsim_plan *p);
 

@@ -60,6 +60,7 @@ _SIGS = {
     "qsim_plan_block": ([P, I, P, P, P], I),
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
     "qsim_apply_fused": ([P, P], I),
+    "qsim_plan_autotune": ([P, P, I, P, P, P, P], I),
     "qsim_probabilities": ([P, P, I, P, I], I),
     "qsim_norm2": ([P, P], I),
     "qsim_sample": ([P, U64, U64, U64, P, I], I),
@@ -178,6 +179,19 @@ class Plan:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.qsim_plan_destroy(self.handle)
             self.handle = None
+
+    @classmethod
+    def autotune(cls, circuit, scratch_state: "State", reps: int = 1) -> "Plan":
+        """Fastest plan for `circuit`, timed on `scratch_state` (overwritten)."""
+        qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+        h = ctypes.c_void_p()
+        mode, kmax, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().qsim_plan_autotune(qc.handle, scratch_state.handle, reps, ctypes.byref(h),
+                                        ctypes.byref(mode), ctypes.byref(kmax), ctypes.byref(ms)))
+        self = cls.__new__(cls)
+        self.n, self.handle, self.mode = qc.n, h, mode.value
+        self.kmax, self.tuned_ms = kmax.value, ms.value
+        return self
 
     def info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

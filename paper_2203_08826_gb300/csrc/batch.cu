@@ -30,7 +30,7 @@ struct BCirc {
 };
 struct BStage {
     IndexMap outer;  // zeros at the tile qubits (tile id -> base index)
-    int op0, nops, phase_base, phase0, pool0, pad;
+    int op0, nops, phase_base, phase0, pool0, aux0;
 };
 
 struct BatchParams {
@@ -39,6 +39,7 @@ struct BatchParams {
     const StageOp *ops;
     const Phase *phases;
     const float2 *pool;
+    const uint64_t *aux;
     const int *order;
     int ncirc;
     int *counter;
@@ -51,9 +52,11 @@ struct GSrc {
     const StageOp *ops;
     const Phase *phases;
     const float2 *pl;
+    const uint64_t *ax;
     __device__ const StageOp &op(int o) const { return ops[o]; }
     __device__ const Phase &phase(int i) const { return phases[i]; }
     __device__ float2 pool(int i) const { return pl[i]; }
+    __device__ uint64_t aux(int i) const { return ax[i]; }
 };
 
 __device__ __forceinline__ double zz_chain(uint64_t x, int n) {
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
             uint64_t base = 0;
             for (int s = 0; s < bc.nstages; ++s) {
                 const BStage &S = bp.stages[bc.stage0 + s];
-                const GSrc src{bp.ops + S.op0, bp.phases + S.phase_base, bp.pool + S.pool0};
+                const GSrc src{bp.ops + S.op0, bp.phases + S.phase_base, bp.pool + S.pool0, bp.aux + S.aux0};
                 ph = S.phase0;
                 base = thread_base<W>(src.phase(ph), 0, lane, warp);
 #pragma unroll
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
             const uint64_t ntiles = uint64_t(1) << (n - TB);
             for (int s = 0; s < bc.nstages; ++s) {
                 const BStage &S = bp.stages[bc.stage0 + s];
-                const GSrc src{bp.ops + S.op0, bp.phases + S.phase_base, bp.pool + S.pool0};
+                const GSrc src{bp.ops + S.op0, bp.phases + S.phase_base, bp.pool + S.pool0, bp.aux + S.aux0};
                 for (uint64_t t = 0; t < ntiles; ++t) {
                     uint64_t tb = t;
                     for (int i = 0; i < S.outer.nins; ++i) {
@@ -175,18 +178,22 @@ struct Packed {
     std::vector<StageOp> ops;
     std::vector<Phase> phases;
     std::vector<float2> pool;
+    std::vector<uint64_t> aux;
     // device copies
     BCirc *d_circ = nullptr;
     BStage *d_stages = nullptr;
     StageOp *d_ops = nullptr;
     Phase *d_phases = nullptr;
     float2 *d_pool = nullptr;
+    uint64_t *d_aux = nullptr;
     void release() {
         cudaFree(d_circ);
         cudaFree(d_stages);
         cudaFree(d_ops);
         cudaFree(d_phases);
         cudaFree(d_pool);
+        cudaFree(d_aux);
+        d_aux = nullptr;
         d_circ = nullptr;
         d_stages = nullptr;
         d_ops = nullptr;
@@ -244,6 +251,7 @@ int pack(qsim_batch &b, int W) {
     pk.ops.clear();
     pk.phases.clear();
     pk.pool.clear();
+    pk.aux.clear();
     for (const qsim_circuit &c : b.circuits) {
         std::vector<stage::Stage> st;
         QSIM_TRY(stage::plan_stage_list(c, W, false, st));
@@ -261,6 +269,8 @@ int pack(qsim_batch &b, int W) {
             bs.phase_base = int(pk.phases.size());
             bs.phase0 = s.phase0;
             bs.pool0 = int(pk.pool.size());
+            bs.aux0 = int(pk.aux.size());
+            pk.aux.insert(pk.aux.end(), s.aux.begin(), s.aux.end());
             pk.ops.insert(pk.ops.end(), s.ops.begin(), s.ops.end());
             pk.phases.insert(pk.phases.end(), s.phases.begin(), s.phases.end());
             for (const cd &z : s.pool) pk.pool.push_back(make_float2(float(z.real()), float(z.imag())));
@@ -280,6 +290,7 @@ int pack(qsim_batch &b, int W) {
     QSIM_TRY(up(pk.ops, &pk.d_ops, "batch ops"));
     QSIM_TRY(up(pk.phases, &pk.d_phases, "batch phases"));
     QSIM_TRY(up(pk.pool, &pk.d_pool, "batch pool"));
+    QSIM_TRY(up(pk.aux, &pk.d_aux, "batch aux"));
     pk.ready = true;
     return QSIM_OK;
 }
@@ -323,6 +334,7 @@ int launch_batch(qsim_batch &b, double *out, cudaStream_t st, int ctas_per_sm) {
     bp.ops = pk.d_ops;
     bp.phases = pk.d_phases;
     bp.pool = pk.d_pool;
+    bp.aux = pk.d_aux;
     bp.order = b.d_order;
     bp.ncirc = int(b.circuits.size());
     bp.counter = b.d_counter;

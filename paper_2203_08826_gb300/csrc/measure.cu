@@ -432,42 +432,42 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
-// chunk sums of the integer weights (one CTA of 256 threads per chunk)
+// chunk sums of the integer weights: one warp per chunk of CHUNK
+// probabilities (lane l takes elements l, l + 32, ...), 8 chunks per CTA; the
+// probability sum only guards against inputs summing above 1.5, so it is
+// accumulated in fp32 per warp and once per CTA in double
 template <int SRC>
-__global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ src, uint64_t N,
+__global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ src, uint64_t N, uint64_t nchunks,
                                                       uint64_t *__restrict__ sums, double *__restrict__ psum) {
-    __shared__ uint64_t ws[8];
-    __shared__ double ps[8];
-    const uint64_t c0 = uint64_t(blockIdx.x) * CHUNK;
-    uint64_t w = 0;
-    double pp = 0;
-    float ppf = 0.f;  // the probability sum only guards against p summing above 1.5
-#pragma unroll
-    for (int i = 0; i < CHUNK / 256; ++i) {
-        const uint64_t x = c0 + uint64_t(i) * 256 + threadIdx.x;
-        if (x < N) {
-            const double p = src_prob<SRC>(src, x);
-            w += weight_of(p);
-            ppf += p > 0.0 ? float(p) : 0.f;
+    __shared__ float ps[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t c = uint64_t(blockIdx.x) * 8 + w;
+    uint64_t wsum = 0;
+    float pf = 0.f;
+    if (c < nchunks) {
+        const uint64_t x0 = c * CHUNK;
+#pragma unroll 8
+        for (int j = 0; j < CHUNK / 32; ++j) {
+            const uint64_t x = x0 + uint64_t(j) * 32 + lane;
+            if (x < N) {
+                const double p = src_prob<SRC>(src, x);
+                wsum += weight_of(p);
+                pf += p > 0.0 ? float(p) : 0.f;
+            }
         }
     }
-    pp = ppf;
-    w = warp_sum_u64(w);
-    pp = warp_sum(pp);
-    if ((threadIdx.x & 31) == 0) {
-        ws[threadIdx.x >> 5] = w;
-        ps[threadIdx.x >> 5] = pp;
+    wsum = warp_sum_u64(wsum);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pf += __shfl_xor_sync(0xffffffffu, pf, o);
+    if (lane == 0) {
+        if (c < nchunks) sums[c] = wsum;
+        ps[w] = pf;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint64_t t = 0;
-        double q = 0;
-        for (int i = 0; i < int(blockDim.x >> 5); ++i) {
-            t += ws[i];
-            q += ps[i];
-        }
-        sums[blockIdx.x] = t;
-        atomicAdd(psum, q);
+        double t = 0;
+        for (int i = 0; i < 8; ++i) t += ps[i];
+        atomicAdd(psum, t);
     }
 }
 
@@ -556,7 +556,7 @@ static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_
     QSIM_CUDA_TRY(cudaMemsetAsync(psum, 0, sizeof(double), st), "sampler zero");
     {
         LaunchScope ls(K_SAMPLE_CHUNK, st, double(N) * S);
-        k_sample_chunk<SRC><<<unsigned(nchunks), 256, 0, st>>>(src, N, scratch, psum);
+        k_sample_chunk<SRC><<<unsigned((nchunks + 7) / 8), 256, 0, st>>>(src, N, nchunks, scratch, psum);
         QSIM_CUDA_TRY(cudaGetLastError(), "sampler chunk launch");
     }
     {

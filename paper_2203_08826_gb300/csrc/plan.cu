@@ -87,7 +87,7 @@ int build_greedy2(const qsim_circuit &c, qsim_plan &p) {
             std::vector<int> uni = B.qubits;
             for (int q : gq)
                 if (std::find(uni.begin(), uni.end(), q) == uni.end()) uni.push_back(q);
-            if (uni.size() <= 2) {
+            if (int(uni.size()) <= std::min(p.kmax, 2)) {
                 // the qubits the gate adds must not have a block after F
                 bool ok = true;
                 for (int q : gq)
@@ -251,6 +251,68 @@ int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *mat
             matrix_out[2 * j] = B.m[j].real();
             matrix_out[2 * j + 1] = B.m[j].imag();
         }
+    return QSIM_OK;
+}
+
+int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
+                       int *kmax_out, double *ms_out) {
+    if (!c || !s || !out) return set_error(QSIM_EINVAL, "NULL argument");
+    if (c->n != s->n) return set_error(QSIM_EINVAL, "circuit has %d qubits, state %d", c->n, s->n);
+    *out = nullptr;
+    if (reps < 1) reps = 1;
+    struct Cand {
+        int mode, kmax;
+    };
+    // complex64: staged tiles and tensor-core blocks; complex128 (FP64-bound):
+    // staged tiles against one sweep per gate (greedy fusion limited to 1 qubit)
+    std::vector<Cand> cands = {{QSIM_FUSE_STAGED, 3}, {QSIM_FUSE_STAGED, 4}};
+    if (s->dtype == QSIM_C64) {
+        cands.push_back({QSIM_FUSE_TC, 6});
+        cands.push_back({QSIM_FUSE_TC, 5});
+    } else {
+        cands.push_back({QSIM_FUSE_GREEDY2, 1});
+    }
+    cudaEvent_t e0, e1;
+    QSIM_CUDA_TRY(cudaEventCreate(&e0), "event");
+    QSIM_CUDA_TRY(cudaEventCreate(&e1), "event");
+    qsim_plan *best = nullptr;
+    float best_ms = 1e30f;
+    Cand bc{0, 0};
+    for (const Cand &cd_ : cands) {
+        qsim_plan *p = nullptr;
+        if (qsim_plan_build(c, cd_.kmax, cd_.mode, &p) != QSIM_OK) continue;  // e.g. too narrow for a tile
+        // the state is scratch: time the plan from |0...0> after one warm-up run
+        if (qsim_state_init(s, QSIM_INIT_ZERO, 0, nullptr) != QSIM_OK || qsim_apply_fused(s, p) != QSIM_OK) {
+            qsim_plan_destroy(p);
+            continue;
+        }
+        cudaEventRecord(e0, s->stream);
+        int rc = QSIM_OK;
+        for (int r = 0; r < reps && rc == QSIM_OK; ++r) rc = qsim_apply_fused(s, p);
+        cudaEventRecord(e1, s->stream);
+        if (rc != QSIM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+            qsim_plan_destroy(p);
+            continue;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best_ms) {
+            if (best) qsim_plan_destroy(best);
+            best = p;
+            best_ms = ms;
+            bc = cd_;
+        } else {
+            qsim_plan_destroy(p);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best) return set_error(QSIM_EUNSUPPORTED, "no fusion plan could run this circuit");
+    *out = best;
+    if (mode_out) *mode_out = best->mode;
+    if (kmax_out) *kmax_out = bc.kmax;
+    if (ms_out) *ms_out = best_ms;
     return QSIM_OK;
 }
 

@@ -17,8 +17,13 @@ constexpr int MAX_SLOTS = REG_BITS + MAX_WARP_BITS;
 constexpr int MAX_OPS = 192;
 constexpr int MAX_PHASES = 24;
 constexpr int MAX_POOL = 768;
+constexpr int MAX_AUX = 192;  // (thread mask, register pattern) pairs of batched sign flips
 
-enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3 };
+// SOP_U1R / SOP_U1L: uncontrolled 1-qubit gates on distinct register / lane
+// bits (mask in a, matrices consecutive in the pool, lowest bit first);
+// SOP_NEG: sign flips (k pairs in aux from moff): amplitude j of a thread
+// flips once per pair with (base & mask) == mask and bit j of the pattern.
+enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3, SOP_U1R = 4, SOP_U1L = 5, SOP_NEG = 6 };
 
 // Position codes: 0..4 lane bit, 8 + b register bit b, 32 + q bit q of the
 // thread's base index (lane, warp or tile qubit).
@@ -49,6 +54,7 @@ template <typename C> struct StageParams {
     Phase phases[MAX_PHASES];
     StageOp ops[MAX_OPS];
     C pool[MAX_POOL];
+    uint64_t aux[2 * MAX_AUX];
 };
 
 template <typename R> struct CT;
@@ -194,6 +200,47 @@ __device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 <<
             __syncthreads();
             continue;
         }
+        if (type == SOP_U1R) {
+            int off = op.moff;
+            const int mask = op.a;
+#define QSIM_U1R_BIT(J)                                                                                        \
+    if (mask & (1 << J)) {                                                                                     \
+        u1_reg<C, J, false>(v, src.pool(off), src.pool(off + 1), src.pool(off + 2), src.pool(off + 3), 0);     \
+        off += 4;                                                                                              \
+    }
+            QSIM_U1R_BIT(0)
+            QSIM_U1R_BIT(1)
+            QSIM_U1R_BIT(2)
+            QSIM_U1R_BIT(3)
+#undef QSIM_U1R_BIT
+            continue;
+        }
+        if (type == SOP_U1L) {
+            int off = op.moff;
+            for (int l = 0; l < LANE_BITS; ++l) {
+                if (!(op.a & (1 << l))) continue;
+                const int bit = (lane >> l) & 1;
+                const C cs = bit ? src.pool(off + 3) : src.pool(off), co = bit ? src.pool(off + 2) : src.pool(off + 1);
+                off += 4;
+#pragma unroll
+                for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], 1 << l), cmul(cs, v[j]));
+            }
+            continue;
+        }
+        if (type == SOP_NEG) {
+            uint32_t flip = 0;
+            for (int e = 0; e < op.k; ++e) {
+                const uint64_t tm = src.aux(op.moff + 2 * e);
+                if ((base & tm) == tm) flip ^= uint32_t(src.aux(op.moff + 2 * e + 1));
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if ((flip >> j) & 1) {
+                    v[j].x = -v[j].x;
+                    v[j].y = -v[j].y;
+                }
+            continue;
+        }
         // controls on lane / warp / tile qubits: one test per thread (a lane
         // gate still takes part in the shuffles when its controls are not met)
         const bool tok = (base & op.tmask) == op.tmask;
@@ -302,6 +349,7 @@ struct Stage {
     std::vector<StageOp> ops;
     std::vector<Phase> phases;
     std::vector<cd> pool;
+    std::vector<uint64_t> aux;
     int phase0 = 0;
 };
 

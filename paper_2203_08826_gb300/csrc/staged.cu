@@ -43,6 +43,7 @@ template <typename C> struct ParamSrc {
     __device__ const StageOp &op(int o) const { return p.ops[o]; }
     __device__ const Phase &phase(int i) const { return p.phases[i]; }
     __device__ C pool(int i) const { return p.pool[i]; }
+    __device__ uint64_t aux(int i) const { return p.aux[i]; }
 };
 
 template <typename R, int W>
@@ -68,6 +69,77 @@ uint64_t qmask(const int *q, int n) {
     uint64_t m = 0;
     for (int i = 0; i < n; ++i) m |= uint64_t(1) << q[i];
     return m;
+}
+
+// Merge adjacent ops that need no ordering among themselves: uncontrolled
+// 1-qubit gates on distinct register bits (or distinct lane bits) commute, and
+// so do sign flips.  One merged op costs one dispatch instead of several.
+void batch_ops(Stage &st) {
+    std::vector<StageOp> out;
+    std::vector<cd> pool;
+    const auto &in = st.ops;
+    size_t i = 0;
+    auto plain_u1 = [](const StageOp &o) { return o.type == SOP_U1 && o.tmask == 0 && o.rneed == 0; };
+    while (i < in.size()) {
+        const StageOp &o = in[i];
+        if (plain_u1(o)) {
+            const bool reg = o.a >= POS_REG;
+            int mask = 0;
+            size_t j = i;
+            while (j < in.size() && plain_u1(in[j]) && ((in[j].a >= POS_REG) == reg)) {
+                const int b = reg ? in[j].a - POS_REG : in[j].a;
+                if (mask & (1 << b)) break;
+                mask |= 1 << b;
+                ++j;
+            }
+            if (j - i >= 2) {
+                StageOp m{};
+                m.type = reg ? SOP_U1R : SOP_U1L;
+                m.a = int8_t(mask);
+                m.moff = int(pool.size());
+                // matrices in increasing bit order
+                for (int b = 0; b < 8; ++b)
+                    for (size_t t = i; t < j; ++t) {
+                        const int tb = reg ? in[t].a - POS_REG : in[t].a;
+                        if (tb == b) pool.insert(pool.end(), st.pool.begin() + in[t].moff, st.pool.begin() + in[t].moff + 4);
+                    }
+                out.push_back(m);
+                i = j;
+                continue;
+            }
+        }
+        if (o.type == SOP_DIAG && o.k == 0 && (o.flags & 1)) {
+            size_t j = i;
+            while (j < in.size() && in[j].type == SOP_DIAG && in[j].k == 0 && (in[j].flags & 1)) ++j;
+            if (j - i >= 2) {
+                StageOp m{};
+                m.type = SOP_NEG;
+                m.k = int8_t(std::min<size_t>(j - i, 127));
+                j = i + size_t(m.k);
+                m.moff = int(st.aux.size());
+                for (size_t t = i; t < j; ++t) {
+                    uint64_t pat = 0;
+                    for (int r = 0; r < (1 << REG_BITS); ++r)
+                        if ((r & in[t].rneed) == in[t].rneed) pat |= uint64_t(1) << r;
+                    st.aux.push_back(in[t].tmask);
+                    st.aux.push_back(pat);
+                }
+                out.push_back(m);
+                i = j;
+                continue;
+            }
+        }
+        StageOp c = o;
+        if (o.type == SOP_U1 || o.type == SOP_U2 || o.type == SOP_DIAG) {
+            const int cnt = o.type == SOP_U1 ? 4 : o.type == SOP_U2 ? 16 : (1 << o.k);
+            c.moff = int(pool.size());
+            pool.insert(pool.end(), st.pool.begin() + o.moff, st.pool.begin() + o.moff + cnt);
+        }
+        out.push_back(c);
+        ++i;
+    }
+    st.ops.swap(out);
+    st.pool.swap(pool);
 }
 
 // Build the op list of one tile stage from its gates (circuit order).
@@ -233,8 +305,9 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         so.moff = add_pool(g.op.m);
         st.ops.push_back(so);
     }
+    batch_ops(st);
     if (limits && (st.ops.size() > size_t(MAX_OPS) || st.phases.size() > size_t(MAX_PHASES) ||
-                   st.pool.size() > size_t(MAX_POOL)))
+                   st.pool.size() > size_t(MAX_POOL) || st.aux.size() > size_t(2 * MAX_AUX)))
         return QSIM_EUNSUPPORTED;
     return QSIM_OK;
 }
@@ -391,6 +464,7 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
             for (const StageOp &o : st.ops) {
                 const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
                 if (o.type == SOP_U1) f += 16.0 * frac;
+                else if (o.type == SOP_U1R || o.type == SOP_U1L) f += 16.0 * __builtin_popcount(unsigned(o.a));
                 else if (o.type == SOP_U2) f += 32.0 * frac;
                 else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
             }
@@ -415,6 +489,7 @@ template <typename C> static void make_params(const Stage &st, StageParams<C> &p
         prm.pool[i].x = decltype(prm.pool[i].x)(st.pool[i].real());
         prm.pool[i].y = decltype(prm.pool[i].y)(st.pool[i].imag());
     }
+    for (size_t i = 0; i < st.aux.size(); ++i) prm.aux[i] = st.aux[i];
 }
 
 static int prepare_staged(qsim_plan &p, int dtype) {
@@ -522,15 +597,17 @@ void staged_describe(const qsim_plan &p, std::string &out) {
             out += buf;
             continue;
         }
-        int cnt[4] = {0, 0, 0, 0}, lane_u1 = 0;
+        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lane_u1 = 0;
         for (const StageOp &o : st.ops) {
             cnt[int(o.type)]++;
             if (o.type == SOP_U1 && o.a < POS_REG) ++lane_u1;
         }
         std::string sl;
         for (int q : st.slots) sl += std::to_string(q) + " ";
-        snprintf(buf, sizeof buf, "  %3zu tile [%s]: u1=%d (lane %d) u2=%d diag=%d exchange=%d\n", i, sl.c_str(),
-                 cnt[SOP_U1], lane_u1, cnt[SOP_U2], cnt[SOP_DIAG], cnt[SOP_EXCHANGE]);
+        snprintf(buf, sizeof buf,
+                 "  %3zu tile [%s]: u1=%d (lane %d) u1-batches reg=%d lane=%d u2=%d diag=%d sign-batches=%d exchange=%d\n",
+                 i, sl.c_str(), cnt[SOP_U1], lane_u1, cnt[SOP_U1R], cnt[SOP_U1L], cnt[SOP_U2], cnt[SOP_DIAG], cnt[SOP_NEG],
+                 cnt[SOP_EXCHANGE]);
         out += buf;
     }
 }

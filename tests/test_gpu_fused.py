@@ -123,3 +123,16 @@ def test_tensor_core_rejects_complex128(q):
     s = q.State(13, "c128").init_zero()
     with pytest.raises(q.QsimError):
         s.run_fused(q.Plan(circ, kmax=6, mode=q.FUSE_TC))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_plan_autotuner_picks_a_correct_plan(q, orc, dtype):
+    circ = inputs.random_circuit(14, 6, seed=31)
+    scratch = q.State(14, dtype)
+    plan = q.Plan.autotune(circ, scratch, reps=1)
+    assert plan.mode in (q.FUSE_GREEDY2, q.FUSE_STAGED, q.FUSE_TC) and plan.tuned_ms > 0
+    psi0 = inputs.gaussian_state(14, seed=32)
+    s = q.State(14, dtype).from_host(psi0)
+    s.run_fused(plan)
+    err = np.max(np.abs(s.to_host().astype(np.complex128) - orc.simulate(circ, psi0)))
+    assert err <= TOL[dtype]
