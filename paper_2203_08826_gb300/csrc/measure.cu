@@ -5,11 +5,14 @@
 
 namespace qsim {
 
-// |psi|^2 in double without contraction into an FMA, so that the result does
-// not depend on how the compiler schedules the two products.
+// |psi|^2 in double, rounded once from the exact value re^2 + im^2.
+// complex64: both squares of fp32 values are exact in double (48-bit
+// products), so one fused multiply-add gives the same double as the separate
+// product-and-sum; complex128 keeps the two roundings of the product-and-sum
+// without contraction, so the result does not depend on scheduling.
 __device__ __forceinline__ double prob_of(float2 a) {
     const double re = a.x, im = a.y;
-    return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+    return __fma_rn(re, re, __dmul_rn(im, im));
 }
 __device__ __forceinline__ double prob_of(double2 a) {
     return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
@@ -409,11 +412,13 @@ constexpr int CHUNK = 2048;  // amplitudes per first-level CDF entry
 // floor(p * 2^62) for 0 < p < 1, read off the binary representation: with
 // p = m 2^(e-52) (m the 53-bit significand) the weight is m shifted by e + 10.
 __device__ __forceinline__ uint64_t weight_of(double p) {
-    if (!(p > 0.0)) return 0;
-    if (p >= 1.0) return uint64_t(1) << 62;
+    // integer tests on the bits: negative, zero, subnormal -> 0; NaN -> 0; >= 1 -> 2^62
     const uint64_t bits = uint64_t(__double_as_longlong(p));
+    if (bits >> 63) return 0;
     const int ex = int((bits >> 52) & 0x7FF);
-    if (ex == 0) return 0;  // subnormal: far below 2^-62
+    if (ex == 0) return 0;  // zero or subnormal: far below 2^-62
+    if (ex == 0x7FF) return (bits & ((uint64_t(1) << 52) - 1)) ? 0 : (uint64_t(1) << 62);
+    if (ex >= 1023) return uint64_t(1) << 62;
     const uint64_t m = (bits & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
     const int sh = ex - 1023 + 10;  // <= 9 because p < 1
     return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0);
@@ -450,9 +455,15 @@ __global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ s
         for (int j = 0; j < CHUNK / 32; ++j) {
             const uint64_t x = x0 + uint64_t(j) * 32 + lane;
             if (x < N) {
-                const double p = src_prob<SRC>(src, x);
-                wsum += weight_of(p);
-                pf += p > 0.0 ? float(p) : 0.f;
+                if (SRC == SRC_C64) {
+                    const float2 a = static_cast<const float2 *>(src)[x];
+                    wsum += weight_of(prob_of(a));
+                    pf += a.x * a.x + a.y * a.y;
+                } else {
+                    const double p = src_prob<SRC>(src, x);
+                    wsum += weight_of(p);
+                    pf += p > 0.0 ? float(p) : 0.f;
+                }
             }
         }
     }
