@@ -15,6 +15,7 @@
 
 #include "internal.h"
 #include "plan.h"
+#include "stage_common.cuh"
 
 namespace qsim {
 namespace {
@@ -323,6 +324,186 @@ int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HPar
     return QSIM_OK;
 }
 
+// ------------------------------------------------------------------ fused reverse sweep
+// complex64, n >= 12: the reverse sweep runs as register-tile stages over both
+// states at once (tiles of 2^12 amplitudes, the forward sweep as a staged
+// plan).  Each rotation's gradient is a SOP_GRAD op of the stage holding its
+// qubit; the CTA sums it in shared memory (double) and writes one partial per
+// tile, reduced per rotation afterwards.
+constexpr int DUAL_W = 3;
+
+struct DualParams {
+    stage::StageParams<float2> sp;
+    int ngrad;
+    int gslot[stage::MAX_GRAD];
+    uint64_t ntiles;
+};
+
+struct DualSrc {
+    const stage::StageParams<float2> &p;
+    __device__ const stage::StageOp &op(int o) const { return p.ops[o]; }
+    __device__ const stage::Phase &phase(int i) const { return p.phases[i]; }
+    __device__ float2 pool(int i) const { return p.pool[i]; }
+    __device__ uint64_t aux(int i) const { return p.aux[i]; }
+};
+
+template <int W>
+__global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam, const __grid_constant__ DualParams dp,
+                                                      double *__restrict__ partial) {
+    using namespace stage;
+    extern __shared__ unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ double gacc[MAX_GRAD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x) gacc[g] = 0.0;
+    __syncthreads();
+    const uint64_t tile_base = expand(blockIdx.x, dp.sp.outer);
+    int ph = dp.sp.phase0;
+    uint64_t base = thread_base<W>(dp.sp.phases[ph], tile_base, lane, warp);
+    float2 v[1 << REG_BITS], w[1 << REG_BITS];
+    tile_global<float2, W, false>(psi, v, dp.sp.phases[ph], base);
+    tile_global<float2, W, false>(lam, w, dp.sp.phases[ph], base);
+    const DualSrc src{dp.sp};
+    stage_exec2<float2, W>(src, dp.sp.nops, v, w, ph, base, tile_base, tile, lane, warp, gacc);
+    tile_global<float2, W, true>(psi, v, dp.sp.phases[ph], base);
+    tile_global<float2, W, true>(lam, w, dp.sp.phases[ph], base);
+    __syncthreads();
+    for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x)
+        partial[uint64_t(dp.gslot[g]) * dp.ntiles + blockIdx.x] = gacc[g];
+}
+
+int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, const HParams &hp, double *grads,
+                      double *energies, cudaStream_t st) {
+    const int n = c.n;
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = sm_count_a() * ADJ_BLOCKS_PER_SM;
+    const int TB = stage::LANE_BITS + stage::REG_BITS + DUAL_W;
+    const uint64_t ntiles = uint64_t(1) << (n - TB);
+    std::vector<int> rot_of_gate(c.gates.size(), -1);
+    int nrot = 0;
+    for (size_t i = 0; i < c.gates.size(); ++i) {
+        const GateRec &g = c.gates[i];
+        if (g.pindex < 0) continue;
+        if (g.nc != 0 || g.k != 1) return set_error(QSIM_EUNSUPPORTED, "trainable rotations must be uncontrolled 1-qubit gates");
+        rot_of_gate[i] = nrot++;
+    }
+    float2 *psi = nullptr, *lam = nullptr;
+    double *partial = nullptr, *rows = nullptr, *epart = nullptr;
+    cudaError_t e = cudaMalloc(&psi, N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&lam, N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&partial, std::max<size_t>(1, size_t(nrot) * ntiles) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&epart, size_t(blocks) * sizeof(double));
+    struct Guard {
+        void *p[5];
+        ~Guard() {
+            for (void *x : p)
+                if (x) cudaFree(x);
+        }
+    } guard{{psi, lam, partial, rows, epart}};
+    if (e != cudaSuccess) return cuda_error(e, "adjoint buffers");
+    qsim_state *ps = nullptr;
+    QSIM_TRY(qsim_state_create(n, QSIM_C64, psi, st, &ps));
+    struct SGuard {
+        qsim_state *s;
+        ~SGuard() { qsim_state_destroy(s); }
+    } sguard{ps};
+    std::vector<double> host_rows(size_t(nrot) + 1);
+    const size_t smem = (size_t(1) << TB) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        QSIM_CUDA_TRY(cudaFuncSetAttribute(k_adj_stage<DUAL_W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                      "adjoint stage smem");
+        attr = true;
+    }
+    for (int set = 0; set < nsets; ++set) {
+        const double *th = params + size_t(set) * size_t(c.nparams);
+        // forward circuit with this set's angles, and the reverse sweep:
+        // gates un-applied last to first, a gradient marker before each rotation
+        qsim_circuit fwd, bwd;
+        fwd.n = bwd.n = n;
+        fwd.gates = c.gates;
+        for (size_t i = 0; i < fwd.gates.size(); ++i)
+            if (fwd.gates[i].pindex >= 0) QSIM_TRY(rotation_matrix(fwd.gates[i].kind, th[fwd.gates[i].pindex], fwd.gates[i].m));
+        for (size_t ii = fwd.gates.size(); ii-- > 0;) {
+            const GateRec &g = fwd.gates[ii];
+            if (rot_of_gate[ii] >= 0) {
+                GateRec mk;
+                mk.kind = QSIM_GATE_MATRIX;
+                mk.k = 1;
+                mk.targets[0] = g.targets[0];
+                mk.m = {1.0, 0.0, 0.0, 1.0};
+                mk.grad_slot = rot_of_gate[ii];
+                mk.grad_P = g.kind == QSIM_GATE_RX ? 0 : g.kind == QSIM_GATE_RY ? 1 : 2;
+                bwd.gates.push_back(mk);
+            }
+            GateRec inv = g;
+            inv.kind = QSIM_GATE_MATRIX;
+            inv.pindex = -1;
+            const size_t d = size_t(1) << g.k;
+            for (size_t r = 0; r < d; ++r)
+                for (size_t col = 0; col < d; ++col) inv.m[col * d + r] = std::conj(g.m[r * d + col]);
+            bwd.gates.push_back(inv);
+        }
+        // forward sweep (staged plan) from |0>
+        qsim_plan *fp = nullptr;
+        QSIM_TRY(qsim_plan_build(&fwd, DUAL_W, QSIM_FUSE_STAGED, &fp));
+        struct PGuard {
+            qsim_plan *p;
+            ~PGuard() { qsim_plan_destroy(p); }
+        } pguard{fp};
+        QSIM_TRY(launch_init(psi, n, QSIM_C64, 0, st));
+        QSIM_TRY(qsim_apply_fused(ps, fp));
+        {
+            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(float2) * (hp.ngroups + 1));
+            k_happly<float2><<<blocks, 256, 0, st>>>(psi, lam, N, hp);
+            QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+        }
+        {
+            LaunchScope ls(K_REDUCE, st, 2.0 * double(N) * sizeof(float2));
+            k_dot_re<float2><<<blocks, 256, 0, st>>>(psi, lam, N, epart);
+            QSIM_CUDA_TRY(cudaGetLastError(), "energy launch");
+        }
+        // reverse sweep as two-state stages
+        std::vector<stage::Stage> stages;
+        QSIM_TRY(stage::plan_stage_list(bwd, DUAL_W, true, stages));
+        for (const stage::Stage &sg : stages) {
+            if (sg.plain) {
+                if (sg.op.type == Op::DENSE && sg.op.k >= 2)
+                    return set_error(QSIM_EUNSUPPORTED, "adjoint: gates of more than 2 targets");
+                QSIM_TRY(launch_op(psi, n, QSIM_C64, sg.op, st, nullptr));
+                QSIM_TRY(launch_op(lam, n, QSIM_C64, sg.op, st, nullptr));
+                continue;
+            }
+            DualParams dp;
+            memset(&dp, 0, sizeof dp);
+            stage::make_params<float2>(sg, dp.sp);
+            dp.ngrad = int(sg.grad_slots.size());
+            for (int g = 0; g < dp.ngrad; ++g) dp.gslot[g] = sg.grad_slots[g];
+            dp.ntiles = ntiles;
+            LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2));
+            k_adj_stage<DUAL_W><<<unsigned(ntiles), 32 << DUAL_W, smem, st>>>(psi, lam, dp, partial);
+            QSIM_CUDA_TRY(cudaGetLastError(), "adjoint stage launch");
+        }
+        {
+            LaunchScope ls(K_REDUCE, st, double(nrot) * ntiles * 8.0);
+            if (nrot) k_rows<<<std::min(nrot, 1024), 256, 0, st>>>(partial, nrot, int(ntiles), rows);
+            k_rows<<<1, 256, 0, st>>>(epart, 1, blocks, rows + nrot);
+            QSIM_CUDA_TRY(cudaGetLastError(), "adjoint reduce launch");
+        }
+        QSIM_CUDA_TRY(cudaMemcpyAsync(host_rows.data(), rows, host_rows.size() * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st),
+                      "adjoint result copy");
+        QSIM_CUDA_TRY(cudaStreamSynchronize(st), "adjoint sync");
+        double *gset = grads + size_t(set) * size_t(c.nparams);
+        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
+        for (size_t i = 0; i < c.gates.size(); ++i)
+            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += host_rows[rot_of_gate[i]];
+        if (energies) energies[set] = host_rows[nrot];
+    }
+    return QSIM_OK;
+}
+
 }  // namespace
 }  // namespace qsim
 
@@ -360,6 +541,10 @@ extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, co
         hp.t0[hp.ngroups] = nt;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // complex64 from 12 qubits: register-tile stages over both states;
+    // otherwise one sweep per gate
+    if (dtype == QSIM_C64 && c->n >= stage::LANE_BITS + stage::REG_BITS + DUAL_W)
+        return adjoint_fused_c64(*c, nsets, params, hp, grads, energies, st);
     return dtype == QSIM_C64 ? adjoint_t<float>(*c, nsets, params, hp, grads, energies, st)
                              : adjoint_t<double>(*c, nsets, params, hp, grads, energies, st);
 }

@@ -2,6 +2,7 @@
 // batched persistent kernel (see staged.cu for the scheme).
 #pragma once
 
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -18,12 +19,15 @@ constexpr int MAX_OPS = 192;
 constexpr int MAX_PHASES = 24;
 constexpr int MAX_POOL = 768;
 constexpr int MAX_AUX = 192;  // (thread mask, register pattern) pairs of batched sign flips
+constexpr int MAX_GRAD = 96;  // gradient slots of one reverse-sweep stage
 
 // SOP_U1R / SOP_U1L: uncontrolled 1-qubit gates on distinct register / lane
 // bits (mask in a, matrices consecutive in the pool, lowest bit first);
 // SOP_NEG: sign flips (k pairs in aux from moff): amplitude j of a thread
 // flips once per pair with (base & mask) == mask and bit j of the pattern.
-enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3, SOP_U1R = 4, SOP_U1L = 5, SOP_NEG = 6 };
+// SOP_GRAD: adjoint gradient term Im<lambda|P|psi> (a = position, k = Pauli,
+// moff = slot); only the two-state executor runs it.
+enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3, SOP_U1R = 4, SOP_U1L = 5, SOP_NEG = 6, SOP_GRAD = 7 };
 
 // Position codes: 0..4 lane bit, 8 + b register bit b, 32 + q bit q of the
 // thread's base index (lane, warp or tile qubit).
@@ -181,17 +185,157 @@ __device__ __forceinline__ void tile_shared(C *tile, C (&v)[1 << REG_BITS], cons
 }
 
 
+// One non-exchange op on the 16 amplitudes v of a thread whose register 0
+// sits at global index `base`.
+template <typename C, typename Src>
+__device__ __forceinline__ void apply_op(const StageOp &op, const Src &src, C (&v)[1 << REG_BITS], uint64_t base,
+                                         int lane) {
+    constexpr int NR = 1 << REG_BITS;
+    const int type = op.type;
+    if (type == SOP_U1R) {
+        int off = op.moff;
+        const int mask = op.a;
+#define QSIM_U1R_BIT(J)                                                                                        \
+if (mask & (1 << J)) {                                                                                     \
+    u1_reg<C, J, false>(v, src.pool(off), src.pool(off + 1), src.pool(off + 2), src.pool(off + 3), 0);     \
+    off += 4;                                                                                              \
+}
+        QSIM_U1R_BIT(0)
+        QSIM_U1R_BIT(1)
+        QSIM_U1R_BIT(2)
+        QSIM_U1R_BIT(3)
+#undef QSIM_U1R_BIT
+        return;
+    }
+    if (type == SOP_U1L) {
+        int off = op.moff;
+        for (int l = 0; l < LANE_BITS; ++l) {
+            if (!(op.a & (1 << l))) continue;
+            const int bit = (lane >> l) & 1;
+            const C cs = bit ? src.pool(off + 3) : src.pool(off), co = bit ? src.pool(off + 2) : src.pool(off + 1);
+            off += 4;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], 1 << l), cmul(cs, v[j]));
+        }
+        return;
+    }
+    if (type == SOP_NEG) {
+        uint32_t flip = 0;
+        for (int e = 0; e < op.k; ++e) {
+            const uint64_t tm = src.aux(op.moff + 2 * e);
+            if ((base & tm) == tm) flip ^= uint32_t(src.aux(op.moff + 2 * e + 1));
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((flip >> j) & 1) {
+                v[j].x = -v[j].x;
+                v[j].y = -v[j].y;
+            }
+        return;
+    }
+    // controls on lane / warp / tile qubits: one test per thread (a lane
+    // gate still takes part in the shuffles when its controls are not met)
+    const bool tok = (base & op.tmask) == op.tmask;
+    if (!tok && !(type == SOP_U1 && op.a < POS_REG)) return;
+    const int rneed = op.rneed;
+    if (type == SOP_U1) {
+        const C m00 = src.pool(op.moff), m01 = src.pool(op.moff + 1);
+        const C m10 = src.pool(op.moff + 2), m11 = src.pool(op.moff + 3);
+        if (op.a >= POS_REG) {
+            switch (op.a - POS_REG) {
+                case 0: u1_reg_dispatch<C, 0>(v, m00, m01, m10, m11, rneed); break;
+                case 1: u1_reg_dispatch<C, 1>(v, m00, m01, m10, m11, rneed); break;
+                case 2: u1_reg_dispatch<C, 2>(v, m00, m01, m10, m11, rneed); break;
+                default: u1_reg_dispatch<C, 3>(v, m00, m01, m10, m11, rneed); break;
+            }
+        } else {
+            const int bit = (lane >> op.a) & 1;
+            const C cs = bit ? m11 : m00, co = bit ? m10 : m01;
+            const int lm = 1 << op.a;
+            if (tok && rneed == 0) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], lm), cmul(cs, v[j]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const C other = shfl_c(v[j], lm);
+                    if (tok && (j & rneed) == rneed) v[j] = cmad(co, other, cmul(cs, v[j]));
+                }
+            }
+        }
+    } else if (type == SOP_U2) {
+        C m[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) m[e] = src.pool(op.moff + e);
+        switch ((op.a - POS_REG) * 4 + (op.b - POS_REG)) {
+            case 1: u2_reg<C, 0, 1>(v, m, rneed); break;
+            case 2: u2_reg<C, 0, 2>(v, m, rneed); break;
+            case 3: u2_reg<C, 0, 3>(v, m, rneed); break;
+            case 4: u2_reg<C, 1, 0>(v, m, rneed); break;
+            case 6: u2_reg<C, 1, 2>(v, m, rneed); break;
+            case 7: u2_reg<C, 1, 3>(v, m, rneed); break;
+            case 8: u2_reg<C, 2, 0>(v, m, rneed); break;
+            case 9: u2_reg<C, 2, 1>(v, m, rneed); break;
+            case 11: u2_reg<C, 2, 3>(v, m, rneed); break;
+            case 12: u2_reg<C, 3, 0>(v, m, rneed); break;
+            case 13: u2_reg<C, 3, 1>(v, m, rneed); break;
+            default: u2_reg<C, 3, 2>(v, m, rneed); break;
+        }
+    } else if (op.k == 0) {  // SOP_DIAG, one factor on the control subspace
+        if (op.flags & 1) {
+            if (rneed == 0) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    v[j].x = -v[j].x;
+                    v[j].y = -v[j].y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NR; ++j)
+                    if ((j & rneed) == rneed) {
+                        v[j].x = -v[j].x;
+                        v[j].y = -v[j].y;
+                    }
+            }
+        } else {
+            const C f = src.pool(op.moff);
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if ((j & rneed) == rneed) v[j] = cmul(f, v[j]);
+        }
+    } else {  // SOP_DIAG with selector qubits
+        int sel_t = 0, regsel[QSIM_MAX_TARGETS];
+        const int k = op.k;
+        for (int t = 0; t < k; ++t) {
+            const int code = op.dq[t];
+            const int sh = k - 1 - t;
+            if (code >= POS_BASE) {
+                sel_t |= int((base >> (code - POS_BASE)) & 1) << sh;
+                regsel[t] = 0;
+            } else {
+                regsel[t] = code - POS_REG + 1;  // register bit + 1
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if ((j & rneed) != rneed) continue;
+            int sel = sel_t;
+            for (int t = 0; t < k; ++t)
+                if (regsel[t]) sel |= ((j >> (regsel[t] - 1)) & 1) << (k - 1 - t);
+            v[j] = cmul(src.pool(op.moff + sel), v[j]);
+        }
+    }
+}
+
 // One pass of the op list over the tile held in v (16 amplitudes per thread).
-// Src supplies op(o), phase(i) and pool(i); ph / base are the current phase
-// and the thread's base index, updated by EXCHANGE ops.
+// Src supplies op(o), phase(i), pool(i) and aux(i); ph / base are the current
+// phase and the thread's base index, updated by EXCHANGE ops.
 template <typename C, int W, typename Src>
 __device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 << REG_BITS], int &ph, uint64_t &base,
                                            uint64_t tile_base, C *tile, int lane, int warp) {
-    constexpr int NR = 1 << REG_BITS;
     for (int o = 0; o < nops; ++o) {
         const StageOp &op = src.op(o);
-        const int type = op.type;
-        if (type == SOP_EXCHANGE) {
+        if (op.type == SOP_EXCHANGE) {
             tile_shared<C, W, true>(tile, v, src.phase(ph), lane, warp);
             __syncthreads();
             ph = op.a;
@@ -200,146 +344,98 @@ __device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 <<
             __syncthreads();
             continue;
         }
-        if (type == SOP_U1R) {
-            int off = op.moff;
-            const int mask = op.a;
-#define QSIM_U1R_BIT(J)                                                                                        \
-    if (mask & (1 << J)) {                                                                                     \
-        u1_reg<C, J, false>(v, src.pool(off), src.pool(off + 1), src.pool(off + 2), src.pool(off + 3), 0);     \
-        off += 4;                                                                                              \
+        apply_op<C>(op, src, v, base, lane);
     }
-            QSIM_U1R_BIT(0)
-            QSIM_U1R_BIT(1)
-            QSIM_U1R_BIT(2)
-            QSIM_U1R_BIT(3)
-#undef QSIM_U1R_BIT
+}
+
+// Im<w| P |v> over the thread's 16 amplitudes for the Pauli P (0 X, 1 Y, 2 Z)
+// on register bit RB (RB < 0: lane bit a): Im(conj(w_j) (P v)_j).  The
+// register bit is a template argument so that v and w stay in registers.
+template <typename C, int RB>
+__device__ __forceinline__ float grad_partial_t(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int P,
+                                                int lane) {
+    constexpr int NR = 1 << REG_BITS;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        C partner;
+        int bit;
+        if (RB < 0) {
+            partner = shfl_c(v[j], 1 << a);
+            bit = (lane >> a) & 1;
+        } else {
+            partner = v[j ^ (1 << (RB < 0 ? 0 : RB))];
+            bit = (j >> (RB < 0 ? 0 : RB)) & 1;
+        }
+        C pv;
+        if (P == 0) {  // X
+            pv = partner;
+        } else if (P == 1) {  // Y: (P v)_x = -i v_{x^b} for bit 0, +i v_{x^b} for bit 1
+            pv.x = bit ? -partner.y : partner.y;
+            pv.y = bit ? partner.x : -partner.x;
+        } else {  // Z
+            pv.x = bit ? -v[j].x : v[j].x;
+            pv.y = bit ? -v[j].y : v[j].y;
+        }
+        acc += float(w[j].x) * float(pv.y) - float(w[j].y) * float(pv.x);
+    }
+    return acc;
+}
+
+// position a: lane bit a < 8, register bit a - 8
+template <typename C>
+__device__ __forceinline__ float grad_partial(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int P,
+                                              int lane) {
+    switch (a - POS_REG) {
+        case 0: return grad_partial_t<C, 0>(v, w, a, P, lane);
+        case 1: return grad_partial_t<C, 1>(v, w, a, P, lane);
+        case 2: return grad_partial_t<C, 2>(v, w, a, P, lane);
+        case 3: return grad_partial_t<C, 3>(v, w, a, P, lane);
+        default: return grad_partial_t<C, -1>(v, w, a, P, lane);
+    }
+}
+
+// The reverse sweep of the adjoint gradient: the same op list applied to two
+// tiles (psi in v, lambda in w); SOP_GRAD ops (a = position, k = Pauli, moff =
+// local slot) add Im<lambda|P|psi> of the CTA to gacc[slot] (shared, double).
+template <typename C, int W, typename Src>
+__device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 << REG_BITS], C (&w)[1 << REG_BITS],
+                                            int &ph, uint64_t &base, uint64_t tile_base, C *tile, int lane, int warp,
+                                            double *gacc) {
+    for (int o = 0; o < nops; ++o) {
+        const StageOp &op = src.op(o);
+        if (op.type == SOP_EXCHANGE) {
+            tile_shared<C, W, true>(tile, v, src.phase(ph), lane, warp);
+            __syncthreads();
+            const int nph = op.a;
+            tile_shared<C, W, false>(tile, v, src.phase(nph), lane, warp);
+            __syncthreads();
+            tile_shared<C, W, true>(tile, w, src.phase(ph), lane, warp);
+            __syncthreads();
+            tile_shared<C, W, false>(tile, w, src.phase(nph), lane, warp);
+            __syncthreads();
+            ph = nph;
+            base = thread_base<W>(src.phase(ph), tile_base, lane, warp);
             continue;
         }
-        if (type == SOP_U1L) {
-            int off = op.moff;
-            for (int l = 0; l < LANE_BITS; ++l) {
-                if (!(op.a & (1 << l))) continue;
-                const int bit = (lane >> l) & 1;
-                const C cs = bit ? src.pool(off + 3) : src.pool(off), co = bit ? src.pool(off + 2) : src.pool(off + 1);
-                off += 4;
+        if (op.type == SOP_GRAD) {
+            double g = grad_partial<C>(v, w, op.a, op.k, lane);
 #pragma unroll
-                for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], 1 << l), cmul(cs, v[j]));
-            }
+            for (int s = 16; s > 0; s >>= 1) g += __shfl_xor_sync(0xffffffffu, g, s);
+            if (lane == 0) atomicAdd(&gacc[op.moff], g);
             continue;
         }
-        if (type == SOP_NEG) {
-            uint32_t flip = 0;
-            for (int e = 0; e < op.k; ++e) {
-                const uint64_t tm = src.aux(op.moff + 2 * e);
-                if ((base & tm) == tm) flip ^= uint32_t(src.aux(op.moff + 2 * e + 1));
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j)
-                if ((flip >> j) & 1) {
-                    v[j].x = -v[j].x;
-                    v[j].y = -v[j].y;
-                }
-            continue;
-        }
-        // controls on lane / warp / tile qubits: one test per thread (a lane
-        // gate still takes part in the shuffles when its controls are not met)
-        const bool tok = (base & op.tmask) == op.tmask;
-        if (!tok && !(type == SOP_U1 && op.a < POS_REG)) continue;
-        const int rneed = op.rneed;
-        if (type == SOP_U1) {
-            const C m00 = src.pool(op.moff), m01 = src.pool(op.moff + 1);
-            const C m10 = src.pool(op.moff + 2), m11 = src.pool(op.moff + 3);
-            if (op.a >= POS_REG) {
-                switch (op.a - POS_REG) {
-                    case 0: u1_reg_dispatch<C, 0>(v, m00, m01, m10, m11, rneed); break;
-                    case 1: u1_reg_dispatch<C, 1>(v, m00, m01, m10, m11, rneed); break;
-                    case 2: u1_reg_dispatch<C, 2>(v, m00, m01, m10, m11, rneed); break;
-                    default: u1_reg_dispatch<C, 3>(v, m00, m01, m10, m11, rneed); break;
-                }
-            } else {
-                const int bit = (lane >> op.a) & 1;
-                const C cs = bit ? m11 : m00, co = bit ? m10 : m01;
-                const int lm = 1 << op.a;
-                if (tok && rneed == 0) {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], lm), cmul(cs, v[j]));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) {
-                        const C other = shfl_c(v[j], lm);
-                        if (tok && (j & rneed) == rneed) v[j] = cmad(co, other, cmul(cs, v[j]));
-                    }
-                }
-            }
-        } else if (type == SOP_U2) {
-            C m[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) m[e] = src.pool(op.moff + e);
-            switch ((op.a - POS_REG) * 4 + (op.b - POS_REG)) {
-                case 1: u2_reg<C, 0, 1>(v, m, rneed); break;
-                case 2: u2_reg<C, 0, 2>(v, m, rneed); break;
-                case 3: u2_reg<C, 0, 3>(v, m, rneed); break;
-                case 4: u2_reg<C, 1, 0>(v, m, rneed); break;
-                case 6: u2_reg<C, 1, 2>(v, m, rneed); break;
-                case 7: u2_reg<C, 1, 3>(v, m, rneed); break;
-                case 8: u2_reg<C, 2, 0>(v, m, rneed); break;
-                case 9: u2_reg<C, 2, 1>(v, m, rneed); break;
-                case 11: u2_reg<C, 2, 3>(v, m, rneed); break;
-                case 12: u2_reg<C, 3, 0>(v, m, rneed); break;
-                case 13: u2_reg<C, 3, 1>(v, m, rneed); break;
-                default: u2_reg<C, 3, 2>(v, m, rneed); break;
-            }
-        } else if (op.k == 0) {  // SOP_DIAG, one factor on the control subspace
-            if (op.flags & 1) {
-                if (rneed == 0) {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) {
-                        v[j].x = -v[j].x;
-                        v[j].y = -v[j].y;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j)
-                        if ((j & rneed) == rneed) {
-                            v[j].x = -v[j].x;
-                            v[j].y = -v[j].y;
-                        }
-                }
-            } else {
-                const C f = src.pool(op.moff);
-#pragma unroll
-                for (int j = 0; j < NR; ++j)
-                    if ((j & rneed) == rneed) v[j] = cmul(f, v[j]);
-            }
-        } else {  // SOP_DIAG with selector qubits
-            int sel_t = 0, regsel[QSIM_MAX_TARGETS];
-            const int k = op.k;
-            for (int t = 0; t < k; ++t) {
-                const int code = op.dq[t];
-                const int sh = k - 1 - t;
-                if (code >= POS_BASE) {
-                    sel_t |= int((base >> (code - POS_BASE)) & 1) << sh;
-                    regsel[t] = 0;
-                } else {
-                    regsel[t] = code - POS_REG + 1;  // register bit + 1
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                if ((j & rneed) != rneed) continue;
-                int sel = sel_t;
-                for (int t = 0; t < k; ++t)
-                    if (regsel[t]) sel |= ((j >> (regsel[t] - 1)) & 1) << (k - 1 - t);
-                v[j] = cmul(src.pool(op.moff + sel), v[j]);
-            }
-        }
+        apply_op<C>(op, src, v, base, lane);
+        apply_op<C>(op, src, w, base, lane);
     }
 }
 
 // ------------------------------------------------------------------ host planner
 struct GateClass {
     enum { DIAG, DENSE1, DENSE2, OTHER } kind;
-    Op op;  // classified form (targets reduced, controls extended)
+    Op op;            // classified form (targets reduced, controls extended)
+    int grad_slot = -1;  // >= 0: an adjoint gradient marker on op.targets[0]
+    int grad_P = 0;
 };
 
 struct Stage {
@@ -350,6 +446,7 @@ struct Stage {
     std::vector<Phase> phases;
     std::vector<cd> pool;
     std::vector<uint64_t> aux;
+    std::vector<int> grad_slots;  // global gradient slot of each local SOP_GRAD slot
     int phase0 = 0;
 };
 
@@ -357,6 +454,25 @@ struct Stage {
 // `limits` the op, phase and pool counts of a stage stay within one kernel
 // parameter block.
 int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out);
+
+// Kernel parameter block of one tile stage.
+template <typename C> inline void make_params(const Stage &st, StageParams<C> &prm) {
+    memset(&prm, 0, sizeof prm);
+    int tq[LANE_BITS + MAX_SLOTS];
+    int nt = 0;
+    for (int q = 0; q < LANE_BITS; ++q) tq[nt++] = q;
+    for (int q : st.slots) tq[nt++] = q;
+    prm.outer = make_index_map(tq, nt, nullptr, 0);
+    prm.nops = int(st.ops.size());
+    prm.phase0 = st.phase0;
+    for (size_t i = 0; i < st.phases.size(); ++i) prm.phases[i] = st.phases[i];
+    for (size_t i = 0; i < st.ops.size(); ++i) prm.ops[i] = st.ops[i];
+    for (size_t i = 0; i < st.pool.size(); ++i) {
+        prm.pool[i].x = decltype(prm.pool[i].x)(st.pool[i].real());
+        prm.pool[i].y = decltype(prm.pool[i].y)(st.pool[i].imag());
+    }
+    for (size_t i = 0; i < st.aux.size(); ++i) prm.aux[i] = st.aux[i];
+}
 
 }  // namespace stage
 }  // namespace qsim

@@ -223,7 +223,7 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         const int b = reg_bit(q);
         if (b >= 0 && (so.rneed >> b & 1)) return true;
         if (so.tmask >> q & 1) return true;
-        if (so.type == SOP_U1) return so.a == pos_of(q);
+        if (so.type == SOP_U1 || so.type == SOP_GRAD) return so.a == pos_of(q);
         if (so.type == SOP_U2) return so.a == pos_of(q) || so.b == pos_of(q);
         if (so.type == SOP_DIAG)
             for (int t = 0; t < so.k; ++t)
@@ -284,6 +284,15 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         }
         StageOp so{};
         split_controls(g.op, so);
+        if (g.grad_slot >= 0) {
+            so.type = SOP_GRAD;
+            so.a = int8_t(pos_of(g.op.targets[0]));
+            so.k = int8_t(g.grad_P);
+            so.moff = int(st.grad_slots.size());
+            st.grad_slots.push_back(g.grad_slot);
+            st.ops.push_back(so);
+            continue;
+        }
         if (g.kind == GateClass::DENSE1) {
             so.type = SOP_U1;
             so.a = int8_t(pos_of(g.op.targets[0]));
@@ -307,7 +316,8 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
     }
     batch_ops(st);
     if (limits && (st.ops.size() > size_t(MAX_OPS) || st.phases.size() > size_t(MAX_PHASES) ||
-                   st.pool.size() > size_t(MAX_POOL) || st.aux.size() > size_t(2 * MAX_AUX)))
+                   st.pool.size() > size_t(MAX_POOL) || st.aux.size() > size_t(2 * MAX_AUX) ||
+                   st.grad_slots.size() > size_t(MAX_GRAD)))
         return QSIM_EUNSUPPORTED;
     return QSIM_OK;
 }
@@ -320,6 +330,18 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
     std::vector<GateClass> cls(c.gates.size());
     for (size_t i = 0; i < c.gates.size(); ++i) {
         const GateRec &g = c.gates[i];
+        if (g.grad_slot >= 0) {
+            // adjoint gradient marker: needs its qubit in the tile like a 1-qubit gate
+            cls[i].kind = GateClass::DENSE1;
+            cls[i].op = Op{};
+            cls[i].op.type = Op::DENSE;
+            cls[i].op.k = 1;
+            cls[i].op.targets[0] = g.targets[0];
+            cls[i].op.m = {1.0, 0.0, 0.0, 1.0};
+            cls[i].grad_slot = g.grad_slot;
+            cls[i].grad_P = g.grad_P;
+            continue;
+        }
         QSIM_TRY(classify(g.m, g.targets, g.k, g.controls, g.nc, cls[i].op));
         Op &op = cls[i].op;
         if (op.type == Op::IDENTITY || op.type == Op::DIAG) {
@@ -472,24 +494,6 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
         sp->flops_per_amp.push_back(f);
     }
     return QSIM_OK;
-}
-
-template <typename C> static void make_params(const Stage &st, StageParams<C> &prm) {
-    memset(&prm, 0, sizeof prm);
-    int tq[LANE_BITS + MAX_SLOTS];
-    int nt = 0;
-    for (int q = 0; q < LANE_BITS; ++q) tq[nt++] = q;
-    for (int q : st.slots) tq[nt++] = q;
-    prm.outer = make_index_map(tq, nt, nullptr, 0);
-    prm.nops = int(st.ops.size());
-    prm.phase0 = st.phase0;
-    for (size_t i = 0; i < st.phases.size(); ++i) prm.phases[i] = st.phases[i];
-    for (size_t i = 0; i < st.ops.size(); ++i) prm.ops[i] = st.ops[i];
-    for (size_t i = 0; i < st.pool.size(); ++i) {
-        prm.pool[i].x = decltype(prm.pool[i].x)(st.pool[i].real());
-        prm.pool[i].y = decltype(prm.pool[i].y)(st.pool[i].imag());
-    }
-    for (size_t i = 0; i < st.aux.size(); ++i) prm.aux[i] = st.aux[i];
 }
 
 static int prepare_staged(qsim_plan &p, int dtype) {

@@ -91,3 +91,20 @@ def test_adjoint_24q_config_properties(q):
         _, ep = q.adjoint_grad(circ, ham, tp[None, :], "c128")
         _, em = q.adjoint_grad(circ, ham, tm[None, :], "c128")
         assert abs((ep[0] - em[0]) / (2 * h) - g128[0, p_]) < 1e-6
+
+
+@pytest.mark.parametrize("maker", ["variational", "mixed"])
+def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker):
+    """complex64 from 12 qubits runs the reverse sweep as two-state register
+    tiles (gradient terms accumulated per CTA): all gradients vs the oracle."""
+    circ = inputs.variational(13, 2, seed=7) if maker == "variational" else mixed_ansatz(13, 2, seed=8)
+    ham = inputs.tfim(13)
+    rng = np.random.default_rng(9)
+    thetas = rng.uniform(0, 2 * np.pi, size=(2, circ.nparams))
+    grads, en = q.adjoint_grad(circ, ham, thetas, "c64")
+    g128, e128 = q.adjoint_grad(circ, ham, thetas, "c128")   # the plain sweeps path
+    for s in range(2):
+        want = orc.parameter_shift_gradient(circ, ham, thetas[s])
+        np.testing.assert_allclose(grads[s], want, atol=2e-4)
+        np.testing.assert_allclose(g128[s], want, atol=1e-10)
+        assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < 2e-4

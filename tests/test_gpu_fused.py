@@ -83,6 +83,19 @@ def test_staged_small_widths(q, orc, n):
     assert np.max(np.abs(got - want)) <= 1e-12
 
 
+@pytest.mark.parametrize("kmax", [3, 4])
+@pytest.mark.parametrize("maker", ["random", "mixed"])
+def test_staged_many_tiles(q, orc, kmax, maker):
+    """21 qubits: hundreds of tiles, phases with warp and tile qubits high."""
+    n = 21
+    circ = inputs.random_circuit(n, 5, seed=9) if maker == "random" else mixed_circuit(n, seed=10, depth=4)
+    psi0 = inputs.gaussian_state(n, seed=12)
+    want = orc.simulate(circ, psi0)
+    got = run_plan(q, circ, "c64", psi0, q.FUSE_STAGED, kmax)
+    err = np.max(np.abs(got - want))
+    assert err <= TOL["c64"], f"staged {maker} n=21 kmax={kmax}: {err:.3e}"
+
+
 def test_staged_covers_fewer_sweeps(q):
     c = inputs.random_circuit(30, 20, seed=2022)
     info = q.Plan(c, kmax=4, mode=q.FUSE_STAGED).info()
