@@ -491,14 +491,34 @@ def other_workloads(q, torch, peak, peak_src):
     c = inputs.variational(24, 10, seed=5)
     qc = q.QCircuit(c)
     ham = inputs.tfim(24)
-    th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(4, c.nparams))
+    th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(64, c.nparams))
     q.adjoint_grad(qc, ham, th[:1], "c64")
     t0 = time.perf_counter()
     q.adjoint_grad(qc, ham, th, "c64")
     dt = (time.perf_counter() - t0) / len(th)
     out["adjoint24_c64"] = {"s_per_parameter_set": dt, "gradients_per_s": c.nparams / dt,
                             "workload": "24 qubits, 10 layers RY/RZ + CZ ladder, 480 parameters, "
-                                        "H = sum(Z_i Z_i+1 + 0.5 X_i), 4 parameter sets"}
+                                        "H = sum(Z_i Z_i+1 + 0.5 X_i), 64 parameter sets"}
+    # sliced states (Sec. 3.1 multi-GPU scheme): 30-qubit random circuit, 8 slices
+    from paper_2203_08826_gb300 import sliced
+    c = inputs.random_circuit(30, DEPTH, seed=2022)
+    qc = q.QCircuit(c)
+    res = {}
+    for loc in ("device", "host"):
+        plan = q.SlicePlan(qc, 3, kmax=4, mode=q.FUSE_STAGED)
+        stt = sliced.SlicedState(30, 3, "c64", loc).init_zero()
+        ms, prof = ev_time(lambda: stt.run(plan), 1, 2, profile=True)
+        info = plan.info()
+        r = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3), "swaps": info["swaps"],
+             "segments": sum(1 for x in plan.steps() if x["type"] == "segment")}
+        for k in ("slice_exchange", "copy_h2d", "copy_d2h"):
+            if k in prof and prof[k]["ms"] > 0:
+                r[k + "_gbs"] = round(prof[k]["bytes"] / (prof[k]["ms"] / 1e3) / 1e9, 1)
+        res[loc] = r
+        del stt
+        torch.cuda.empty_cache()
+    out["sliced30_c64_g3"] = dict(res, workload="random 30 qubits depth 20, 3 global qubits (8 slices of 27), "
+                                                "staged segments; host = page-locked host slices streamed")
     return out
 
 

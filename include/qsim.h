@@ -131,6 +131,9 @@ QSIM_API int qsim_apply_named(qsim_state *s, int kind, const int *targets, int k
 /* ---------------------------------------------------------------- circuits */
 typedef struct qsim_circuit qsim_circuit;
 
+/* Circuits may name up to QSIM_CIRCUIT_MAX_QUBITS qubits; states, plans and
+ * the adjoint method take at most 34, wider circuits run on sliced states. */
+#define QSIM_CIRCUIT_MAX_QUBITS 48
 QSIM_API int qsim_circuit_create(int n, qsim_circuit **out);
 QSIM_API int qsim_circuit_destroy(qsim_circuit *c);
 /* Append a gate.  params: up to 4 doubles (angle, or the SU2 quaternion);
@@ -140,6 +143,11 @@ QSIM_API int qsim_circuit_destroy(qsim_circuit *c);
 QSIM_API int qsim_circuit_add(qsim_circuit *c, int kind, const int *targets, int k, const int *controls,
                      int nc, const double *params, int param_index, const double *matrix);
 QSIM_API int qsim_circuit_info(const qsim_circuit *c, int *n, int *ngates, int *nparams);
+/* Gate i as stored: kind, k targets, nc controls and its 2^k x 2^k matrix
+ * (row-major, interleaved re/im: 2 * 4^k doubles).  Any output may be NULL;
+ * targets/controls need room for k / nc entries. */
+QSIM_API int qsim_circuit_gate(const qsim_circuit *c, int i, int *kind, int *k, int *targets, int *nc,
+                               int *controls, double *matrix);
 /* Plain execution: one sweep per gate, in order (the unfused baseline). */
 QSIM_API int qsim_run(qsim_state *s, const qsim_circuit *c);
 
@@ -299,6 +307,72 @@ QSIM_API int qsim_batch_set_config(qsim_batch *b, int ctas_per_sm, int tile_qubi
 QSIM_API int qsim_batch_autotune(qsim_batch *b, void *cuda_stream, int reps, int *best_tile_qubits,
                                  int *best_ctas_per_sm, double *best_ms);
 
+/* ---------------------------------------------------------------- sliced states
+ * The multi-GPU scheme of Sec. 3.1 (its figure: one or several devices, the
+ * full state in host memory, slices copied to the GPU and processed in turn).
+ * An n-qubit state is split by its top g ("global") qubits into 2^g slices of
+ * L = n - g ("local") qubits; slice i holds the amplitudes whose top g bits
+ * equal i, in the usual order.  A gate whose targets are local acts on each
+ * slice alone; a control, or a diagonal target, on a global qubit only
+ * decides per slice what applies.  Every other gate on a global qubit is
+ * preceded by an exchange of that qubit with a local one (SWAP step): for
+ * global bit b and local position l, every slice pair (i, i | 1<<b) with bit b
+ * of i clear swaps the amplitudes of slice i whose bit l is 1 with those of
+ * slice i | 1<<b whose bit l is 0.  Afterwards the two qubits have traded
+ * positions; the plan keeps the map.
+ *
+ * qsim_slice_plan_build: n_global = g (0..QSIM_SLICE_MAX_GLOBAL, < n; L <= 34);
+ * each local segment gets a fusion plan (kmax, mode as qsim_plan_build) per
+ * distinct value of the global bits it reads.  restore_layout != 0 appends
+ * exchanges and local SWAP gates that return every qubit to its own position,
+ * so the slices end in the plain order; otherwise qsim_slice_plan_layout gives
+ * the final position of each qubit.  Host-side only (no device work). */
+typedef struct qsim_slice_plan qsim_slice_plan;
+#define QSIM_SLICE_MAX_GLOBAL 16
+#define QSIM_SLICE_SEGMENT 0
+#define QSIM_SLICE_SWAP 1
+#define QSIM_SLICES_DEVICE 0 /* slices[i] are device pointers              */
+#define QSIM_SLICES_HOST 1   /* slices[i] are page-locked host pointers    */
+QSIM_API int qsim_slice_plan_build(const qsim_circuit *c, int n_global, int kmax, int mode, int restore_layout,
+                                   qsim_slice_plan **out);
+QSIM_API int qsim_slice_plan_destroy(qsim_slice_plan *p);
+/* Counts (outputs may be NULL): global and local qubits, steps, SWAP steps,
+ * segment variants (fusion plans) in total. */
+QSIM_API int qsim_slice_plan_info(const qsim_slice_plan *p, int *n_global, int *n_local, int *nsteps, int *nswaps,
+                                  int *nvariants);
+/* Step i: type (QSIM_SLICE_SEGMENT / QSIM_SLICE_SWAP); for a SWAP the global
+ * bit b and local position l; for a SEGMENT the mask of global bits whose
+ * value selects the variant and the number of source gates it covers. */
+QSIM_API int qsim_slice_plan_step(const qsim_slice_plan *p, int i, int *type, int *global_bit, int *local_pos,
+                                  uint32_t *keymask, int *ngates);
+/* Final physical position of every logical qubit (n ints). */
+QSIM_API int qsim_slice_plan_layout(const qsim_slice_plan *p, int *pos);
+/* The local circuit that segment `step` applies to slice `slice` (a new
+ * circuit of L qubits, owned by the caller). */
+QSIM_API int qsim_slice_segment_circuit(const qsim_slice_plan *p, int step, uint32_t slice, qsim_circuit **out);
+/* Apply segment `step` to one slice held in `state` (an L-qubit state, e.g.
+ * borrowing the slice's device memory); asynchronous on the state's stream. */
+QSIM_API int qsim_slice_apply_segment(const qsim_slice_plan *p, int step, uint32_t slice, qsim_state *state);
+/* The SWAP step's data movement between two slices in device memory of this
+ * process: a = the slice with the global bit 0, b = its partner; both 2^n_local
+ * amplitudes of dtype; asynchronous on `stream`. */
+QSIM_API int qsim_slice_exchange(void *a, void *b, int n_local, int dtype, int local_pos, void *stream);
+/* For an exchange between processes: gather the 2^(n_local-1) amplitudes of a
+ * device slice whose bit local_pos equals `bit` into the contiguous device
+ * buffer `out` (pack), or scatter them back from `in` (unpack). */
+QSIM_API int qsim_slice_pack(const void *slice, int n_local, int dtype, int local_pos, int bit, void *out,
+                             void *stream);
+QSIM_API int qsim_slice_unpack(void *slice, int n_local, int dtype, int local_pos, int bit, const void *in,
+                               void *stream);
+/* Run every step on 2^g slices (each 2^L amplitudes of dtype, 256-byte
+ * aligned, distinct).  QSIM_SLICES_DEVICE: in place in device memory, on
+ * `stream`.  QSIM_SLICES_HOST: slices stay in page-locked host memory; each
+ * pass (a run of SWAP steps and the segment after it) streams groups of
+ * slices through two device staging buffers on two internal streams (the
+ * upload of one group overlaps the work on the other) and returns after the
+ * last download.  QSIM_ENOMEM when the staging buffers do not fit. */
+QSIM_API int qsim_slice_run(const qsim_slice_plan *p, int dtype, void *const *slices, int location, void *stream);
+
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each
  * launch is bracketed by CUDA events on its own stream; qsim_profile_get
@@ -311,7 +385,8 @@ QSIM_API int qsim_profile_reset(void);
 QSIM_API int qsim_profile_count(int *nkinds);
 QSIM_API int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total_ms,
                      double *total_bytes, double *total_flops);
-/* Total kernel launches issued by the library since load (always counted). */
+/* Total kernel launches issued by the library since load (always counted;
+ * host/device copies are not kernel launches and are not counted). */
 QSIM_API uint64_t qsim_launch_count(void);
 
 #ifdef __cplusplus

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
 C64, C128 = 0, 1
 FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
 INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE = 0, 1, 2, 3
+SLICE_SEGMENT, SLICE_SWAP = 0, 1
+SLICES_DEVICE, SLICES_HOST = 0, 1
 GATE_KIND = {"matrix": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "t": 6, "rx": 7, "ry": 8,
              "rz": 9, "phase": 10, "cz": 11, "swap": 12, "su2": 13}
 
@@ -53,6 +55,7 @@ _SIGS = {
     "qsim_circuit_destroy": ([P], I),
     "qsim_circuit_add": ([P, I, P, I, P, I, P, I, P], I),
     "qsim_circuit_info": ([P, P, P, P], I),
+    "qsim_circuit_gate": ([P, I, P, P, P, P, P, P], I),
     "qsim_run": ([P, P], I),
     "qsim_plan_build": ([P, I, I, P], I),
     "qsim_plan_destroy": ([P], I),
@@ -74,6 +77,17 @@ _SIGS = {
     "qsim_batch_run": ([P, P, P], I),
     "qsim_batch_set_config": ([P, I, I], I),
     "qsim_batch_autotune": ([P, P, I, P, P, P], I),
+    "qsim_slice_plan_build": ([P, I, I, I, I, P], I),
+    "qsim_slice_plan_destroy": ([P], I),
+    "qsim_slice_plan_info": ([P, P, P, P, P, P], I),
+    "qsim_slice_plan_step": ([P, I, P, P, P, P, P], I),
+    "qsim_slice_plan_layout": ([P, P], I),
+    "qsim_slice_segment_circuit": ([P, I, ctypes.c_uint32, P], I),
+    "qsim_slice_apply_segment": ([P, I, ctypes.c_uint32, P], I),
+    "qsim_slice_exchange": ([P, P, I, I, I, P], I),
+    "qsim_slice_pack": ([P, I, I, I, I, P, P], I),
+    "qsim_slice_unpack": ([P, I, I, I, I, P, P], I),
+    "qsim_slice_run": ([P, I, P, I, P], I),
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),
@@ -164,6 +178,24 @@ class QCircuit:
         return p.value
 
 
+def circuit_gates(handle) -> list:
+    """The gates stored in a library circuit, as ``inputs.Gate`` matrix gates."""
+    n, ng, npar = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().qsim_circuit_info(handle, ctypes.byref(n), ctypes.byref(ng), ctypes.byref(npar)))
+    out = []
+    for i in range(ng.value):
+        k, nc = ctypes.c_int(), ctypes.c_int()
+        _check(lib().qsim_circuit_gate(handle, i, None, ctypes.byref(k), None, ctypes.byref(nc), None, None))
+        t = np.zeros(max(1, k.value), dtype=np.int32)
+        c = np.zeros(max(1, nc.value), dtype=np.int32)
+        m = np.zeros(2 * (1 << (2 * k.value)), dtype=np.float64)
+        _check(lib().qsim_circuit_gate(handle, i, None, ctypes.byref(k), _p(t), ctypes.byref(nc), _p(c), _p(m)))
+        d = 1 << k.value
+        out.append(inputs.Gate("matrix", tuple(int(v) for v in t[: k.value]), tuple(int(v) for v in c[: nc.value]),
+                               (), -1, m.view(np.complex128).reshape(d, d).copy()))
+    return out
+
+
 class Plan:
     """A fusion plan (QSIM_FUSE_GREEDY2 / STAGED / TC) built on the host."""
 
@@ -211,6 +243,78 @@ class Plan:
         _check(lib().qsim_plan_block(self.handle, i, ctypes.byref(k), _p(t), _p(m)))
         d = 1 << k.value
         return tuple(int(v) for v in t[: k.value]), m.view(np.complex128).reshape(d, d)
+
+
+class SlicePlan:
+    """A sliced-state plan: SWAP steps and per-slice segment plans (qsim_slice_plan_build)."""
+
+    def __init__(self, circuit, n_global: int, kmax: int = 4, mode: int = FUSE_STAGED, restore: bool = True):
+        qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+        self.n, self.g, self.L = qc.n, n_global, qc.n - n_global
+        h = ctypes.c_void_p()
+        _check(lib().qsim_slice_plan_build(qc.handle, n_global, kmax, mode, int(restore), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsim_slice_plan_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> dict:
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(lib().qsim_slice_plan_info(self.handle, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("n_global", "n_local", "steps", "swaps", "variants"), (x.value for x in v)))
+
+    def steps(self) -> list:
+        out = []
+        for i in range(self.info()["steps"]):
+            t, b, l, ng = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            km = ctypes.c_uint32()
+            _check(lib().qsim_slice_plan_step(self.handle, i, ctypes.byref(t), ctypes.byref(b), ctypes.byref(l),
+                                              ctypes.byref(km), ctypes.byref(ng)))
+            if t.value == SLICE_SWAP:
+                out.append({"type": "swap", "global_bit": b.value, "local_pos": l.value})
+            else:
+                out.append({"type": "segment", "keymask": km.value, "gates": ng.value})
+        return out
+
+    def layout(self) -> list:
+        pos = np.zeros(self.n, dtype=np.int32)
+        _check(lib().qsim_slice_plan_layout(self.handle, _p(pos)))
+        return [int(v) for v in pos]
+
+    def segment_gates(self, step: int, slice_index: int) -> list:
+        h = ctypes.c_void_p()
+        _check(lib().qsim_slice_segment_circuit(self.handle, step, slice_index, ctypes.byref(h)))
+        try:
+            return circuit_gates(h)
+        finally:
+            lib().qsim_circuit_destroy(h)
+
+    def apply_segment(self, step: int, slice_index: int, state: "State"):
+        _check(lib().qsim_slice_apply_segment(self.handle, step, slice_index, state.handle))
+
+    def run(self, slices: Sequence, dtype: int, location: int, stream=None):
+        ptrs = (ctypes.c_void_p * len(slices))(*[t.data_ptr() for t in slices])
+        _check(lib().qsim_slice_run(self.handle, dtype, ptrs, location, _stream_ptr(stream)))
+
+
+def slice_exchange(a, b, n_local: int, local_pos: int, stream=None):
+    dt = C64 if str(a.dtype) == "torch.complex64" else C128
+    _check(lib().qsim_slice_exchange(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), n_local, dt,
+                                     local_pos, _stream_ptr(stream)))
+
+
+def slice_pack(slice_t, n_local: int, local_pos: int, bit: int, out, stream=None):
+    dt = C64 if str(slice_t.dtype) == "torch.complex64" else C128
+    _check(lib().qsim_slice_pack(ctypes.c_void_p(slice_t.data_ptr()), n_local, dt, local_pos, bit,
+                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+
+
+def slice_unpack(slice_t, n_local: int, local_pos: int, bit: int, src, stream=None):
+    dt = C64 if str(slice_t.dtype) == "torch.complex64" else C128
+    _check(lib().qsim_slice_unpack(ctypes.c_void_p(slice_t.data_ptr()), n_local, dt, local_pos, bit,
+                                   ctypes.c_void_p(src.data_ptr()), _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------------ state

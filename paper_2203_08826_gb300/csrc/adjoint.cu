@@ -514,6 +514,7 @@ extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, co
                                  double *energies, void *cuda_stream) {
     if (!c || !grads || nsets < 1 || (c->nparams > 0 && !params)) return set_error(QSIM_EINVAL, "bad arguments");
     if (dtype != QSIM_C64 && dtype != QSIM_C128) return set_error(QSIM_EINVAL, "bad dtype");
+    if (c->n > 34) return set_error(QSIM_EINVAL, "the adjoint method needs a state of at most 34 qubits");
     if (nterms < 1 || !xmask || !zmask || !coeff) return set_error(QSIM_EINVAL, "empty Hamiltonian");
     const uint64_t full = (uint64_t(1) << c->n) - 1;
     HParams hp;

@@ -37,7 +37,8 @@ static const char *k_names[K_NUM_KINDS] = {
     "init",          "sweep_dense1",  "sweep_densek", "sweep_diag",   "sweep_monomial",
     "probabilities", "marginal",      "reduce",       "expect_pauli", "sample_chunk",
     "sample_scan",   "sample_draw",   "stage",        "tc_block",     "batch",
-    "adjoint_step",  "hamiltonian_apply", "copy"};
+    "adjoint_step",  "hamiltonian_apply", "copy",  "slice_exchange", "slice_pack",
+    "copy_h2d",      "copy_d2h"};
 
 const char *kernel_name(int kind) { return (kind >= 0 && kind < K_NUM_KINDS) ? k_names[kind] : "?"; }
 
@@ -76,7 +77,7 @@ int prof_collect() {
 
 LaunchScope::LaunchScope(int kind_, cudaStream_t stream_, double bytes, double flops)
     : kind(kind_), stream(stream_), slot(-1) {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (kind_ != K_COPY && kind_ != K_H2D && kind_ != K_D2H) g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (g_used == g_slots.size()) {
@@ -411,8 +412,9 @@ static int apply_matrix(qsim_state *s, const std::vector<cd> &m, const int *targ
     QSIM_TRY(classify(m, targets, k, controls, c, op));
     if (op.type == Op::IDENTITY) return QSIM_OK;
     void *mat_dev = nullptr;
-    if (op.type == Op::DENSE && op.k >= 2) {
-        // dense multi-target matrices travel through the state's scratch
+    if (op.type == Op::DENSE && op.k >= 4) {
+        // dense matrices of 4+ targets travel through the state's scratch
+        // (smaller ones are kernel parameters)
         const size_t d = size_t(1) << op.k;
         const size_t eb = s->amp_bytes();
         QSIM_TRY(s->ensure_scratch(d * d * eb));
@@ -454,7 +456,8 @@ int qsim_apply_named(qsim_state *s, int kind, const int *targets, int k, const i
 // ------------------------------------------------------------------ circuits
 int qsim_circuit_create(int n, qsim_circuit **out) {
     if (!out) return set_error(QSIM_EINVAL, "out is NULL");
-    if (n < 1 || n > 34) return set_error(QSIM_EINVAL, "n=%d outside 1..34", n);
+    if (n < 1 || n > QSIM_CIRCUIT_MAX_QUBITS)
+        return set_error(QSIM_EINVAL, "n=%d outside 1..%d", n, QSIM_CIRCUIT_MAX_QUBITS);
     *out = new qsim_circuit();
     (*out)->n = n;
     return QSIM_OK;
@@ -488,6 +491,26 @@ int qsim_circuit_add(qsim_circuit *c, int kind, const int *targets, int k, const
     QSIM_TRY(gate_matrix(kind, k, g.params, matrix, g.m));
     c->gates.push_back(std::move(g));
     if (param_index >= c->nparams) c->nparams = param_index + 1;
+    return QSIM_OK;
+}
+
+int qsim_circuit_gate(const qsim_circuit *c, int i, int *kind, int *k, int *targets, int *nc, int *controls,
+                      double *matrix) {
+    if (!c) return set_error(QSIM_EINVAL, "circuit is NULL");
+    if (i < 0 || i >= int(c->gates.size())) return set_error(QSIM_EINVAL, "gate %d outside the circuit", i);
+    const GateRec &g = c->gates[size_t(i)];
+    if (kind) *kind = g.kind;
+    if (k) *k = g.k;
+    if (nc) *nc = g.nc;
+    if (targets)
+        for (int t = 0; t < g.k; ++t) targets[t] = g.targets[t];
+    if (controls)
+        for (int t = 0; t < g.nc; ++t) controls[t] = g.controls[t];
+    if (matrix)
+        for (size_t e = 0; e < g.m.size(); ++e) {
+            matrix[2 * e] = g.m[e].real();
+            matrix[2 * e + 1] = g.m[e].imag();
+        }
     return QSIM_OK;
 }
 

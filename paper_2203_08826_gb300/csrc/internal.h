@@ -48,13 +48,18 @@ enum KernelKind {
     K_BATCH,
     K_ADJ_STEP,
     K_HAPPLY,
-    K_COPY,
+    K_COPY,          // device-to-device copy (not a kernel)
+    K_SLICE_EXCHANGE,
+    K_SLICE_PACK,
+    K_H2D,           // host-to-device copy (not a kernel)
+    K_D2H,           // device-to-host copy (not a kernel)
     K_NUM_KINDS
 };
 const char *kernel_name(int kind);
 
-// RAII bracket around one launch: counts it and, when profiling is on,
-// records CUDA events on `stream` before and after.
+// RAII bracket around one launch: counts it (copies are not counted as
+// kernel launches) and, when profiling is on, records CUDA events on `stream`
+// before and after.
 struct LaunchScope {
     // bytes: algorithmic HBM bytes of the launch; flops: useful arithmetic
     LaunchScope(int kind, cudaStream_t stream, double bytes, double flops = 0.0);

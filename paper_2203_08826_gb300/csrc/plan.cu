@@ -185,6 +185,7 @@ int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out) 
     if (!c || !out) return set_error(QSIM_EINVAL, "NULL argument");
     *out = nullptr;
     if (kmax < 1 || kmax > QSIM_MAX_TARGETS) return set_error(QSIM_EINVAL, "kmax=%d outside 1..6", kmax);
+    if (c->n > 34) return set_error(QSIM_EINVAL, "plans act on states of at most 34 qubits (circuit has %d)", c->n);
     qsim_plan *p = new qsim_plan();
     p->n = c->n;
     p->mode = mode;

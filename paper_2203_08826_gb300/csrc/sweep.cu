@@ -113,6 +113,45 @@ __global__ void __launch_bounds__(256) k_dense1(typename CT<R>::T *__restrict__ 
     }
 }
 
+// ------------------------------------------------------------------ dense k = 2, 3
+// Register form for small blocks: each thread loads PER whole groups (2^K
+// amplitudes each at the target offsets), multiplies by G held in kernel
+// parameters and stores them back (Eq. (1) over the 2^K target values).
+template <typename R, int K> struct SmallDense {
+    typename CT<R>::T m[1 << (2 * K)];
+    uint64_t off[1 << K];
+};
+
+template <typename R, int K, int PER>
+__global__ void __launch_bounds__(256) k_dense_small(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
+                                                     IndexMap map, const __grid_constant__ SmallDense<R, K> G) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
+    C v[PER][D];
+    uint64_t idx[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t g = base + uint64_t(j) * blockDim.x;
+        idx[j] = g < ngroups ? expand_index(g, map) : ~uint64_t(0);
+        if (g < ngroups) {
+#pragma unroll
+            for (int r = 0; r < D; ++r) v[j][r] = psi[idx[j] | G.off[r]];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (idx[j] == ~uint64_t(0)) continue;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            C acc = cmul(G.m[r * D], v[j][0]);
+#pragma unroll
+            for (int c = 1; c < D; ++c) acc = cfma(G.m[r * D + c], v[j][c], acc);
+            psi[idx[j] | G.off[r]] = acc;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ dense k
 // CTA stages GPB groups of 2^K amplitudes in shared memory (coalesced loads:
 // consecutive threads take consecutive groups for the same matrix column),
@@ -237,6 +276,23 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 LaunchScope ls(K_DENSE1, st, bytes, 16.0 * double(ngroups << 1));
                 k_dense1<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, ngroups, map,
                                                                   uint64_t(1) << op.targets[0], m);
+            } else if (k <= 3) {
+                constexpr int T = 256;
+                const double flops = 8.0 * double(1 << k) * double(ngroups << k);
+                LaunchScope ls(K_DENSEK, st, bytes, flops);
+                if (k == 2) {
+                    SmallDense<R, 2> G{};
+                    for (int e = 0; e < 16; ++e) G.m[e] = to_c<R>(op.m[size_t(e)]);
+                    for (int j = 0; j < 4; ++j) G.off[j] = target_offset(j, op.targets, k);
+                    constexpr int PER = 2;
+                    k_dense_small<R, 2, PER><<<unsigned((ngroups + T * PER - 1) / (T * PER)), T, 0, st>>>(psi, ngroups,
+                                                                                                         map, G);
+                } else {
+                    SmallDense<R, 3> G{};
+                    for (int e = 0; e < 64; ++e) G.m[e] = to_c<R>(op.m[size_t(e)]);
+                    for (int j = 0; j < 8; ++j) G.off[j] = target_offset(j, op.targets, k);
+                    k_dense_small<R, 3, 1><<<unsigned((ngroups + T - 1) / T), T, 0, st>>>(psi, ngroups, map, G);
+                }
             } else {
                 if (!mat_dev) return set_error(QSIM_EINVAL, "dense k>1 needs the matrix on the device");
                 Offsets offs{};
