@@ -39,7 +39,13 @@ namespace qsim {
 namespace {
 
 constexpr int TC_M = 128;          // rows per tile (tcgen05 M)
-constexpr int TC_THREADS = 256;    // 8 warps: each TMEM lane quarter is read by two warps
+// warp roles: 4 epilogue warps (warp w reads TMEM lanes 32w..32w+31), one
+// MMA warp (also allocates TMEM), 8 producer warps
+constexpr int TC_EPI_WARPS = 4;
+constexpr int TC_MMA_WARP = 4;
+constexpr int TC_PROD_WARPS = 8;
+constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 1 + TC_PROD_WARPS);
+constexpr int TC_PROD_THREADS = 32 * TC_PROD_WARPS;
 constexpr int MAX_EPI = 48;        // epilogue diagonal ops per pass
 constexpr int MAX_EPI_POOL = 256;  // their complex entries
 constexpr unsigned long long WAIT_LIMIT = 1ull << 26;  // bounded mbarrier waits
@@ -61,8 +67,11 @@ struct TcParams {
     int *err;            // set to 1 when a bounded wait expires
     uint64_t ntiles;     // 2^(n-k) / 128
     int n;
-    int nepi;
+    int nepi;               // phase ops (evaluated per element)
+    int nneg;               // sign flips on a control subspace: row mask + column flip mask
     EpiOp epi[MAX_EPI];
+    uint64_t negr[MAX_EPI];  // bits of the row index R that must all be 1
+    uint64_t negc[MAX_EPI];  // bit c set: column c is negated (when the row bits hold)
     float2 pool[MAX_EPI_POOL];
 };
 
@@ -125,12 +134,19 @@ template <int K, int PREC>
 struct TcShape {
     static constexpr int KR = 2 << K;                   // reals per row (GEMM K and N)
     static constexpr int EB = Elem<PREC>::EB;
-    static constexpr int RAW = TC_M * KR * 4;           // bytes of one fp32 tile
     static constexpr int OPND = TC_M * KR * EB;         // bytes of one A split
     static constexpr int BOPND = KR * KR * EB;          // bytes of one B split
-    static constexpr int SMEM = RAW + 2 * OPND + 2 * BOPND + 1024 + 64;
-    static constexpr int TCOLS = KR < 32 ? 32 : KR;     // TMEM columns (power of 2 >= 32)
+    static constexpr int STAGES = 2;                    // A operand buffers (hi + lo each)
+    static constexpr int BAR_OFF = 2 * BOPND + STAGES * 2 * OPND;
+    static constexpr int EPI_OFF = BAR_OFF + 128;       // epilogue ops copied from the parameters
+    static constexpr int EPI_BYTES = 2 * MAX_EPI * 8 + MAX_EPI * int(sizeof(EpiOp)) + MAX_EPI_POOL * 8;
+    static constexpr int SMEM = EPI_OFF + EPI_BYTES + 1024;  // + alignment slack
+    static constexpr int TCOLS = 2 * KR < 32 ? 32 : 2 * KR;  // two accumulators (power of 2)
     static constexpr int KSTEP = 32 / EB;               // K elements per MMA
+    static constexpr int NV = TC_M * KR / 4;            // float4 per fp32 tile
+    static constexpr int PER = NV / TC_PROD_THREADS;    // float4 per producer thread
+    static_assert(SMEM <= 227 * 1024, "tensor-core tile does not fit shared memory");
+    static_assert(NV % TC_PROD_THREADS == 0, "tile not divisible among producers");
 };
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
@@ -148,193 +164,289 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// bulk copy global -> shared, completion counted in bytes on an mbarrier
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
+// Bounded wait that also gives up as soon as another role has given up
+// (*abort set); on its own expiry it sets *abort.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int *abort) {
+    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 31) == 31 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
 }
 
-// Persistent CTA: while the tensor cores and the epilogue work on tile t, the
-// bulk copy of tile t + gridDim.x is already in flight.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Every lane of a warp waits; the warp goes on only if all lanes saw the
+// phase complete, so its lanes never leave a loop in different iterations.
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
+    const bool ok = mbar_wait_ab(mbar, parity, abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Persistent, warp-specialised CTA (one per SM).  Tile i (rows of the
+// (2^(n-k) x 2^k) view, CTAs take every gridDim.x-th tile) moves through
+//   producers: global fp32 -> registers -> hi/lo split -> A stage i % 2
+//   MMA thread: A stage + B -> accumulator i % 2 in TMEM (3 products)
+//   epilogue:   accumulator -> diagonal epilogue ops -> rotated global store
+// with one mbarrier per hand-off and direction: full_a / empty_a per A stage
+// (producers -> MMA, MMA commit -> producers), full_acc / empty_acc per
+// accumulator (MMA commit -> epilogue, epilogue -> MMA).  Two of each let the
+// loads of tile i + 1 and the stores of tile i - 1 overlap the MMAs of tile i.
 template <int K, int PREC>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_block(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constant__ TcParams p) {
     using S = TcShape<K, PREC>;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-    unsigned char *a_hi = sm;                      // split operands (1024-aligned)
-    unsigned char *a_lo = sm + S::OPND;
-    unsigned char *b_hi = sm + 2 * S::OPND;
-    unsigned char *b_lo = b_hi + S::BOPND;
-    unsigned char *raw = b_lo + S::BOPND;          // fp32 tile landing buffer
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(raw + S::RAW);  // [0] MMA done, [1] tile loaded
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+    unsigned char *b_hi = sm;
+    unsigned char *b_lo = sm + S::BOPND;
+    auto a_hi = [&](int st) { return sm + 2 * S::BOPND + st * 2 * S::OPND; };
+    auto a_lo = [&](int st) { return sm + 2 * S::BOPND + st * 2 * S::OPND + S::OPND; };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + S::BAR_OFF);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 8);
+    volatile int *abort_f = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const uint32_t full_a0 = smem_u32(&bars[0]), empty_a0 = smem_u32(&bars[2]);
+    const uint32_t full_acc0 = smem_u32(&bars[4]), empty_acc0 = smem_u32(&bars[6]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t mb_mma = smem_u32(&mbar[0]), mb_load = smem_u32(&mbar[1]);
-    const uint32_t raw_s = smem_u32(raw);
 
+    uint64_t *s_negr = reinterpret_cast<uint64_t *>(sm + S::EPI_OFF);
+    uint64_t *s_negc = s_negr + MAX_EPI;
+    EpiOp *s_epi = reinterpret_cast<EpiOp *>(s_negc + MAX_EPI);
+    float2 *s_pool = reinterpret_cast<float2 *>(s_epi + MAX_EPI);
     {  // B (both splits): the host built the swizzled image
         const uint4 *src = p.bimg;
         uint4 *dst = reinterpret_cast<uint4 *>(b_hi);
         for (int i = tid; i < 2 * S::BOPND / 16; i += TC_THREADS) dst[i] = src[i];
+        for (int i = tid; i < p.nneg; i += TC_THREADS) {
+            s_negr[i] = p.negr[i];
+            s_negc[i] = p.negc[i];
+        }
+        for (int i = tid; i < p.nepi; i += TC_THREADS) s_epi[i] = p.epi[i];
+        for (int i = tid; i < MAX_EPI_POOL; i += TC_THREADS) s_pool[i] = p.pool[i];
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_load));
+        for (int st = 0; st < 2; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full_a0 + 8 * st), "r"(TC_PROD_WARPS));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_a0 + 8 * st));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_acc0 + 8 * st));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty_acc0 + 8 * st), "r"(TC_EPI_WARPS));
+        }
+        *abort_f = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == 0) {
+    if (warp == TC_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(S::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B image -> tensor core
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    uint32_t ph_mma = 0, ph_load = 0;
-    bool load_pending = false;
-    constexpr uint32_t IDESC = tc_idesc<PREC>(S::KR, TC_M);
     const int n = p.n;
-    const size_t tile_bytes = size_t(S::RAW);
+    const uint64_t my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    uint64_t tile = blockIdx.x;
-    if (tile < p.ntiles && tid == 0) bulk_load(raw_s, reinterpret_cast<const char *>(p.in) + tile * tile_bytes, S::RAW, mb_load);
-    load_pending = tile < p.ntiles;
-    bool failed = false;
-    for (; tile < p.ntiles; tile += gridDim.x) {
-        // ---- tile landed?
-        if (!__syncthreads_and(mbar_wait(mb_load, ph_load))) {
-            failed = true;
-            break;
-        }
-        ph_load ^= 1;
-        load_pending = false;
-        // ---- split the fp32 tile into the swizzled K-major operands
-        {
-            const float4 *src = reinterpret_cast<const float4 *>(raw);
-            constexpr int NV = TC_M * S::KR / 4;
-#pragma unroll 4
-            for (int i = tid; i < NV; i += TC_THREADS) {
-                const float4 v = src[i];
-                const int m = (i * 4) / S::KR, e = (i * 4) % S::KR;
+    if (warp > TC_MMA_WARP) {
+        // ---------------- producers
+        // Software-pipelined by half tiles: while one half of tile i is split
+        // into the operands, the same half of tile i + 1 is already loading.
+        const int pt = tid - 32 * (TC_MMA_WARP + 1);
+        constexpr int PH = S::PER / 2;
+        static_assert(S::PER % 2 == 0, "half tiles");
+        auto load_half = [&](float4 (&v)[PH], uint64_t i, int h) {
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            const float4 *src = reinterpret_cast<const float4 *>(p.in) + tile * uint64_t(S::NV);
+#pragma unroll
+            for (int j = 0; j < PH; ++j) v[j] = __ldcs(src + pt + (h * PH + j) * TC_PROD_THREADS);
+        };
+        auto convert_half = [&](const float4 (&v)[PH], int st, int h) {
+            unsigned char *ah = a_hi(st), *al = a_lo(st);
+#pragma unroll
+            for (int j = 0; j < PH; ++j) {
+                const int vi = pt + (h * PH + j) * TC_PROD_THREADS;
+                const int m = (vi * 4) / S::KR, e = (vi * 4) % S::KR;
                 if (PREC == TC_BF16X3) {
-                    uint16_t h[4], l[4];
-                    Elem<TC_BF16X3>::split(v.x, h[0], l[0]);
-                    Elem<TC_BF16X3>::split(v.y, h[1], l[1]);
-                    Elem<TC_BF16X3>::split(v.z, h[2], l[2]);
-                    Elem<TC_BF16X3>::split(v.w, h[3], l[3]);
+                    uint16_t hh[4], ll[4];
+                    Elem<TC_BF16X3>::split(v[j].x, hh[0], ll[0]);
+                    Elem<TC_BF16X3>::split(v[j].y, hh[1], ll[1]);
+                    Elem<TC_BF16X3>::split(v[j].z, hh[2], ll[2]);
+                    Elem<TC_BF16X3>::split(v[j].w, hh[3], ll[3]);
                     const uint32_t off = sw128_offset<2>(m, e, TC_M);
-                    *reinterpret_cast<uint2 *>(a_hi + off) = make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
-                    *reinterpret_cast<uint2 *>(a_lo + off) = make_uint2(l[0] | (uint32_t(l[1]) << 16), l[2] | (uint32_t(l[3]) << 16));
+                    *reinterpret_cast<uint2 *>(ah + off) =
+                        make_uint2(hh[0] | (uint32_t(hh[1]) << 16), hh[2] | (uint32_t(hh[3]) << 16));
+                    *reinterpret_cast<uint2 *>(al + off) =
+                        make_uint2(ll[0] | (uint32_t(ll[1]) << 16), ll[2] | (uint32_t(ll[3]) << 16));
                 } else {
-                    uint32_t h[4], l[4];
-                    Elem<TC_TF32X3>::split(v.x, h[0], l[0]);
-                    Elem<TC_TF32X3>::split(v.y, h[1], l[1]);
-                    Elem<TC_TF32X3>::split(v.z, h[2], l[2]);
-                    Elem<TC_TF32X3>::split(v.w, h[3], l[3]);
+                    uint32_t hh[4], ll[4];
+                    Elem<TC_TF32X3>::split(v[j].x, hh[0], ll[0]);
+                    Elem<TC_TF32X3>::split(v[j].y, hh[1], ll[1]);
+                    Elem<TC_TF32X3>::split(v[j].z, hh[2], ll[2]);
+                    Elem<TC_TF32X3>::split(v[j].w, hh[3], ll[3]);
                     const uint32_t off = sw128_offset<4>(m, e, TC_M);
-                    *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                    *reinterpret_cast<uint4 *>(ah + off) = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+                    *reinterpret_cast<uint4 *>(al + off) = make_uint4(ll[0], ll[1], ll[2], ll[3]);
                 }
             }
+        };
+        float4 v0[PH], v1[PH];
+        if (my_tiles > 0) {
+            load_half(v0, 0, 0);
+            load_half(v1, 0, 1);
         }
-        // generic-proxy writes -> visible to the tensor core (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            // the landing buffer is free again: fetch the next tile
-            const uint64_t next = tile + gridDim.x;
-            if (next < p.ntiles) {
-                bulk_load(raw_s, reinterpret_cast<const char *>(p.in) + next * tile_bytes, S::RAW, mb_load);
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-            constexpr int PER = 128 / S::EB;  // elements per 128-byte column block
-            int acc = 0;
-#pragma unroll
-            for (int pass = 0; pass < 3; ++pass) {
-                const uint32_t A = pass == 2 ? al : ah;
-                const uint32_t B = pass == 1 ? bl : bh;
-#pragma unroll
-                for (int ks = 0; ks < S::KR / S::KSTEP; ++ks) {
-                    const int e = ks * S::KSTEP;
-                    const uint32_t aoff = uint32_t(e / PER) * TC_M * 128 + uint32_t(e % PER) * S::EB;
-                    const uint32_t boff = uint32_t(e / PER) * S::KR * 128 + uint32_t(e % PER) * S::EB;
-                    const uint64_t ad = sw128_desc(A + aoff), bd = sw128_desc(B + boff);
-                    if (PREC == TC_BF16X3)
-                        asm volatile(
-                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                    else
-                        asm volatile(
-                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
-                    acc = 1;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma)
-                         : "memory");
+        for (uint64_t i = 0; i < my_tiles; ++i) {
+            const int st = int(i & 1);
+            const uint32_t u = uint32_t(i >> 1);
+            const bool more = i + 1 < my_tiles;
+            if (i >= 2 && !warp_wait(empty_a0 + 8 * st, (u - 1) & 1, abort_f)) break;
+            convert_half(v0, st, 0);
+            if (more) load_half(v0, i + 1, 0);
+            convert_half(v1, st, 1);
+            // generic-proxy writes -> visible to the tensor core (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full_a0 + 8 * st);
+            if (more) load_half(v1, i + 1, 1);
         }
-        load_pending = tile + gridDim.x < p.ntiles;
-        __syncwarp();
-        if (!__syncthreads_and(mbar_wait(mb_mma, ph_mma))) {
-            failed = true;
-            mbar_wait(mb_mma, ph_mma);  // bounded: let the MMAs in flight drain
-            break;
-        }
-        ph_mma ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: TMEM lane = row; warps w and w + 4 split the columns
-        const int q4 = warp & 3, half = warp >> 2;
-        const int m = q4 * 32 + lane;
-        const uint64_t R = tile * TC_M + m;  // row index = bits K.. of the current index
-        const uint32_t trow = tmem + (uint32_t(q4 * 32) << 16);
-        constexpr int CPW = S::KR / 2;  // columns per warp half
-#pragma unroll 1
-        for (int c0 = half * CPW; c0 < (half + 1) * CPW; c0 += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(trow + uint32_t(c0)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else if (warp == TC_MMA_WARP) {
+        // ---------------- MMA issue (one thread)
+        if (lane == 0) {
+            constexpr uint32_t IDESC = tc_idesc<PREC>(S::KR, TC_M);
+            constexpr int PERB = 128 / S::EB;  // elements per 128-byte column block
+            const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+            uint64_t issued = 0;
+            for (uint64_t i = 0; i < my_tiles; ++i) {
+                const int st = int(i & 1);
+                const uint32_t u = uint32_t(i >> 1);
+                if (!mbar_wait_ab(full_a0 + 8 * st, u & 1, abort_f)) break;
+                if (i >= 2 && !mbar_wait_ab(empty_acc0 + 8 * st, (u - 1) & 1, abort_f)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t ah = smem_u32(a_hi(st)), al = smem_u32(a_lo(st));
+                const uint32_t dacc = tmem + uint32_t(st * S::KR);
+                int acc = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = c0 / 2 + j;  // complex column = low K bits of the current index
-                float2 v = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-                const uint64_t x = (R << K) | uint64_t(c);
-                for (int e = 0; e < p.nepi; ++e) {
-                    const EpiOp &op = p.epi[e];
-                    if ((x & op.cmask) != op.cmask) continue;
-                    if (op.neg) {
-                        v.x = -v.x;
-                        v.y = -v.y;
-                        continue;
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t A = pass == 2 ? al : ah;
+                    const uint32_t B = pass == 1 ? bl : bh;
+#pragma unroll
+                    for (int ks = 0; ks < S::KR / S::KSTEP; ++ks) {
+                        const int e = ks * S::KSTEP;
+                        const uint32_t aoff = uint32_t(e / PERB) * TC_M * 128 + uint32_t(e % PERB) * S::EB;
+                        const uint32_t boff = uint32_t(e / PERB) * S::KR * 128 + uint32_t(e % PERB) * S::EB;
+                        const uint64_t ad = sw128_desc(A + aoff), bd = sw128_desc(B + boff);
+                        if (PREC == TC_BF16X3)
+                            asm volatile(
+                                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(dacc),
+                                "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                        else
+                            asm volatile(
+                                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(dacc),
+                                "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+                        acc = 1;
                     }
-                    int s = 0;
-                    for (int t = 0; t < op.k; ++t) s = (s << 1) | int((x >> op.sel[t]) & 1);
-                    const float2 f = p.pool[op.moff + s];
-                    v = make_float2(f.x * v.x - f.y * v.y, f.x * v.y + f.y * v.x);
                 }
-                p.out[(uint64_t(c) << (n - K)) | R] = v;
+                // completion frees the A stage and fills the accumulator
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 empty_a0 + 8 * st)
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 full_acc0 + 8 * st)
+                             : "memory");
+                issued = i + 1;
             }
+            // no MMA may be in flight at teardown: wait (bounded) for the last
+            // commit of each stage
+            for (uint64_t i = issued >= 2 ? issued - 2 : 0; i < issued; ++i)
+                mbar_wait(empty_a0 + 8 * int(i & 1), uint32_t(i >> 1) & 1);
         }
-        // the next tile reuses the operands and the accumulator
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: TMEM lane = row of the tile
+        const int m = warp * 32 + lane;
+        for (uint64_t i = 0; i < my_tiles; ++i) {
+            const uint64_t tile = blockIdx.x + i * gridDim.x;
+            const int st = int(i & 1);
+            const uint32_t u = uint32_t(i >> 1);
+            if (!warp_wait(full_acc0 + 8 * st, u & 1, abort_f)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t R = tile * TC_M + m;  // row index = bits K.. of the current index
+            const uint32_t trow = tmem + uint32_t(st * S::KR) + (uint32_t(warp * 32) << 16);
+            // sign flips: one 64-bit column mask per row
+            uint64_t flip = 0;
+            for (int e = 0; e < p.nneg; ++e)
+                if ((R & s_negr[e]) == s_negr[e]) flip ^= s_negc[e];
+            const int nph = p.nepi;
+#pragma unroll 1
+            for (int c0 = 0; c0 < S::KR; c0 += 16) {
+                uint32_t r[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                    : "r"(trow + uint32_t(c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = c0 / 2 + j;  // complex column = low K bits of the current index
+                    v[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+                    if ((flip >> c) & 1) {
+                        v[j].x = -v[j].x;
+                        v[j].y = -v[j].y;
+                    }
+                    if (nph) {
+                        const uint64_t x = (R << K) | uint64_t(c);
+                        for (int e = 0; e < nph; ++e) {
+                            const EpiOp &op = s_epi[e];
+                            if ((x & op.cmask) != op.cmask) continue;
+                            int s = 0;
+                            for (int t = 0; t < op.k; ++t) s = (s << 1) | int((x >> op.sel[t]) & 1);
+                            const float2 f = s_pool[op.moff + s];
+                            v[j] = make_float2(f.x * v[j].x - f.y * v[j].y, f.x * v[j].y + f.y * v[j].x);
+                        }
+                    }
+                }
+                // 16-byte stores of two consecutive rows: lanes 2m and 2m+1
+                // trade one value per column pair (c, c + 1); the even lane
+                // writes column c, the odd lane column c + 1, both at row 2m
+                const bool odd = lane & 1;
+                const uint64_t R0 = R & ~uint64_t(1);
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    const int c = c0 / 2 + j;
+                    const float2 send = odd ? v[j] : v[j + 1];
+                    float2 recv;
+                    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+                    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+                    const float4 w = odd ? make_float4(recv.x, recv.y, v[j + 1].x, v[j + 1].y)
+                                         : make_float4(v[j].x, v[j].y, recv.x, recv.y);
+                    const uint64_t col = uint64_t(odd ? c + 1 : c);
+                    __stcs(reinterpret_cast<float4 *>(&p.out[(col << (n - K)) | R0]), w);
+                }
+            }
+            // the accumulator may be overwritten by the MMAs of tile i + 2
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_acc0 + 8 * st);
+        }
     }
-    if (failed) {
-        if (tid == 0) atomicExch(p.err, 1);
-        if (load_pending) mbar_wait(mb_load, ph_load);  // bounded: the copy in flight lands first
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (tid == 0 && *abort_f) atomicExch(p.err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0)
+    if (warp == TC_MMA_WARP)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
@@ -578,13 +690,26 @@ int prepare_tc(qsim_plan &p, int n) {
         prm.ntiles = (uint64_t(1) << (n - ps.k)) / TC_M;
         int pool = 0;
         for (const TcPass::Diag &dg : ps.epi) {
-            EpiOp &e = prm.epi[prm.nepi++];
             auto cur = [&](int q) { return (q - ps.off + n) % n; };
-            e.cmask = 0;
-            for (int q : dg.controls) e.cmask |= uint64_t(1) << cur(q);
+            uint64_t cmask = 0;
+            for (int q : dg.controls) cmask |= uint64_t(1) << cur(q);
+            if (dg.targets.empty() && dg.d[0] == cd(-1.0)) {
+                // -1 on the control subspace: rows whose control bits are set
+                // negate the columns whose control bits are set
+                const uint64_t cm = cmask & ((uint64_t(1) << ps.k) - 1);
+                uint64_t cols = 0;
+                for (uint64_t c = 0; c < (uint64_t(1) << ps.k); ++c)
+                    if ((c & cm) == cm) cols |= uint64_t(1) << c;
+                prm.negr[prm.nneg] = cmask >> ps.k;
+                prm.negc[prm.nneg] = cols;
+                ++prm.nneg;
+                continue;
+            }
+            EpiOp &e = prm.epi[prm.nepi++];
+            e.cmask = cmask;
             e.k = int(dg.targets.size());
             for (int t = 0; t < e.k; ++t) e.sel[t] = cur(dg.targets[t]);
-            e.neg = (e.k == 0 && dg.d[0] == cd(-1.0)) ? 1 : 0;
+            e.neg = 0;
             e.moff = pool;
             if (pool + int(dg.d.size()) > MAX_EPI_POOL) return set_error(QSIM_EUNSUPPORTED, "epilogue pool overflow");
             for (const cd &v : dg.d) prm.pool[pool++] = make_float2(float(v.real()), float(v.imag()));
@@ -619,8 +744,7 @@ int launch_tc_k(const TcParams &prm, cudaStream_t st) {
                       "tc smem attribute");
         attr = true;
     }
-    const int per_sm = std::max(1, std::min(2, (227 * 1024) / smem));
-    const uint64_t want = uint64_t(sm_count_tc()) * per_sm;
+    const uint64_t want = uint64_t(sm_count_tc());
     const unsigned grid = unsigned(std::min<uint64_t>(want, prm.ntiles));
     // useful flops: a dense k-qubit block is 2^k complex multiply-adds per amplitude
     LaunchScope ls(K_TC_BLOCK, st, 2.0 * double(prm.ntiles) * TC_M * (2 << K) * 4.0,
@@ -650,7 +774,8 @@ int run_tc(qsim_state *s, qsim_plan &p) {
         const int k = tp.passes[i].k;
         int rc;
         if (tp.prec == TC_BF16X3) rc = k == 6 ? launch_tc_k<6, TC_BF16X3>(prm, s->stream) : launch_tc_k<5, TC_BF16X3>(prm, s->stream);
-        else rc = k == 6 ? launch_tc_k<6, TC_TF32X3>(prm, s->stream) : launch_tc_k<5, TC_TF32X3>(prm, s->stream);
+        else if (k == 5) rc = launch_tc_k<5, TC_TF32X3>(prm, s->stream);
+        else rc = set_error(QSIM_EUNSUPPORTED, "3xTF32 passes are 5 qubits wide");
         QSIM_TRY(rc);
         cur ^= 1;
     }
