@@ -103,6 +103,9 @@ def gate_matrix(g) -> np.ndarray:
         return np.array([[np.exp(-0.5j * p[0]), 0], [0, np.exp(0.5j * p[0])]], dtype=complex)
     if name == "phase":
         return np.array([[1, 0], [0, np.exp(1j * p[0])]], dtype=complex)
+    if name == "rzz":  # exp(-i theta Z (x) Z / 2)
+        even, odd = np.exp(-0.5j * p[0]), np.exp(0.5j * p[0])
+        return np.diag([even, odd, odd, even]).astype(complex)
     if name == "cz":
         return np.diag([1, 1, 1, -1]).astype(complex)
     if name == "swap":
@@ -223,6 +226,45 @@ def hamiltonian_apply(psi: np.ndarray, ham) -> np.ndarray:
     for xm, zm, c in zip(ham.xmask, ham.zmask, ham.coeff):
         out += float(c) * pauli_apply(psi, int(xm), int(zm))
     return out
+
+
+# ---------------------------------------------------------------- Sec. 3.3
+
+def pauli_phase(psi: np.ndarray, zmask: Sequence[int], coeff: Sequence[float], theta: float) -> np.ndarray:
+    """exp(-i theta D) psi for D = sum_t coeff[t] Z(zmask[t]), by definition:
+    D(x) = sum_t coeff[t] (-1)^popcount(x & zmask[t])."""
+    x = np.arange(psi.size, dtype=np.uint64)
+    d = np.zeros(psi.size)
+    for z, c in zip(zmask, coeff):
+        parity = np.array([bin(int(v)).count("1") & 1 for v in (x & np.uint64(z))])
+        d += float(c) * (1 - 2 * parity)
+    return psi * np.exp(-1j * theta * d)
+
+
+def dense_hamiltonian(n: int, ham) -> np.ndarray:
+    """The 2^n x 2^n matrix of a Pauli sum, column by column (n <= 12)."""
+    N = 1 << n
+    H = np.zeros((N, N), dtype=complex)
+    for j in range(N):
+        e = np.zeros(N, dtype=complex)
+        e[j] = 1.0
+        H[:, j] = hamiltonian_apply(e, ham)
+    return H
+
+
+def adiabatic_exact(n: int, H0, H1, T: float, dt: float) -> np.ndarray:
+    """Sec. 3.3's direct method: psi <- expm(-i H(s_k) dt) psi for each step,
+    H(s) = (1 - s) H0 + s H1 at the step's mid-point s_k = (k + 1/2) dt / T,
+    from the ground state of H0 = -sum X_i (|+...+>)."""
+    from scipy.linalg import expm
+    A = dense_hamiltonian(n, H0)
+    B = dense_hamiltonian(n, H1)
+    psi = np.full(1 << n, 2.0 ** (-n / 2), dtype=complex)
+    steps = int(round(T / dt))
+    for k in range(steps):
+        s = (k + 0.5) * dt / T
+        psi = expm(-1j * dt * ((1 - s) * A + s * B)) @ psi
+    return psi
 
 
 def energy(circuit, ham, theta: Sequence[float] | None = None) -> float:

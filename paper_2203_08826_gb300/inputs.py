@@ -28,9 +28,10 @@ import numpy as np
 #   cz (a, b)              diag(1, 1, 1, -1) on targets (a, b)
 #   swap (a, b)            exchange of two qubits
 #   su2 (a, b, c, d)       unit quaternion -> [[a+ib, c+id], [-c+id, a-ib]]
+#   rzz (theta)            exp(-i theta Z Z / 2) on targets (a, b)
 #   matrix                 explicit 2^k x 2^k complex matrix in ``matrix``
 GATE_NAMES = ("h", "x", "y", "z", "s", "t", "rx", "ry", "rz", "phase", "cz",
-              "swap", "su2", "matrix")
+              "swap", "su2", "rzz", "matrix")
 
 
 @dataclass(frozen=True)
@@ -199,6 +200,46 @@ def tfim(n: int, hx: float = 0.5) -> PauliSum:
     return PauliSum(np.concatenate([zz.xmask, x]),
                     np.concatenate([zz.zmask, np.zeros(n, dtype=np.uint64)]),
                     np.concatenate([zz.coeff, np.full(n, hx)]))
+
+
+def x_field(n: int) -> PauliSum:
+    """-sum_i X_i: the starting Hamiltonian of the adiabatic evolution
+    (Sec. 3.3; its ground state is |+...+>)."""
+    x = np.array([1 << i for i in range(n)], dtype=np.uint64)
+    return PauliSum(x, np.zeros(n, dtype=np.uint64), -np.ones(n))
+
+
+def tfim_target(n: int, h: float = 1.0) -> PauliSum:
+    """-sum_i (Z_i Z_{i+1} + h X_i), open chain: the target Hamiltonian of the
+    adiabatic evolution benchmark (Sec. 3.3)."""
+    t = tfim(n, h)
+    return PauliSum(t.xmask, t.zmask, -t.coeff)
+
+
+def adiabatic_schedule(T: float, dt: float) -> List[float]:
+    """Mid-step values s_k = (k + 1/2) dt / T of the linear schedule s(t) = t / T."""
+    steps = int(round(T / dt))
+    return [(k + 0.5) * dt / T for k in range(steps)]
+
+
+def adiabatic_tfim(n: int, h: float, T: float, dt: float) -> Circuit:
+    """Adiabatic evolution from -sum X_i to the TFIM target as a circuit
+    (Sec. 3.3: the Trotter decomposition turns the evolution into gates).
+
+    H(s) = (1 - s) H0 + s H1 = A(s) sum_i X_i + B(s) sum_i Z_i Z_{i+1} with
+    A = -((1 - s) + s h), B = -s.  Each step of length dt is the symmetric
+    (second-order) product exp(-i A dt/2 sum X) exp(-i B dt sum ZZ)
+    exp(-i A dt/2 sum X) at the step's mid-point s_k: RX(A dt) on every qubit,
+    RZZ(2 B dt) on every pair (i, i+1), RX(A dt) again.  The circuit starts
+    with H on every qubit (|0...0> -> |+...+>, the ground state of H0).
+    """
+    gates: List[Gate] = [Gate("h", (q,)) for q in range(n)]
+    for s in adiabatic_schedule(T, dt):
+        A, B = -((1.0 - s) + s * h), -s
+        gates += [Gate("rx", (q,), (), (A * dt,)) for q in range(n)]
+        gates += [Gate("rzz", (i, i + 1), (), (2.0 * B * dt,)) for i in range(n - 1)]
+        gates += [Gate("rx", (q,), (), (A * dt,)) for q in range(n)]
+    return Circuit(n, gates, f"adiabatic-tfim{n}")
 
 
 def random_pauli_sum(n: int, nterms: int, seed: int) -> PauliSum:

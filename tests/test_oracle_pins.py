@@ -376,3 +376,72 @@ def test_collapse_of_ghz_and_bell(orc):
         out, p = orc.collapse(st, qubits, o)
         assert abs(p - orc.probabilities(st, qubits)[o]) < 1e-14
         assert abs(np.linalg.norm(out) - 1) < 1e-14
+
+
+# ---------------------------------------------------------------- Sec. 3.3 evolution
+
+def _kron_z(n, zmask):
+    """Z on every qubit of zmask, identity elsewhere, by Kronecker products
+    (qubit n-1 leftmost, so qubit q is bit q of the index)."""
+    Z, I = np.diag([1.0, -1.0]), np.eye(2)
+    M = np.array([[1.0]])
+    for q in reversed(range(n)):
+        M = np.kron(M, Z if (zmask >> q) & 1 else I)
+    return M
+
+
+def test_rzz_is_the_exponential_of_zz(orc):
+    from scipy.linalg import expm
+    for th in (0.3, -1.7, 2 * np.pi / 3):
+        g = inputs.Gate("rzz", (0, 1), (), (th,))
+        np.testing.assert_allclose(orc.gate_matrix(g), expm(-0.5j * th * np.kron(np.diag([1, -1]), np.diag([1, -1]))),
+                                   atol=1e-14)
+
+
+def test_pauli_phase_matches_expm_of_kron_built_diagonal(orc):
+    from scipy.linalg import expm
+    n = 5
+    rng = np.random.default_rng(3)
+    psi = inputs.gaussian_state(n, seed=3)
+    for uniform in (True, False):
+        z = [int(v) for v in rng.integers(1, 1 << n, size=7)]
+        c = [0.8] * 7 if uniform else list(rng.standard_normal(7))
+        D = sum(ci * _kron_z(n, zi) for zi, ci in zip(z, c))
+        np.testing.assert_allclose(orc.pauli_phase(psi, z, c, 0.37), expm(-0.37j * D) @ psi, atol=1e-13)
+
+
+def test_dense_hamiltonian_matches_kron_sum(orc):
+    n = 4
+    X, Z, I = np.array([[0, 1], [1, 0]]), np.diag([1, -1]), np.eye(2)
+
+    def op(mats):
+        M = np.array([[1.0]])
+        for q in reversed(range(n)):
+            M = np.kron(M, mats.get(q, I))
+        return M
+    want = -sum(op({i: Z, i + 1: Z}) for i in range(n - 1)) - 0.7 * sum(op({i: X}) for i in range(n))
+    np.testing.assert_allclose(orc.dense_hamiltonian(n, inputs.tfim_target(n, 0.7)), want, atol=1e-14)
+
+
+def test_trotter_circuit_converges_to_exact_evolution_at_second_order(orc):
+    """The symmetric Trotter step has error O(dt^3) per step: halving dt over
+    a fixed time cuts the difference to the exact piecewise evolution 4x."""
+    n, h, T = 6, 1.0, 2.0
+    H0, H1 = inputs.x_field(n), inputs.tfim_target(n, h)
+    errs = []
+    for dt in (0.1, 0.05, 0.025):
+        got = orc.simulate(inputs.adiabatic_tfim(n, h, T, dt))
+        errs.append(np.max(np.abs(got - orc.adiabatic_exact(n, H0, H1, T, dt))))
+    assert errs[0] < 1e-2
+    for a, b in zip(errs, errs[1:]):
+        assert 3.6 < a / b < 4.4, errs
+
+
+def test_slow_adiabatic_sweep_reaches_the_tfim_ground_state(orc):
+    """Adiabatic theorem: a slow sweep ends near the ground energy of H1."""
+    n, h = 6, 1.0
+    H1 = inputs.tfim_target(n, h)
+    E0 = np.linalg.eigvalsh(orc.dense_hamiltonian(n, H1))[0]
+    e_fast = orc.expectation(orc.simulate(inputs.adiabatic_tfim(n, h, 2.0, 0.05)), H1)
+    e_slow = orc.expectation(orc.simulate(inputs.adiabatic_tfim(n, h, 20.0, 0.05)), H1)
+    assert E0 < e_slow < E0 + 2e-3 and e_slow < e_fast
