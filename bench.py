@@ -37,9 +37,15 @@ N_QUBITS, DEPTH = 30, 20  # --qubits overrides the width for small profiling run
 SHOTS = 1024
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per launch from ncu captures (dram__bytes_read.sum + write.sum),
-# scaled to a 30-qubit complex64 launch; see profiles/.  Entries are removed
-# whenever the kernel changes.
-NCU_TRAFFIC_30Q_C64 = {"sweep_dense1": 17.6e9}
+# scaled to a 30-qubit complex64 launch (each of these kernels reads and
+# writes the whole state once per launch, so traffic scales with 2^n); see
+# profiles/.  Entries are removed whenever the kernel changes.
+NCU_TRAFFIC_30Q_C64 = {
+    "sweep_dense1": 17.6e9,   # 30-qubit capture
+    "stage": 16.70e9,         # 27-qubit capture (2.087 GB) x 8
+    "tc_block": 16.73e9,      # 27-qubit capture (2.091 GB) x 8
+    "sweep_densek": 19.61e9,  # 2-qubit blocks, 27-qubit capture (2.451 GB) x 8
+}
 
 
 def peaks():
@@ -198,7 +204,12 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz):
+def traffic_of(name, n_qubits, amp_bytes):
+    t = NCU_TRAFFIC_30Q_C64.get(name)
+    return None if t is None else t * 2.0 ** (n_qubits - 30) * amp_bytes / 8
+
+
+def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_bytes=8):
     """Roofline object for the kernel with the largest share of device time."""
     if not prof:
         return None
@@ -214,12 +225,12 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz):
         tf = d["flops"] / d["launches"] / (avg_ms / 1e3) / 1e12
         pk = fp32_peak_tflops(sm_max_mhz)
         r = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
-             "frac": round(tf / pk, 4), "traffic": NCU_TRAFFIC_30Q_C64.get(name),
+             "frac": round(tf / pk, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
              "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
     else:
         r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_gbs, "unit": "GB/s",
-             "frac": round(gbs / peak_gbs, 4), "traffic": NCU_TRAFFIC_30Q_C64.get(name),
+             "frac": round(gbs / peak_gbs, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
              "peak_source": peak_src}
     r.update(common)
     return r
@@ -258,11 +269,12 @@ def run_qsim(args, ws, rank, local):
         if name == "tc" and args.dtype != "c64":
             continue
         try:
-            plans[name] = q.Plan(qc, kmax=PLAN_KMAX[name], mode=mode)
+            k = args.kmax if (args.kmax and name == args.mode) else PLAN_KMAX[name]
+            plans[name] = q.Plan(qc, kmax=k, mode=mode)
         except q.QsimError:
             pass
     chosen = args.mode
-    kmax_chosen = PLAN_KMAX.get(chosen, 0)
+    kmax_chosen = (args.kmax or PLAN_KMAX.get(chosen, 0)) if chosen != "auto" else 0
     tune = None
     if chosen == "auto":
         # the library's autotuner times its candidate plans on this state (not in the timed region)
@@ -313,7 +325,8 @@ def run_qsim(args, ws, rank, local):
     clocks = clk.summary()
     value = ngates * args.steps * ws / (ms / 1e3)
     peak, peak_src = peaks()
-    roof = roofline_of(prof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0)
+    ab = 8 if args.dtype == "c64" else 16
+    roof = roofline_of(prof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0, n, ab)
 
     # ---- the same circuit through the other execution modes
     others = {}
@@ -324,7 +337,8 @@ def run_qsim(args, ws, rank, local):
             oms, ol, oprof = timed(lambda: step(other), 1, 1, profile=True)
             others[other] = {"s_per_circuit": oms / 1e3, "gates_per_s": ngates / (oms / 1e3), "launches": ol,
                              "sweeps": plans[other].info()["sweeps"] if other in plans else ngates,
-                             "roofline": roofline_of(oprof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0)}
+                             "roofline": roofline_of(oprof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0,
+                                                     n, ab)}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -466,7 +480,7 @@ def other_workloads(q, torch, peak, peak_src):
         p = q.Plan(qc, kmax=k, mode=mode)
         ms, prof = ev_time(lambda: s.run_fused(p), 1, 1, profile=True)
         res[label] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3), "sweeps": p.info()["sweeps"],
-                      "roofline": roofline_of(prof, peak, peak_src, 2070.0)}
+                      "roofline": roofline_of(prof, peak, peak_src, 2070.0, 32, 8)}
     out["variational32_c64"] = res
     del s
     torch.cuda.empty_cache()
@@ -499,6 +513,26 @@ def other_workloads(q, torch, peak, peak_src):
     out["adjoint24_c64"] = {"s_per_parameter_set": dt, "gradients_per_s": c.nparams / dt,
                             "workload": "24 qubits, 10 layers RY/RZ + CZ ladder, 480 parameters, "
                                         "H = sum(Z_i Z_i+1 + 0.5 X_i), 64 parameter sets"}
+    # adiabatic evolution (Sec. 3.3): -sum X -> TFIM target, 30 qubits, second-order Trotter circuit
+    c = inputs.adiabatic_tfim(30, 1.0, 2.0, 0.05)
+    qc = q.QCircuit(c)
+    s = q.State(30, "c64").init_zero()
+    tuned = q.Plan.autotune(qc, s, reps=1)
+    ms_f, prof = ev_time(lambda: s.run_fused(tuned), 1, 2, profile=True)
+    e_final = s.expectation(inputs.tfim_target(30, 1.0))
+    ms_p, _ = ev_time(lambda: s.run(qc), 0, 1)
+    nsteps = len(inputs.adiabatic_schedule(2.0, 0.05))
+    out["adiabatic_tfim30_c64"] = {
+        "fused": {"s_per_evolution": ms_f / 1e3, "s_per_trotter_step": ms_f / 1e3 / nsteps,
+                  "gates_per_s": len(c) / (ms_f / 1e3),
+                  "mode": {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc"}[tuned.mode],
+                  "kmax": tuned.kmax, "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
+        "plain": {"s_per_evolution": ms_p / 1e3, "gates_per_s": len(c) / (ms_p / 1e3)},
+        "final_energy": e_final,
+        "workload": f"30 qubits, H(s) = (1-s)(-sum X) + s(-sum(ZZ + X)), T = 2, dt = 0.05 ({nsteps} symmetric "
+                    f"Trotter steps, {len(c)} gates), |+...+> start"}
+    del s, tuned
+    torch.cuda.empty_cache()
     # sliced states (Sec. 3.1 multi-GPU scheme): 30-qubit random circuit, 8 slices
     from paper_2203_08826_gb300 import sliced
     c = inputs.random_circuit(30, DEPTH, seed=2022)
@@ -533,6 +567,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--kmax", type=int, default=0,
+                    help="fusion width for a fixed --mode (0 = the default of that mode); pins the plan for profiling")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--quick", action="store_true",
                     help="headline mode only (no other modes, end-to-end or CPU legs): for profiling runs")
