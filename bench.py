@@ -279,12 +279,14 @@ def run_qsim(args, ws, rank, local):
     if chosen == "auto":
         # the library's autotuner times its candidate plans on this state (not in the timed region)
         t0 = time.perf_counter()
-        tuned = q.Plan.autotune(qc, state, reps=1)
+        tuned = q.Plan.autotune(qc, state, reps=1, max_err=args.max_err)
         chosen = {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc"}[tuned.mode]
         kmax_chosen = tuned.kmax
         plans[chosen] = tuned
         tune = {"mode": chosen, "kmax": tuned.kmax, "ms_per_circuit": tuned.tuned_ms,
-                "autotune_s": time.perf_counter() - t0}
+                "autotune_s": time.perf_counter() - t0, "max_err": args.max_err,
+                "table": [{k: (round(v, 9) if isinstance(v, float) else v) for k, v in e.items()}
+                          for e in tuned.table]}
 
     def step(mode_name):
         state.init_zero()
@@ -481,6 +483,12 @@ def other_workloads(q, torch, peak, peak_src):
         ms, prof = ev_time(lambda: s.run_fused(p), 1, 1, profile=True)
         res[label] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3), "sweeps": p.info()["sweeps"],
                       "roofline": roofline_of(prof, peak, peak_src, 2070.0, 32, 8)}
+    tuned = q.Plan.autotune(qc, s, reps=1, max_err=1e-5)
+    res["autotune"] = {"max_err": 1e-5, "chosen": {"mode": tuned.table and
+                                                    {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged",
+                                                     q.FUSE_TC: "tc"}[tuned.mode], "kmax": tuned.kmax},
+                       "table": tuned.table}
+    del tuned
     out["variational32_c64"] = res
     del s
     torch.cuda.empty_cache()
@@ -517,7 +525,7 @@ def other_workloads(q, torch, peak, peak_src):
     c = inputs.adiabatic_tfim(30, 1.0, 2.0, 0.05)
     qc = q.QCircuit(c)
     s = q.State(30, "c64").init_zero()
-    tuned = q.Plan.autotune(qc, s, reps=1)
+    tuned = q.Plan.autotune(qc, s, reps=1, max_err=1e-5)
     ms_f, prof = ev_time(lambda: s.run_fused(tuned), 1, 2, profile=True)
     e_final = s.expectation(inputs.tfim_target(30, 1.0))
     ms_p, _ = ev_time(lambda: s.run(qc), 0, 1)
@@ -526,7 +534,8 @@ def other_workloads(q, torch, peak, peak_src):
         "fused": {"s_per_evolution": ms_f / 1e3, "s_per_trotter_step": ms_f / 1e3 / nsteps,
                   "gates_per_s": len(c) / (ms_f / 1e3),
                   "mode": {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc"}[tuned.mode],
-                  "kmax": tuned.kmax, "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
+                  "kmax": tuned.kmax, "autotune_table": tuned.table,
+                  "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
         "plain": {"s_per_evolution": ms_p / 1e3, "gates_per_s": len(c) / (ms_p / 1e3)},
         "final_energy": e_final,
         "workload": f"30 qubits, H(s) = (1-s)(-sum X) + s(-sum(ZZ + X)), T = 2, dt = 0.05 ({nsteps} symmetric "
@@ -567,6 +576,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--max-err", type=float, default=1e-5,
+                    help="autotuner bound on the 2-norm difference from the FP32 staged plan's result")
     ap.add_argument("--kmax", type=int, default=0,
                     help="fusion width for a fixed --mode (0 = the default of that mode); pins the plan for profiling")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")

@@ -64,6 +64,8 @@ extern "C" {
  *   CZ                 diag(1, 1, 1, -1) on two targets
  *   SWAP               exchange of two targets
  *   SU2 (a, b, c, d)   [[a + ib, c + id], [-c + id, a - ib]] (unit quaternion)
+ *   RZZ (theta)        exp(-i theta Z Z / 2) on two targets: the two-qubit
+ *                      factor of a Trotter step of the TFIM (Sec. 3.3)
  *   MATRIX             explicit matrix given by the caller                     */
 enum {
     QSIM_GATE_MATRIX = 0,
@@ -79,7 +81,8 @@ enum {
     QSIM_GATE_PHASE = 10,
     QSIM_GATE_CZ = 11,
     QSIM_GATE_SWAP = 12,
-    QSIM_GATE_SU2 = 13
+    QSIM_GATE_SU2 = 13,
+    QSIM_GATE_RZZ = 14
 };
 
 QSIM_API const char *qsim_last_error(void);
@@ -198,6 +201,28 @@ QSIM_API int qsim_plan_describe(const qsim_plan *p, char *buf, size_t len);
  * per run.  Synchronous. */
 QSIM_API int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
                                 int *kmax_out, double *ms_out);
+/* Autotuner with a measured error/speed table (mixed-precision refinement of
+ * the fused blocks: FP32 register stages vs BF16x3 vs 3xTF32 tensor-core
+ * blocks).  Every candidate runs from |0...0> once; its error is the
+ * difference of that result from the first candidate's (the FP32 staged
+ * plan, kmax 3): err = ||psi - psi_ref||_2 (relative to ||psi|| = 1) and
+ * max_abs = max_x |psi(x) - psi_ref(x)|.  The fastest candidate with
+ * err <= max_err is kept (max_err <= 0: no bound, and errors are measured only
+ * when table_cap > 0).  Errors need one extra state-sized device buffer; when
+ * it cannot be allocated they are reported as -1, and with max_err > 0 no
+ * candidate qualifies (QSIM_EUNSUPPORTED).  The reference is the first
+ * candidate that runs.  table
+ * (may be NULL when table_cap = 0) receives one entry per candidate, in
+ * order; ms < 0 marks a candidate that could not run. */
+typedef struct qsim_tune_entry {
+    int mode;       /* QSIM_FUSE_* */
+    int kmax;
+    double ms;      /* time per circuit, CUDA events */
+    double err;     /* 2-norm of the difference from the reference plan's result */
+    double max_abs; /* largest amplitude difference */
+} qsim_tune_entry;
+QSIM_API int qsim_plan_autotune_ex(const qsim_circuit *c, qsim_state *scratch, int reps, double max_err,
+                                   qsim_plan **out, qsim_tune_entry *table, int table_cap, int *table_len);
 /* Execute a plan on a state of the circuit's width and precision. */
 QSIM_API int qsim_apply_fused(qsim_state *s, const qsim_plan *p);
 
@@ -306,6 +331,17 @@ QSIM_API int qsim_batch_set_config(qsim_batch *b, int ctas_per_sm, int tile_qubi
  * fastest as the batch's configuration and reports it (outputs may be NULL). */
 QSIM_API int qsim_batch_autotune(qsim_batch *b, void *cuda_stream, int reps, int *best_tile_qubits,
                                  int *best_ctas_per_sm, double *best_ms);
+
+/* ---------------------------------------------------------------- evolution
+ * psi <- exp(-i theta D) psi for the diagonal Pauli sum
+ * D = sum_t coeff[t] Z(zmask[t]) (Z on every qubit set in zmask[t]): the
+ * diagonal factor of a Trotter step of time evolution (Sec. 3.3, the
+ * adiabatic evolution benchmark, whose Trotter decomposition turns the
+ * evolution into a circuit; for the TFIM the Z_i Z_{i+1} terms form this
+ * factor).  One sweep over the state; 0 <= nterms <= 128; asynchronous on the
+ * state's stream. */
+QSIM_API int qsim_apply_pauli_phase(qsim_state *s, int nterms, const uint64_t *zmask, const double *coeff,
+                                    double theta);
 
 /* ---------------------------------------------------------------- sliced states
  * The multi-GPU scheme of Sec. 3.1 (its figure: one or several devices, the

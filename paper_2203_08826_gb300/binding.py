@@ -26,7 +26,7 @@ INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE = 0, 1, 2, 3
 SLICE_SEGMENT, SLICE_SWAP = 0, 1
 SLICES_DEVICE, SLICES_HOST = 0, 1
 GATE_KIND = {"matrix": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "t": 6, "rx": 7, "ry": 8,
-             "rz": 9, "phase": 10, "cz": 11, "swap": 12, "su2": 13}
+             "rz": 9, "phase": 10, "cz": 11, "swap": 12, "su2": 13, "rzz": 14}
 
 
 class QsimError(RuntimeError):
@@ -64,6 +64,7 @@ _SIGS = {
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
     "qsim_apply_fused": ([P, P], I),
     "qsim_plan_autotune": ([P, P, I, P, P, P, P], I),
+    "qsim_plan_autotune_ex": ([P, P, I, D, P, P, I, P], I),
     "qsim_probabilities": ([P, P, I, P, I], I),
     "qsim_norm2": ([P, P], I),
     "qsim_sample": ([P, U64, U64, U64, P, I], I),
@@ -77,6 +78,7 @@ _SIGS = {
     "qsim_batch_run": ([P, P, P], I),
     "qsim_batch_set_config": ([P, I, I], I),
     "qsim_batch_autotune": ([P, P, I, P, P, P], I),
+    "qsim_apply_pauli_phase": ([P, I, P, P, D], I),
     "qsim_slice_plan_build": ([P, I, I, I, I, P], I),
     "qsim_slice_plan_destroy": ([P], I),
     "qsim_slice_plan_info": ([P, P, P, P, P, P], I),
@@ -196,6 +198,11 @@ def circuit_gates(handle) -> list:
     return out
 
 
+class _TuneEntry(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("kmax", ctypes.c_int), ("ms", ctypes.c_double), ("err", ctypes.c_double),
+                ("max_abs", ctypes.c_double)]
+
+
 class Plan:
     """A fusion plan (QSIM_FUSE_GREEDY2 / STAGED / TC) built on the host."""
 
@@ -213,9 +220,32 @@ class Plan:
             self.handle = None
 
     @classmethod
-    def autotune(cls, circuit, scratch_state: "State", reps: int = 1) -> "Plan":
-        """Fastest plan for `circuit`, timed on `scratch_state` (overwritten)."""
+    def autotune(cls, circuit, scratch_state: "State", reps: int = 1, max_err: float | None = None) -> "Plan":
+        """Fastest plan for `circuit`, timed on `scratch_state` (overwritten).
+
+        With `max_err`, every candidate's error against the FP32 staged plan
+        is measured (qsim_plan_autotune_ex) and only plans within it qualify;
+        the measured table is kept in `.table`."""
         qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
+        if max_err is not None:
+            tab = (_TuneEntry * 8)()
+            nt = ctypes.c_int()
+            h = ctypes.c_void_p()
+            _check(lib().qsim_plan_autotune_ex(qc.handle, scratch_state.handle, reps, float(max_err),
+                                               ctypes.byref(h), tab, 8, ctypes.byref(nt)))
+            self = cls.__new__(cls)
+            info = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            self.n, self.handle = qc.n, h
+            _check(lib().qsim_plan_info(h, *[ctypes.byref(x) for x in info]))
+            self.mode = info[2].value
+            names = {FUSE_GREEDY2: "greedy2", FUSE_STAGED: "staged", FUSE_TC: "tc"}
+            self.table = [{"mode": names.get(e.mode, e.mode), "kmax": e.kmax, "ms": e.ms, "err": e.err,
+                           "max_abs": e.max_abs} for e in tab[: nt.value]]
+            ok = [e for e in self.table if e["ms"] >= 0 and 0 <= e["err"] <= max_err]
+            best = min(ok, key=lambda e: e["ms"]) if ok else None
+            self.kmax = best["kmax"] if best else 0
+            self.tuned_ms = best["ms"] if best else -1.0
+            return self
         h = ctypes.c_void_p()
         mode, kmax, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(lib().qsim_plan_autotune(qc.handle, scratch_state.handle, reps, ctypes.byref(h),
@@ -431,6 +461,12 @@ class State:
         p = ctypes.c_double()
         _check(lib().qsim_collapse(self.handle, _p(q), len(q), outcome, ctypes.byref(p)))
         return p.value
+
+    def apply_pauli_phase(self, zmask, coeff, theta: float):
+        """psi <- exp(-i theta sum_t coeff[t] Z(zmask[t])) psi (one sweep)."""
+        zm, c = _arr(zmask, np.uint64), _arr(coeff, np.float64)
+        _check(lib().qsim_apply_pauli_phase(self.handle, len(c), _p(zm), _p(c), float(theta)))
+        return self
 
     def expectation(self, ham: inputs.PauliSum) -> float:
         xm, zm, c = _arr(ham.xmask, np.uint64), _arr(ham.zmask, np.uint64), _arr(ham.coeff, np.float64)

@@ -38,7 +38,7 @@ static const char *k_names[K_NUM_KINDS] = {
     "probabilities", "marginal",      "reduce",       "expect_pauli", "sample_chunk",
     "sample_scan",   "sample_draw",   "stage",        "tc_block",     "batch",
     "adjoint_step",  "hamiltonian_apply", "copy",  "slice_exchange", "slice_pack",
-    "copy_h2d",      "copy_d2h"};
+    "copy_h2d",      "copy_d2h",     "pauli_phase"};
 
 const char *kernel_name(int kind) { return (kind >= 0 && kind < K_NUM_KINDS) ? k_names[kind] : "?"; }
 
@@ -182,6 +182,16 @@ int gate_matrix(int kind, int k, const double *p, const double *matrix, std::vec
             QSIM_TRY(need(1, 1));
             out = {1.0, 0.0, 0.0, std::polar(1.0, p[0])};
             return QSIM_OK;
+        case QSIM_GATE_RZZ: {  // exp(-i theta Z Z / 2): phase -theta/2 on even parity, +theta/2 on odd
+            QSIM_TRY(need(2, 1));
+            const cd e = std::polar(1.0, -p[0] / 2), o = std::polar(1.0, p[0] / 2);
+            out.assign(16, 0.0);
+            out[0] = e;
+            out[5] = o;
+            out[10] = o;
+            out[15] = e;
+            return QSIM_OK;
+        }
         case QSIM_GATE_CZ:
             QSIM_TRY(need(2, 0));
             out.assign(16, 0.0);
@@ -480,7 +490,7 @@ int qsim_circuit_add(qsim_circuit *c, int kind, const int *targets, int k, const
     for (int i = 0; i < nc; ++i) g.controls[i] = controls[i];
     const int np = kind == QSIM_GATE_SU2 ? 4
                    : (kind == QSIM_GATE_RX || kind == QSIM_GATE_RY || kind == QSIM_GATE_RZ ||
-                      kind == QSIM_GATE_PHASE)
+                      kind == QSIM_GATE_PHASE || kind == QSIM_GATE_RZZ)
                        ? 1
                        : 0;
     for (int i = 0; i < np; ++i) g.params[i] = params ? params[i] : 0.0;

@@ -53,6 +53,7 @@ enum KernelKind {
     K_SLICE_PACK,
     K_H2D,           // host-to-device copy (not a kernel)
     K_D2H,           // device-to-host copy (not a kernel)
+    K_PAULI_PHASE,
     K_NUM_KINDS
 };
 const char *kernel_name(int kind);
@@ -115,6 +116,9 @@ size_t marginal_scratch_doubles(int n, int m);
 int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result,
                  cudaStream_t st);
 size_t reduce_partials_needed(int n);
+// result[0] = sum |a - b|^2, result[1] = max |a - b|^2 (partials: 2 x reduce_partials_needed)
+int launch_diff_norm2(const void *a, const void *b, int n, int dtype, double *partials, double *result,
+                      cudaStream_t st);
 int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t *xmask,
                   const uint64_t *zmask, const double *coeff, double *partials,
                   size_t npartials, double *result, cudaStream_t st);

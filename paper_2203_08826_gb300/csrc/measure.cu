@@ -51,6 +51,24 @@ __device__ double block_sum(double v) {
     return v;
 }
 
+// Block-wide maximum of non-negative values, result valid in thread 0.
+__device__ double block_max(double v) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = 0;
+    if (w == 0) {
+        v = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
 // ------------------------------------------------------------------ probabilities
 template <typename C>
 __global__ void k_probs(const C *__restrict__ psi, uint64_t N, double *__restrict__ out) {
@@ -198,6 +216,26 @@ __global__ void __launch_bounds__(256) k_norm2(const C *__restrict__ psi, uint64
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// Squared 2-norm and largest modulus of a - b (double), per block.
+template <typename C>
+__global__ void __launch_bounds__(256) k_diff2(const C *__restrict__ a, const C *__restrict__ b, uint64_t N,
+                                               double *__restrict__ partials, double *__restrict__ maxes) {
+    double acc = 0, mx = 0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double dx = double(a[i].x) - double(b[i].x), dy = double(a[i].y) - double(b[i].y);
+        const double d2 = dx * dx + dy * dy;
+        acc += d2;
+        mx = fmax(mx, d2);
+    }
+    acc = block_sum(acc);
+    mx = block_max(mx);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        maxes[blockIdx.x] = mx;
+    }
+}
+
 // result (+)= sum of partials, in a fixed order (one block)
 __global__ void k_sum_partials(const double *__restrict__ partials, int np, double *__restrict__ result,
                                int accumulate) {
@@ -205,6 +243,34 @@ __global__ void k_sum_partials(const double *__restrict__ partials, int np, doub
     for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
     acc = block_sum(acc);
     if (threadIdx.x == 0) *result = accumulate ? *result + acc : acc;
+}
+
+__global__ void k_max_partials(const double *__restrict__ partials, int np, double *__restrict__ result) {
+    double mx = 0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) mx = fmax(mx, partials[i]);
+    mx = block_max(mx);
+    if (threadIdx.x == 0) *result = mx;
+}
+
+int launch_diff_norm2(const void *a, const void *b, int n, int dtype, double *partials, double *result,
+                      cudaStream_t st) {
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = reduce_blocks(), T = 256;
+    {
+        LaunchScope ls(K_REDUCE, st, 2.0 * double(N) * (dtype == QSIM_C64 ? 8 : 16));
+        if (dtype == QSIM_C64)
+            k_diff2<<<blocks, T, 0, st>>>(static_cast<const float2 *>(a), static_cast<const float2 *>(b), N, partials,
+                                          partials + blocks);
+        else
+            k_diff2<<<blocks, T, 0, st>>>(static_cast<const double2 *>(a), static_cast<const double2 *>(b), N,
+                                          partials, partials + blocks);
+        QSIM_CUDA_TRY(cudaGetLastError(), "difference launch");
+    }
+    LaunchScope ls(K_REDUCE, st, blocks * 16.0);
+    k_sum_partials<<<1, 256, 0, st>>>(partials, blocks, result, 0);
+    k_max_partials<<<1, 256, 0, st>>>(partials + blocks, blocks, result + 1);
+    QSIM_CUDA_TRY(cudaGetLastError(), "difference sum launch");
+    return QSIM_OK;
 }
 
 int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result, cudaStream_t st) {

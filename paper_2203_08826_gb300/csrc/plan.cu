@@ -255,17 +255,24 @@ int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *mat
     return QSIM_OK;
 }
 
-int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
-                       int *kmax_out, double *ms_out) {
+// Candidates: complex64 — staged tiles (FP32 on the CUDA cores) and
+// tensor-core blocks (BF16x3, 3xTF32); complex128 (FP64-bound) — staged
+// tiles against one sweep per gate (greedy fusion limited to 1 qubit).  Each
+// runs once from |0...0> (warm-up, and the state whose error is measured
+// when max_err > 0), then `reps` timed times.  The error of a plan is the
+// difference of its |0...0> result from the first candidate's (staged,
+// kmax 3: the plan with the fewest rounding steps per gate).
+static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double max_err, qsim_plan **out,
+                         qsim_tune_entry *table, int table_cap, int *table_len) {
     if (!c || !s || !out) return set_error(QSIM_EINVAL, "NULL argument");
     if (c->n != s->n) return set_error(QSIM_EINVAL, "circuit has %d qubits, state %d", c->n, s->n);
+    if (table_cap > 0 && !table) return set_error(QSIM_EINVAL, "table is NULL");
     *out = nullptr;
+    if (table_len) *table_len = 0;
     if (reps < 1) reps = 1;
     struct Cand {
         int mode, kmax;
     };
-    // complex64: staged tiles and tensor-core blocks; complex128 (FP64-bound):
-    // staged tiles against one sweep per gate (greedy fusion limited to 1 qubit)
     std::vector<Cand> cands = {{QSIM_FUSE_STAGED, 3}, {QSIM_FUSE_STAGED, 4}};
     if (s->dtype == QSIM_C64) {
         cands.push_back({QSIM_FUSE_TC, 6});
@@ -273,48 +280,94 @@ int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan
     } else {
         cands.push_back({QSIM_FUSE_GREEDY2, 1});
     }
+    const bool measure = max_err > 0 || table_cap > 0;
+    const size_t bytes = s->size() * s->amp_bytes();
+    void *ref = nullptr;
+    bool have_ref = false;
+    if (measure && cudaMalloc(&ref, bytes) != cudaSuccess) {
+        cudaGetLastError();  // not enough memory for the reference copy: errors are not measured
+        ref = nullptr;
+    }
+    struct RefGuard {
+        void *p;
+        ~RefGuard() {
+            if (p) cudaFree(p);
+        }
+    } rg{ref};
+    const size_t np = reduce_partials_needed(s->n);
     cudaEvent_t e0, e1;
     QSIM_CUDA_TRY(cudaEventCreate(&e0), "event");
     QSIM_CUDA_TRY(cudaEventCreate(&e1), "event");
     qsim_plan *best = nullptr;
     float best_ms = 1e30f;
-    Cand bc{0, 0};
+    int nt = 0;
     for (const Cand &cd_ : cands) {
+        qsim_tune_entry ent{cd_.mode, cd_.kmax, -1.0, -1.0, -1.0};
         qsim_plan *p = nullptr;
-        if (qsim_plan_build(c, cd_.kmax, cd_.mode, &p) != QSIM_OK) continue;  // e.g. too narrow for a tile
-        // the state is scratch: time the plan from |0...0> after one warm-up run
-        if (qsim_state_init(s, QSIM_INIT_ZERO, 0, nullptr) != QSIM_OK || qsim_apply_fused(s, p) != QSIM_OK) {
-            qsim_plan_destroy(p);
-            continue;
+        bool ok = qsim_plan_build(c, cd_.kmax, cd_.mode, &p) == QSIM_OK;  // e.g. too narrow for a tile
+        ok = ok && qsim_state_init(s, QSIM_INIT_ZERO, 0, nullptr) == QSIM_OK && qsim_apply_fused(s, p) == QSIM_OK;
+        if (ok && ref) {
+            if (!have_ref) {
+                ok = cudaMemcpyAsync(ref, s->amps, bytes, cudaMemcpyDeviceToDevice, s->stream) == cudaSuccess;
+                have_ref = ok;
+                ent.err = ent.max_abs = 0.0;
+            } else if (s->ensure_scratch((2 * np + 2) * sizeof(double)) == QSIM_OK) {
+                double *part = static_cast<double *>(s->scratch);
+                double host[2] = {0, 0};
+                ok = launch_diff_norm2(s->amps, ref, s->n, s->dtype, part, part + 2 * np, s->stream) == QSIM_OK &&
+                     cudaMemcpyAsync(host, part + 2 * np, sizeof host, cudaMemcpyDeviceToHost, s->stream) ==
+                         cudaSuccess &&
+                     cudaStreamSynchronize(s->stream) == cudaSuccess;
+                ent.err = std::sqrt(host[0]);
+                ent.max_abs = std::sqrt(host[1]);
+            }
         }
-        cudaEventRecord(e0, s->stream);
-        int rc = QSIM_OK;
-        for (int r = 0; r < reps && rc == QSIM_OK; ++r) rc = qsim_apply_fused(s, p);
-        cudaEventRecord(e1, s->stream);
-        if (rc != QSIM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-            qsim_plan_destroy(p);
-            continue;
+        if (ok) {
+            cudaEventRecord(e0, s->stream);
+            int rc = QSIM_OK;
+            for (int r = 0; r < reps && rc == QSIM_OK; ++r) rc = qsim_apply_fused(s, p);
+            cudaEventRecord(e1, s->stream);
+            ok = rc == QSIM_OK && cudaEventSynchronize(e1) == cudaSuccess;
         }
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        if (ms < best_ms) {
+        if (ok) {
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            ent.ms = ms;
+        }
+        if (nt < table_cap) table[nt] = ent;
+        ++nt;
+        // within the bound: the error was measured and is small enough, or no bound
+        const bool accurate = max_err <= 0 || (ent.err >= 0 && ent.err <= max_err);
+        if (ok && accurate && ms < best_ms) {
             if (best) qsim_plan_destroy(best);
             best = p;
             best_ms = ms;
-            bc = cd_;
-        } else {
+        } else if (p) {
             qsim_plan_destroy(p);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!best) return set_error(QSIM_EUNSUPPORTED, "no fusion plan could run this circuit");
+    if (table_len) *table_len = std::min(nt, table_cap);
+    if (!best) return set_error(QSIM_EUNSUPPORTED, "no fusion plan could run this circuit within the bound");
+    best->tuned_ms = best_ms;
     *out = best;
-    if (mode_out) *mode_out = best->mode;
-    if (kmax_out) *kmax_out = bc.kmax;
-    if (ms_out) *ms_out = best_ms;
     return QSIM_OK;
+}
+
+int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
+                       int *kmax_out, double *ms_out) {
+    QSIM_TRY(autotune_impl(c, s, reps, 0.0, out, nullptr, 0, nullptr));
+    if (mode_out) *mode_out = (*out)->mode;
+    if (kmax_out) *kmax_out = (*out)->kmax;
+    if (ms_out) *ms_out = (*out)->tuned_ms;
+    return QSIM_OK;
+}
+
+int qsim_plan_autotune_ex(const qsim_circuit *c, qsim_state *s, int reps, double max_err, qsim_plan **out,
+                          qsim_tune_entry *table, int table_cap, int *table_len) {
+    return autotune_impl(c, s, reps, max_err, out, table, table_cap, table_len);
 }
 
 int qsim_apply_fused(qsim_state *s, const qsim_plan *pc) {

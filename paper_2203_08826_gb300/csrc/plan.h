@@ -56,6 +56,7 @@ struct qsim_plan {
     int mode = 0;
     int kmax = 2;
     int ngates = 0;
+    double tuned_ms = -1.0;  // autotuned plans: time per run measured by the autotuner
     std::vector<qsim::Block> blocks;  // GREEDY2 and TC block lists
     qsim::PlanDev dev[2];
     qsim::StagedPlan *staged = nullptr;

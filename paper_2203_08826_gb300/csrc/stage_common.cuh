@@ -304,25 +304,44 @@ if (mask & (1 << J)) {                                                          
                 if ((j & rneed) == rneed) v[j] = cmul(f, v[j]);
         }
     } else {  // SOP_DIAG with selector qubits
-        int sel_t = 0, regsel[QSIM_MAX_TARGETS];
+        // selector bits from the thread's base index (lane / warp / tile
+        // qubits), then per register index j the bits its register qubits add
         const int k = op.k;
+        int sel_t = 0;
         for (int t = 0; t < k; ++t) {
             const int code = op.dq[t];
-            const int sh = k - 1 - t;
-            if (code >= POS_BASE) {
-                sel_t |= int((base >> (code - POS_BASE)) & 1) << sh;
-                regsel[t] = 0;
-            } else {
-                regsel[t] = code - POS_REG + 1;  // register bit + 1
-            }
+            if (code >= POS_BASE) sel_t |= int((base >> (code - POS_BASE)) & 1) << (k - 1 - t);
         }
+        const uint32_t pk = uint32_t(uint8_t(op.a)) | (uint32_t(uint8_t(op.b)) << 8);
+        int rm[REG_BITS];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            if ((j & rneed) != rneed) continue;
-            int sel = sel_t;
-            for (int t = 0; t < k; ++t)
-                if (regsel[t]) sel |= ((j >> (regsel[t] - 1)) & 1) << (k - 1 - t);
-            v[j] = cmul(src.pool(op.moff + sel), v[j]);
+        for (int r = 0; r < REG_BITS; ++r) {
+            const int f = int(pk >> (4 * r)) & 15;
+            rm[r] = f ? 1 << (f - 1) : 0;
+        }
+        if (k <= 2) {
+            const C f0 = src.pool(op.moff), f1 = src.pool(op.moff + 1);
+            const C f2 = k == 2 ? src.pool(op.moff + 2) : f0, f3 = k == 2 ? src.pool(op.moff + 3) : f1;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if ((j & rneed) != rneed) continue;
+                int sel = sel_t;
+#pragma unroll
+                for (int r = 0; r < REG_BITS; ++r)
+                    if ((j >> r) & 1) sel |= rm[r];
+                const C f = (sel & 2) ? ((sel & 1) ? f3 : f2) : ((sel & 1) ? f1 : f0);
+                v[j] = cmul(f, v[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                if ((j & rneed) != rneed) continue;
+                int sel = sel_t;
+#pragma unroll
+                for (int r = 0; r < REG_BITS; ++r)
+                    if ((j >> r) & 1) sel |= rm[r];
+                v[j] = cmul(src.pool(op.moff + sel), v[j]);
+            }
         }
     }
 }

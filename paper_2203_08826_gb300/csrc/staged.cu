@@ -259,11 +259,17 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
             so.type = SOP_DIAG;
             so.k = int8_t(g.op.k);
             split_controls(g.op, so);
+            // register selector bits: nibble r of (b:a) holds 1 + the selector
+            // bit that register bit r feeds (0: none)
+            uint32_t pk = 0;
             for (int t = 0; t < g.op.k; ++t) {
                 const int q = g.op.targets[t];
                 const int b = reg_bit(q);
                 so.dq[t] = int8_t(b >= 0 ? POS_REG + b : POS_BASE + q);
+                if (b >= 0) pk |= uint32_t(g.op.k - t) << (4 * b);
             }
+            so.a = int8_t(pk & 0xFF);
+            so.b = int8_t((pk >> 8) & 0xFF);
             if (g.op.k == 0 && g.op.m[0] == cd(-1.0)) so.flags = 1;
             so.moff = add_pool(g.op.m);
             st.ops.push_back(so);

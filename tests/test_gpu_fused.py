@@ -149,3 +149,27 @@ def test_plan_autotuner_picks_a_correct_plan(q, orc, dtype):
     s.run_fused(plan)
     err = np.max(np.abs(s.to_host().astype(np.complex128) - orc.simulate(circ, psi0)))
     assert err <= TOL[dtype]
+
+
+def test_autotuner_error_table_and_bound(q, orc):
+    """qsim_plan_autotune_ex: every candidate's error against the FP32 staged
+    plan; a tight bound keeps only the reference plan, a loose one the
+    fastest; the kept plan matches the oracle."""
+    circ = inputs.random_circuit(18, 6, seed=13)
+    want = orc.simulate(circ)
+    s = q.State(18, "c64")
+    tight = q.Plan.autotune(circ, s, reps=1, max_err=1e-12)
+    tab = tight.table
+    assert [e["mode"] for e in tab] == ["staged", "staged", "tc", "tc"]
+    assert tab[0]["err"] == 0.0 and all(e["ms"] > 0 for e in tab)
+    for e in tab[2:]:
+        assert 0 < e["err"] < 1e-3 and 0 < e["max_abs"] <= e["err"]
+    assert tight.mode == q.FUSE_STAGED
+    assert any(e["mode"] == "staged" and e["kmax"] == tight.kmax and e["err"] <= 1e-12 for e in tab)
+    loose = q.Plan.autotune(circ, s, reps=1, max_err=1.0)
+    fastest = min(loose.table, key=lambda e: e["ms"])
+    assert loose.kmax == fastest["kmax"]
+    for p in (tight, loose):
+        s2 = q.State(18, "c64").init_zero()
+        s2.run_fused(p)
+        assert np.max(np.abs(s2.to_host() - want)) <= 1e-5
