@@ -530,6 +530,10 @@ def other_workloads(q, torch, peak, peak_src):
     e_final = s.expectation(inputs.tfim_target(30, 1.0))
     ms_p, _ = ev_time(lambda: s.run(qc), 0, 1)
     nsteps = len(inputs.adiabatic_schedule(2.0, 0.05))
+    # the whole ZZ layer of one step as a single diagonal sweep
+    zz = inputs.zz_chain(30)
+    ms_z, zprof = ev_time(lambda: s.apply_pauli_phase(zz.zmask, zz.coeff, 0.05), 2, 10, profile=True)
+    zroof = roofline_of(zprof, peak, peak_src, 2070.0, 30, 8)
     out["adiabatic_tfim30_c64"] = {
         "fused": {"s_per_evolution": ms_f / 1e3, "s_per_trotter_step": ms_f / 1e3 / nsteps,
                   "gates_per_s": len(c) / (ms_f / 1e3),
@@ -537,6 +541,7 @@ def other_workloads(q, torch, peak, peak_src):
                   "kmax": tuned.kmax, "autotune_table": tuned.table,
                   "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
         "plain": {"s_per_evolution": ms_p / 1e3, "gates_per_s": len(c) / (ms_p / 1e3)},
+        "zz_layer_phase_sweep": {"ms": ms_z, "terms": len(zz), "roofline": zroof},
         "final_energy": e_final,
         "workload": f"30 qubits, H(s) = (1-s)(-sum X) + s(-sum(ZZ + X)), T = 2, dt = 0.05 ({nsteps} symmetric "
                     f"Trotter steps, {len(c)} gates), |+...+> start"}
