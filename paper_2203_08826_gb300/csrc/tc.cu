@@ -454,6 +454,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constan
 
 // ------------------------------------------------------------------ plan
 struct TcPass {
+    bool plain = false;          // a gate no window can hold, applied by a plain sweep
+    Op op;                       // plain: the classified gate (original qubits)
     int k = 6;
     int off = 0;                 // original qubit held by bit 0 of the current index
     std::vector<cd> block;       // 2^k x 2^k on the window (index bit i = qubit off + i)
@@ -508,11 +510,12 @@ int build_tc(const qsim_circuit &c, qsim_plan &p) {
     p.tc = tp;
     tp->prec = kw == 6 ? TC_BF16X3 : TC_TF32X3;
     // classify gates
-    std::vector<Op> ops(c.gates.size());
+    std::vector<Op> ops(c.gates.size()), orig(c.gates.size());
     std::vector<bool> diag(c.gates.size());
     for (size_t i = 0; i < c.gates.size(); ++i) {
         const GateRec &g = c.gates[i];
         QSIM_TRY(classify(g.m, g.targets, g.k, g.controls, g.nc, ops[i]));
+        orig[i] = ops[i];
         diag[i] = ops[i].type == Op::DIAG || ops[i].type == Op::IDENTITY;
         if (ops[i].type == Op::MONO) {
             const size_t d = size_t(1) << ops[i].k;
@@ -523,10 +526,47 @@ int build_tc(const qsim_circuit &c, qsim_plan &p) {
     }
     std::vector<int> remaining(c.gates.size());
     for (size_t i = 0; i < remaining.size(); ++i) remaining[i] = int(i);
+    // does a gate fit one of the windows the planner will visit from offset
+    // `from` on (offsets from + t k mod n)?
+    auto fits_orbit = [&](const Op &op, int from, int k) {
+        uint64_t q = 0;
+        for (int t = 0; t < op.k; ++t) q |= uint64_t(1) << op.targets[t];
+        for (int t = 0; t < op.c; ++t) q |= uint64_t(1) << op.controls[t];
+        int o = from;
+        for (int t = 0; t < n; ++t) {
+            uint64_t w = 0;
+            for (int i = 0; i < k; ++i) w |= uint64_t(1) << ((o + i) % n);
+            if ((q & ~w) == 0) return true;
+            o = (o + k) % n;
+        }
+        return false;
+    };
     int off = 0, rotated = 0;
     int stall = 0;
     while (!remaining.empty()) {
         const int k = kw;
+        {
+            // the earliest pending gate fits no window (a SWAP or a 2- or
+            // 3-qubit gate on distant qubits): one plain sweep, here, on the
+            // current index order; the gates already taken past it act on
+            // other qubits
+            const int g0 = remaining.front();
+            const Op &o0 = ops[g0];
+            if (!diag[g0] && !fits_orbit(o0, off, k)) {
+                const Op &og = orig[g0];
+                if (og.type == Op::DENSE && og.k > 3)
+                    return set_error(QSIM_EUNSUPPORTED, "tensor-core planner: a %d-qubit gate spans more than %d qubits",
+                                     og.k, k);
+                TcPass ps;
+                ps.plain = true;
+                ps.op = og;
+                ps.off = off;
+                ps.ngates = 1;
+                tp->passes.push_back(std::move(ps));
+                remaining.erase(remaining.begin());
+                continue;
+            }
+        }
         TcPass ps;
         ps.k = k;
         ps.off = off;
@@ -598,7 +638,12 @@ int build_tc(const qsim_circuit &c, qsim_plan &p) {
             rest.push_back(gi);
         }
         stall = ps.ngates ? 0 : stall + 1;
-        if (stall > 2 * n) return set_error(QSIM_EUNSUPPORTED, "tensor-core planner: a gate wider than %d qubits", k);
+        if (stall > 2 * n) {
+            const Op &o = ops[remaining.front()];
+            return set_error(QSIM_EUNSUPPORTED,
+                             "tensor-core planner: gate %d (%d targets, %d controls, first qubit %d) fits no %d-qubit window",
+                             remaining.front(), o.k, o.c, o.k ? o.targets[0] : o.controls[0], k);
+        }
         tp->passes.push_back(std::move(ps));
         remaining.swap(rest);
         off = (off + k) % n;
@@ -679,6 +724,13 @@ int prepare_tc(qsim_plan &p, int n) {
     tp.dev.boff.clear();
     tp.dev.params.clear();
     for (const TcPass &ps : tp.passes) {
+        if (ps.plain) {  // no tensor-core work: placeholders keep the indices aligned
+            tp.dev.boff.push_back(0);
+            TcParams prm;
+            memset(&prm, 0, sizeof prm);
+            tp.dev.params.push_back(prm);
+            continue;
+        }
         if (tp.prec == TC_BF16X3) build_bimage<2>(ps.block, ps.k, img, tp.prec);
         else build_bimage<4>(ps.block, ps.k, img, tp.prec);
         tp.dev.boff.push_back(all.size());
@@ -766,6 +818,15 @@ int run_tc(qsim_state *s, qsim_plan &p) {
     float2 *bufs[2] = {static_cast<float2 *>(s->amps), static_cast<float2 *>(s->scratch)};
     int cur = 0;
     for (size_t i = 0; i < tp.passes.size(); ++i) {
+        if (tp.passes[i].plain) {
+            // in place on the current buffer, qubits moved to their current bits
+            Op op = tp.passes[i].op;
+            const int off = tp.passes[i].off, n = s->n;
+            for (int t = 0; t < op.k; ++t) op.targets[t] = (op.targets[t] - off + n) % n;
+            for (int t = 0; t < op.c; ++t) op.controls[t] = (op.controls[t] - off + n) % n;
+            QSIM_TRY(launch_op(bufs[cur], n, QSIM_C64, op, s->stream, nullptr));
+            continue;
+        }
         TcParams prm = tp.dev.params[i];
         prm.in = bufs[cur];
         prm.out = bufs[cur ^ 1];
@@ -803,6 +864,12 @@ void tc_describe(const qsim_plan &p, std::string &out) {
     out += buf;
     for (size_t i = 0; i < p.tc->passes.size(); ++i) {
         const TcPass &ps = p.tc->passes[i];
+        if (ps.plain) {
+            snprintf(buf, sizeof buf, "  %3zu plain sweep: %d-target gate (kind %d) on the rotated index\n", i, ps.op.k,
+                     int(ps.op.type));
+            out += buf;
+            continue;
+        }
         snprintf(buf, sizeof buf, "  %3zu k=%d qubits %d..%d (mod n) gates=%d epilogue=%zu\n", i, ps.k, ps.off,
                  ps.off + ps.k - 1, ps.ngates, ps.epi.size());
         out += buf;

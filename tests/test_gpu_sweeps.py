@@ -241,3 +241,19 @@ def test_collapse(q, orc, dtype):
     s = new_state(q, 4, dtype)
     with pytest.raises(q.QsimError):
         s.collapse((1,), 1)  # |0000>: outcome 1 has probability 0
+
+
+@pytest.mark.parametrize("dtype,rate", [("c128", 0.9999), ("c64", 0.999)])
+def test_sampler_end_to_end_match_rate(q, orc, dtype, rate):
+    """Shots from the GPU state and from the independently simulated oracle
+    state, same seed and counters: they differ only where a draw falls within
+    rounding of a CDF boundary (complex64 rounds the amplitudes)."""
+    n = 16
+    circ = inputs.random_circuit(n, 6, seed=77)
+    s = new_state(q, n, dtype)
+    s.run(circ)
+    shots = 200000
+    got = s.sample(shots, seed=99, counter0=5)
+    want = orc.sample(orc.probabilities(orc.simulate(circ)), shots, seed=99, counter0=5)
+    match = float(np.mean(got == want))
+    assert match >= rate, f"match rate {match:.6f}"
