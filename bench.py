@@ -220,7 +220,7 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_byt
     common = {"kernel": name, "avg_launch_ms": avg_ms, "launch_share": round(share, 4),
               "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
               "flops_per_launch": d.get("flops", 0.0) / d["launches"]}
-    if name == "stage":
+    if name in ("stage", "batch"):
         # register-tile interpreter: bound by the FP32 pipe / issue, not HBM
         tf = d["flops"] / d["launches"] / (avg_ms / 1e3) / 1e12
         pk = fp32_peak_tflops(sm_max_mhz)
@@ -503,9 +503,11 @@ def other_workloads(q, torch, peak, peak_src):
     with torch.cuda.graph(g):
         b.run(o)
     ms, _ = ev_time(g.replay, 3, 5)
+    _, bprof = ev_time(lambda: b.run(o), 1, 2, profile=True)
     upd = sum((1 << cc.n) * len(cc.gates) for cc in circs)
     out["batch4096_c64"] = {"s_per_batch": ms / 1e3, "circuits_per_s": len(circs) / (ms / 1e3),
                             "amp_gate_updates_per_s": upd / (ms / 1e3), "config": cfg,
+                            "roofline": roofline_of(bprof, peak, peak_src, 2070.0, 30, 8),
                             "workload": "4096 variational circuits, n ~ U{12..20}, 4..12 layers, <sum Z_i Z_i+1>"}
     del b, g
     torch.cuda.empty_cache()

@@ -409,6 +409,14 @@ QSIM_API int qsim_slice_unpack(void *slice, int n_local, int dtype, int local_po
  * last download.  QSIM_ENOMEM when the staging buffers do not fit. */
 QSIM_API int qsim_slice_run(const qsim_slice_plan *p, int dtype, void *const *slices, int location, void *stream);
 
+/* ---------------------------------------------------------------- test support
+ * The sampler's integer weight of a complex64 amplitude, evaluated on the
+ * host by the same source the device runs: floor(p * 2^62) for
+ * p = re^2 + im^2 rounded once to double (the inverse-CDF weights
+ * qsim_sample draws complex64 shots from), 2^62 for p >= 1 or an infinite
+ * part, 0 for a NaN.  Pure function, no device work. */
+QSIM_API uint64_t qsim_sampler_weight_c64(float re, float im);
+
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each
  * launch is bracketed by CUDA events on its own stream; qsim_profile_get

@@ -124,20 +124,24 @@ struct HParams {
     double cr[HAPPLY_TERMS], ci[HAPPLY_TERMS];
 };
 
+// Arithmetic in the state's own precision (fp32 for complex64: lambda is
+// stored in complex64 anyway), so the fp64 units are not on this path.
 template <typename C>
 __global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__restrict__ lam, uint64_t N,
                                                 const __grid_constant__ HParams h) {
+    using R = decltype(C::x);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
-        double sr = 0, si = 0;
+        R sr = 0, si = 0;
+#pragma unroll 4
         for (int g = 0; g < h.ngroups; ++g) {
             const uint64_t x = y ^ h.X[g];
             const C a = psi[x];
-            double fr = 0, fi = 0;
+            R fr = 0, fi = 0;
             for (int t = h.t0[g]; t < h.t0[g + 1]; ++t) {
-                const double s = (__popcll(x & h.Z[t]) & 1) ? -1.0 : 1.0;
-                fr += s * h.cr[t];
-                fi += s * h.ci[t];
+                const bool odd = __popcll(x & h.Z[t]) & 1;
+                fr += odd ? -R(h.cr[t]) : R(h.cr[t]);
+                fi += odd ? -R(h.ci[t]) : R(h.ci[t]);
             }
             sr += fr * a.x - fi * a.y;
             si += fr * a.y + fi * a.x;

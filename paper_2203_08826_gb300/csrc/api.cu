@@ -607,11 +607,12 @@ int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *xmask, con
 static int sample_common(const void *src, int src_kind, uint64_t N, uint64_t nshots, uint64_t seed,
                          uint64_t counter0, uint64_t *out, int out_on_device, cudaStream_t st,
                          uint64_t *scratch) {
-    // scratch layout: [chunk sums / prefix (sample_scratch_u64)] [psum double] [shots if host]
-    const size_t nsc = sample_scratch_u64(N);
-    uint64_t *dst = out_on_device ? out : scratch + nsc + 8;
-    double *psum = reinterpret_cast<double *>(scratch + nsc);
-    QSIM_TRY(launch_sample(src, src_kind, N, nshots, seed, counter0, dst, scratch, psum, st));
+    // scratch layout: [chunk sums / prefix (sample_scratch_u64)] [scan offsets] [psum double] [shots if host]
+    const size_t nsc = sample_scratch_u64(N), nof = sample_offsets_u64(N);
+    uint64_t *offs = scratch + nsc;
+    double *psum = reinterpret_cast<double *>(scratch + nsc + nof);
+    uint64_t *dst = out_on_device ? out : scratch + nsc + nof + 8;
+    QSIM_TRY(launch_sample(src, src_kind, N, nshots, seed, counter0, dst, scratch, offs, psum, st));
     double hp = 0.0;
     uint64_t total = 0;
     QSIM_CUDA_TRY(cudaMemcpyAsync(&hp, psum, sizeof(double), cudaMemcpyDeviceToHost, st), "psum copy");
@@ -629,7 +630,7 @@ static int sample_common(const void *src, int src_kind, uint64_t N, uint64_t nsh
 int qsim_sample(qsim_state *s, uint64_t nshots, uint64_t seed, uint64_t counter0, uint64_t *out,
                 int out_on_device) {
     if (!s || (!out && nshots)) return set_error(QSIM_EINVAL, "NULL argument");
-    const size_t nsc = sample_scratch_u64(s->size());
+    const size_t nsc = sample_scratch_u64(s->size()) + sample_offsets_u64(s->size());
     QSIM_TRY(s->ensure_scratch((nsc + 8 + (out_on_device ? 0 : nshots)) * sizeof(uint64_t)));
     return sample_common(s->amps, s->dtype == QSIM_C64 ? SRC_C64 : SRC_C128, s->size(), nshots, seed,
                          counter0, out, out_on_device, s->stream, static_cast<uint64_t *>(s->scratch));
@@ -639,7 +640,7 @@ int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t
                       uint64_t *out, int out_on_device, void *cuda_stream) {
     if (!p_dev || N == 0 || (!out && nshots)) return set_error(QSIM_EINVAL, "bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const size_t nsc = sample_scratch_u64(N);
+    const size_t nsc = sample_scratch_u64(N) + sample_offsets_u64(N);
     uint64_t *scratch = nullptr;
     QSIM_CUDA_TRY(cudaMalloc(&scratch, (nsc + 8 + (out_on_device ? 0 : nshots)) * sizeof(uint64_t)),
                   "sampler scratch");

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
 struct Packed {
     bool ready = false;
     int W = 3;
+    double flops = 0;  // useful flops of one run of the whole batch
     std::vector<BCirc> circ;
     std::vector<BStage> stages;
     std::vector<StageOp> ops;
@@ -252,12 +253,14 @@ int pack(qsim_batch &b, int W) {
     pk.phases.clear();
     pk.pool.clear();
     pk.aux.clear();
+    pk.flops = 0;
     for (const qsim_circuit &c : b.circuits) {
         std::vector<stage::Stage> st;
         QSIM_TRY(stage::plan_stage_list(c, W, false, st));
         BCirc bc{c.n, int(pk.stages.size()), int(st.size()), 0};
         for (const stage::Stage &s : st) {
             if (s.plain) return set_error(QSIM_EUNSUPPORTED, "batch circuits need gates of at most 2 targets");
+            pk.flops += stage::stage_flops_per_amp(s) * double(uint64_t(1) << c.n);
             BStage bs{};
             int tq[LANE_BITS + MAX_SLOTS];
             int nt = 0;
@@ -344,7 +347,7 @@ int launch_batch(qsim_batch &b, double *out, cudaStream_t st, int ctas_per_sm) {
     QSIM_CUDA_TRY(cudaMemsetAsync(b.d_counter, 0, sizeof(int), st), "batch counter reset");
     double bytes = 0;
     for (const qsim_circuit &c : b.circuits) bytes += double(uint64_t(1) << c.n) * 8.0;
-    LaunchScope ls(K_BATCH, st, bytes);
+    LaunchScope ls(K_BATCH, st, bytes, pk.flops);
     k_batch<W><<<unsigned(grid), 32 << W, smem, st>>>(bp);
     QSIM_CUDA_TRY(cudaGetLastError(), "batch launch");
     return QSIM_OK;

@@ -123,9 +123,12 @@ int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t 
                   const uint64_t *zmask, const double *coeff, double *partials,
                   size_t npartials, double *result, cudaStream_t st);
 size_t sample_scratch_u64(uint64_t N);
+// scratch: sample_scratch_u64(N) words (chunk prefix + total); offs:
+// sample_offsets_u64(N) words for the scan
 int launch_sample(const void *src, int src_kind, uint64_t N, uint64_t nshots, uint64_t seed,
-                  uint64_t counter0, uint64_t *out_dev, uint64_t *scratch, double *psum_dev,
+                  uint64_t counter0, uint64_t *out_dev, uint64_t *scratch, uint64_t *offs, double *psum_dev,
                   cudaStream_t st);
+size_t sample_offsets_u64(uint64_t N);
 enum { SRC_C64 = 0, SRC_C128 = 1, SRC_PROBS = 2 };
 
 }  // namespace qsim

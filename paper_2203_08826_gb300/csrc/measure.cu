@@ -105,7 +105,7 @@ __device__ __forceinline__ uint64_t gather_bits(uint64_t x, const MargParams &p)
 
 // few bins: per-CTA shared-memory histogram, then per-CTA rows in scratch
 template <typename C>
-__global__ void k_marg_hist(const C *__restrict__ psi, uint64_t N, MargParams p, double *__restrict__ rows) {
+__global__ void k_marg_hist(const C *__restrict__ psi, uint64_t N, const __grid_constant__ MargParams p, double *__restrict__ rows) {
     extern __shared__ double hist[];
     const int nb = 1 << p.m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
@@ -127,7 +127,7 @@ __global__ void k_marg_rows(const double *__restrict__ rows, int nrows, int nb, 
 
 // many bins: one thread per output, summing over the complementary bits
 template <typename C>
-__global__ void k_marg_many(const C *__restrict__ psi, uint64_t nout, uint64_t nrest, MargParams p,
+__global__ void k_marg_many(const C *__restrict__ psi, uint64_t nout, uint64_t nrest, const __grid_constant__ MargParams p,
                             IndexMap zero_at_listed, double *__restrict__ out) {
     const uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (y >= nout) return;
@@ -273,12 +273,54 @@ int launch_diff_norm2(const void *a, const void *b, int n, int dtype, double *pa
     return QSIM_OK;
 }
 
+// complex64 squared norm without FP64 per amplitude: each square is split
+// exactly into p + e (p = x*x, e = fma(x, x, -p)); the p's are summed in a
+// float-float pair (Knuth's two-sum), the small e's in float.  Eight 16-byte
+// loads per thread are in flight per iteration.
+constexpr int RED_U = 4;
+
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float a) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (a - bp);
+    hi = s;
+}
+
+__global__ void __launch_bounds__(256) k_norm2_c64(const float4 *__restrict__ psi4, uint64_t n4,
+                                                   double *__restrict__ partials) {
+    float hi = 0.f, lo = 0.f, el = 0.f;
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x * RED_U;
+    for (uint64_t b = uint64_t(blockIdx.x) * blockDim.x * RED_U + threadIdx.x; b < n4; b += step) {
+        float4 v[RED_U];
+#pragma unroll
+        for (int u = 0; u < RED_U; ++u) {
+            const uint64_t i = b + uint64_t(u) * blockDim.x;
+            v[u] = i < n4 ? psi4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < RED_U; ++u) {
+            const float c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float sq = c[t] * c[t];
+                el += fmaf(c[t], c[t], -sq);
+                two_sum_add(hi, lo, sq);
+            }
+        }
+    }
+    double acc = double(hi) + double(lo) + double(el);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result, cudaStream_t st) {
     const uint64_t N = uint64_t(1) << n;
     const int blocks = reduce_blocks(), T = 256;
     {
         LaunchScope ls(K_REDUCE, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
-        if (dtype == QSIM_C64)
+        if (dtype == QSIM_C64 && N >= 2)
+            k_norm2_c64<<<blocks, T, 0, st>>>(static_cast<const float4 *>(psi), N / 2, partials);
+        else if (dtype == QSIM_C64)
             k_norm2<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, partials);
         else
             k_norm2<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), N, partials);
@@ -340,21 +382,26 @@ __device__ __forceinline__ void f_of(uint64_t y, const ExpParams &p, double &fr,
 }
 
 // Diagonal pass of a complex64 state with one real coefficient: |psi|^2 times
-// the integer sign sum is formed in fp32 for 16 amplitudes per thread (the
-// precision of the complex64 amplitudes themselves) and accumulated in double.
-__global__ void __launch_bounds__(256) k_expect_diag_c64(const float2 *__restrict__ psi, uint64_t N, ExpParams p,
+// the integer sign sum is formed in fp32 (the precision of the complex64
+// amplitudes themselves) for the eight amplitudes of one iteration and
+// accumulated in double; 16-byte loads, several in flight per thread.
+__global__ void __launch_bounds__(256) k_expect_diag_c64(const float4 *__restrict__ psi4, uint64_t n4, const __grid_constant__ ExpParams p,
                                                          double *__restrict__ partials) {
     double acc = 0;
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t g0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g0 < N; g0 += 16 * stride) {
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x * RED_U;
+    for (uint64_t b = uint64_t(blockIdx.x) * blockDim.x * RED_U + threadIdx.x; b < n4; b += step) {
+        float4 v[RED_U];
+#pragma unroll
+        for (int u = 0; u < RED_U; ++u) {
+            const uint64_t i = b + uint64_t(u) * blockDim.x;
+            v[u] = i < n4 ? psi4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float part = 0.f;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const uint64_t g = g0 + uint64_t(u) * stride;
-            if (g < N) {
-                const float2 a = psi[g];
-                part += (a.x * a.x + a.y * a.y) * float(p.nt - 2 * odd_terms(g, p));
-            }
+        for (int u = 0; u < RED_U; ++u) {
+            const uint64_t g = 2 * (b + uint64_t(u) * blockDim.x);  // amplitude index of .xy (and g + 1 of .zw)
+            part = fmaf(fmaf(v[u].x, v[u].x, v[u].y * v[u].y), float(p.nt - 2 * odd_terms(g, p)), part);
+            part = fmaf(fmaf(v[u].z, v[u].z, v[u].w * v[u].w), float(p.nt - 2 * odd_terms(g + 1, p)), part);
         }
         acc += double(part);
     }
@@ -362,8 +409,118 @@ __global__ void __launch_bounds__(256) k_expect_diag_c64(const float2 *__restric
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
+// Any pass of a complex64 state: products in fp32, eight pairs per iteration
+// summed in fp32 and accumulated in double.
+__device__ __forceinline__ void f_of_f(uint64_t y, const ExpParams &p, float &fr, float &fi) {
+    if (p.uniform) {
+        const float s = float(p.nt - 2 * odd_terms(y, p));
+        fr = s * float(p.ur);
+        fi = s * float(p.ui);
+        return;
+    }
+    fr = 0.f;
+    fi = 0.f;
+    for (int t = 0; t < p.nt; ++t) {
+        const bool odd = __popcll(y & p.z[t]) & 1;
+        fr += odd ? -float(p.cr[t]) : float(p.cr[t]);
+        fi += odd ? -float(p.ci[t]) : float(p.ci[t]);
+    }
+}
+
+constexpr int EXP_U = 8;
+
+__global__ void __launch_bounds__(256) k_expect_c64(const float2 *__restrict__ psi, uint64_t count, const __grid_constant__ ExpParams p,
+                                                    double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x * EXP_U;
+    for (uint64_t b = uint64_t(blockIdx.x) * blockDim.x * EXP_U + threadIdx.x; b < count; b += step) {
+        float2 a[EXP_U], c[EXP_U];
+        uint64_t y[EXP_U];
+#pragma unroll
+        for (int u = 0; u < EXP_U; ++u) {
+            const uint64_t g = b + uint64_t(u) * blockDim.x;
+            if (p.h < 0) {
+                y[u] = g;
+            } else {
+                const uint64_t low = g & ((uint64_t(1) << p.h) - 1);
+                y[u] = ((g ^ low) << 1) | low;  // bit h of y is 0
+            }
+            a[u] = g < count ? psi[y[u]] : make_float2(0.f, 0.f);
+            c[u] = (g < count && p.h >= 0) ? psi[y[u] ^ p.X] : make_float2(0.f, 0.f);
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int u = 0; u < EXP_U; ++u) {
+            float fr, fi;
+            f_of_f(y[u], p, fr, fi);
+            if (p.h < 0) {
+                part = fmaf(fmaf(a[u].x, a[u].x, a[u].y * a[u].y), fr, part);
+            } else {
+                float gr, gi;
+                f_of_f(y[u] ^ p.X, p, gr, gi);
+                const float bar = fmaf(c[u].x, a[u].x, c[u].y * a[u].y);   // Re(conj(b) a)
+                const float bai = fmaf(c[u].x, a[u].y, -c[u].y * a[u].x);  // Im(conj(b) a)
+                part += (fr + gr) * bar + (gi - fi) * bai;
+            }
+        }
+        acc += double(part);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// X-group pass of a complex64 state (X != 0): for the pair (y, y ^ X) with
+// bit h of y clear, a = psi[y], b = psi[y ^ X], the group contributes
+// Re(conj(b) a) sum_t s_t A_t + Im(conj(b) a) sum_t s_t B_t with
+// s_t = (-1)^popcount(y & z_t); the host folded the sign change of each term
+// between y and y ^ X into A_t = Re c_t (1 + sigma_t), B_t = Im c_t (sigma_t - 1),
+// sigma_t = (-1)^popcount(X & z_t).
+struct ExpXParams {
+    uint64_t X;
+    int h, nt;
+    uint64_t z[EXP_TERMS];
+    float A[EXP_TERMS], B[EXP_TERMS];
+};
+
+__global__ void __launch_bounds__(256) k_expect_x_c64(const float2 *__restrict__ psi, uint64_t count,
+                                                      const __grid_constant__ ExpXParams p,
+                                                      double *__restrict__ partials) {
+    double acc = 0;
+    const uint64_t lowmask = (uint64_t(1) << p.h) - 1;
+    const uint64_t step = uint64_t(gridDim.x) * blockDim.x * EXP_U;
+    for (uint64_t b = uint64_t(blockIdx.x) * blockDim.x * EXP_U + threadIdx.x; b < count; b += step) {
+        float2 va[EXP_U], vb[EXP_U];
+        uint64_t y[EXP_U];
+#pragma unroll
+        for (int u = 0; u < EXP_U; ++u) {
+            const uint64_t g = b + uint64_t(u) * blockDim.x;
+            const uint64_t low = g & lowmask;
+            y[u] = ((g ^ low) << 1) | low;
+            const bool in = g < count;
+            va[u] = in ? psi[y[u]] : make_float2(0.f, 0.f);
+            vb[u] = in ? psi[y[u] ^ p.X] : make_float2(0.f, 0.f);
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int u = 0; u < EXP_U; ++u) {
+            float sa = 0.f, sb = 0.f;
+            for (int t = 0; t < p.nt; ++t) {
+                const bool odd = __popcll(y[u] & p.z[t]) & 1;
+                sa += odd ? -p.A[t] : p.A[t];
+                sb += odd ? -p.B[t] : p.B[t];
+            }
+            const float bar = fmaf(vb[u].x, va[u].x, vb[u].y * va[u].y);
+            const float bai = fmaf(vb[u].x, va[u].y, -vb[u].y * va[u].x);
+            part = fmaf(bar, sa, fmaf(bai, sb, part));
+        }
+        acc += double(part);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
 template <typename C>
-__global__ void __launch_bounds__(256) k_expect(const C *__restrict__ psi, uint64_t count, ExpParams p,
+__global__ void __launch_bounds__(256) k_expect(const C *__restrict__ psi, uint64_t count, const __grid_constant__ ExpParams p,
                                                 double *__restrict__ partials) {
     double acc = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
@@ -439,10 +596,22 @@ int launch_expect(const void *psi, int n, int dtype, int nterms, const uint64_t 
         }
         {
             LaunchScope ls(K_EXPECT, st, double(N) * (dtype == QSIM_C64 ? 8 : 16));
-            if (dtype == QSIM_C64 && p.h < 0 && p.uniform && p.ui == 0.0)
-                k_expect_diag_c64<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, p, partials);
-            else if (dtype == QSIM_C64)
-                k_expect<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), count, p, partials);
+            if (dtype == QSIM_C64 && p.h < 0 && p.uniform && p.ui == 0.0 && N >= 2)
+                k_expect_diag_c64<<<blocks, T, 0, st>>>(static_cast<const float4 *>(psi), N / 2, p, partials);
+            else if (dtype == QSIM_C64 && p.h >= 0) {
+                ExpXParams xp{};
+                xp.X = p.X;
+                xp.h = p.h;
+                xp.nt = p.nt;
+                for (int t = 0; t < p.nt; ++t) {
+                    const double sigma = (__builtin_popcountll(p.X & p.z[t]) & 1) ? -1.0 : 1.0;
+                    xp.z[t] = p.z[t];
+                    xp.A[t] = float(p.cr[t] * (1.0 + sigma));
+                    xp.B[t] = float(p.ci[t] * (sigma - 1.0));
+                }
+                k_expect_x_c64<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), count, xp, partials);
+            } else if (dtype == QSIM_C64)
+                k_expect_c64<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), count, p, partials);
             else
                 k_expect<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), count, p, partials);
             QSIM_CUDA_TRY(cudaGetLastError(), "expectation launch");
@@ -490,11 +659,107 @@ __device__ __forceinline__ uint64_t weight_of(double p) {
     return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0);
 }
 
+// ---- complex64 weights in integer arithmetic
+// floor(p * 2^62) for p = RN_double(re^2 + im^2), the value prob_of gives,
+// without fp64 (GB300's fp64 rate made the fp64 form the sampler's limit).
+// re^2 and im^2 are exact products of the 24-bit significands (subnormals
+// normalised first); the two are aligned in 128 bits (a gap above 79 bits
+// leaves the larger square exactly representable: the smaller one is below
+// half its unit in the last place) and rounded to 53 bits, nearest-even.
+__host__ __device__ inline int clz64_hd(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll(static_cast<long long>(v));
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+__host__ __device__ inline void square_of_float(uint32_t u, uint64_t &M, int &E) {
+    const uint32_t e = u >> 23, m = u & 0x7FFFFFu;
+    uint64_t mant;
+    int ex;
+    if (e == 0) {
+        const int sh = (clz64_hd(m) - 32) - 8;  // leading bit to position 23
+        mant = uint64_t(m) << sh;
+        ex = -149 - sh;
+    } else {
+        mant = m | 0x800000u;
+        ex = int(e) - 150;
+    }
+    M = mant * mant;
+    E = 2 * ex;
+}
+
+__host__ __device__ inline uint64_t weight_c64(float re, float im) {
+    uint32_t ux, uy;
+    memcpy(&ux, &re, 4);
+    memcpy(&uy, &im, 4);
+    ux &= 0x7FFFFFFFu;
+    uy &= 0x7FFFFFFFu;
+    if (ux > 0x7F800000u || uy > 0x7F800000u) return 0;                       // NaN
+    if (ux == 0x7F800000u || uy == 0x7F800000u) return uint64_t(1) << 62;     // infinite
+    if (ux == 0 && uy == 0) return 0;
+    uint64_t M53;
+    int E53;
+    if (ux == 0 || uy == 0) {
+        square_of_float(ux ? ux : uy, M53, E53);
+    } else {
+        uint64_t M1, M2;
+        int E1, E2;
+        square_of_float(ux, M1, E1);
+        square_of_float(uy, M2, E2);
+        if (E1 < E2) {
+            const uint64_t tm = M1;
+            M1 = M2;
+            M2 = tm;
+            const int te = E1;
+            E1 = E2;
+            E2 = te;
+        }
+        const int d = E1 - E2;
+        if (d > 79) {
+            M53 = M1;
+            E53 = E1;
+        } else {
+            const unsigned __int128 T = (static_cast<unsigned __int128>(M1) << d) + M2;
+            const uint64_t hi = uint64_t(T >> 64), lo = uint64_t(T);
+            const int L = hi ? 128 - clz64_hd(hi) : 64 - clz64_hd(lo);
+            if (L <= 53) {
+                M53 = lo;
+                E53 = E2;
+            } else {
+                int sh = L - 53;
+                M53 = uint64_t(T >> sh);
+                const unsigned __int128 rem = T & ((static_cast<unsigned __int128>(1) << sh) - 1);
+                const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+                if (rem > half || (rem == half && (M53 & 1))) ++M53;
+                if (M53 == (uint64_t(1) << 53)) {
+                    M53 >>= 1;
+                    ++sh;
+                }
+                E53 = E2 + sh;
+            }
+        }
+    }
+    if ((64 - clz64_hd(M53)) + E53 > 0) return uint64_t(1) << 62;  // p >= 1
+    const int s = E53 + 62;
+    return s >= 0 ? (M53 << s) : (-s < 64 ? (M53 >> -s) : 0);
+}
+
 template <int SRC>
 __device__ __forceinline__ double src_prob(const void *src, uint64_t x) {
     if (SRC == SRC_C64) return prob_of(static_cast<const float2 *>(src)[x]);
     if (SRC == SRC_C128) return prob_of(static_cast<const double2 *>(src)[x]);
     return static_cast<const double *>(src)[x];
+}
+
+template <int SRC>
+__device__ __forceinline__ uint64_t src_weight(const void *src, uint64_t x) {
+    if (SRC == SRC_C64) {
+        const float2 a = static_cast<const float2 *>(src)[x];
+        return weight_c64(a.x, a.y);
+    }
+    return weight_of(src_prob<SRC>(src, x));
 }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
@@ -523,7 +788,7 @@ __global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ s
             if (x < N) {
                 if (SRC == SRC_C64) {
                     const float2 a = static_cast<const float2 *>(src)[x];
-                    wsum += weight_of(prob_of(a));
+                    wsum += weight_c64(a.x, a.y);
                     pf += a.x * a.x + a.y * a.y;
                 } else {
                     const double p = src_prob<SRC>(src, x);
@@ -548,28 +813,82 @@ __global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ s
     }
 }
 
-// inclusive prefix over the chunk sums in place; total -> sums[nchunks]
-__global__ void __launch_bounds__(1024) k_sample_scan(uint64_t *__restrict__ sums, uint64_t nchunks) {
-    __shared__ uint64_t part[1024];
-    const uint64_t per = (nchunks + blockDim.x - 1) / blockDim.x;
-    const uint64_t b = threadIdx.x * per, e = (b + per < nchunks) ? b + per : nchunks;
-    uint64_t s = 0;
-    for (uint64_t i = b; i < e; ++i) s += sums[i];
-    part[threadIdx.x] = s;
+// Inclusive prefix over the chunk sums in place, in three launches: each
+// block scans a tile of SCAN_TILE sums (coalesced, shuffles then shared
+// memory); one block forms the exclusive offsets of the tiles (from their last
+// elements) and the total (-> sums[nchunks]); every block then adds its tile's
+// offset.
+constexpr int SCAN_T = 1024, SCAN_PER = 4, SCAN_TILE = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ uint64_t block_incl_scan_u64(uint64_t x, uint64_t *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the per-thread totals
-    for (int off = 1; off < int(blockDim.x); off <<= 1) {
-        const uint64_t v = threadIdx.x >= unsigned(off) ? part[threadIdx.x - off] : 0;
+    if (warp == 0) {
+        uint64_t w = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t r = x + (warp ? wsum[warp - 1] : 0);
+    __syncthreads();  // wsum may be reused
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(uint64_t *__restrict__ sums, uint64_t n) {
+    __shared__ uint64_t wsum[32];
+    const uint64_t base = uint64_t(blockIdx.x) * SCAN_TILE + uint64_t(threadIdx.x) * SCAN_PER;
+    uint64_t v[SCAN_PER];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) v[k] = base + k < n ? sums[base + k] : 0;
+#pragma unroll
+    for (int k = 1; k < SCAN_PER; ++k) v[k] += v[k - 1];
+    const uint64_t incl = block_incl_scan_u64(v[SCAN_PER - 1], wsum);
+    const uint64_t excl = incl - v[SCAN_PER - 1];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k)
+        if (base + k < n) sums[base + k] = v[k] + excl;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_offsets(uint64_t *__restrict__ sums, uint64_t n, uint64_t ntiles,
+                                                         uint64_t *__restrict__ offs) {
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t round_total;
+    uint64_t carry = 0;
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += SCAN_T) {
+        const uint64_t t = t0 + threadIdx.x;
+        uint64_t last = 0;
+        if (t < ntiles) {
+            const uint64_t e = (t + 1) * SCAN_TILE < n ? (t + 1) * SCAN_TILE : n;
+            last = sums[e - 1];  // the tile's total (its inclusive scan ends there)
+        }
+        const uint64_t incl = block_incl_scan_u64(last, wsum);
+        if (t < ntiles) offs[t] = carry + incl - last;
+        if (threadIdx.x == SCAN_T - 1) round_total = incl;
         __syncthreads();
-        part[threadIdx.x] += v;
+        carry += round_total;
         __syncthreads();
     }
-    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (uint64_t i = b; i < e; ++i) {
-        run += sums[i];
-        sums[i] = run;
-    }
-    if (threadIdx.x == blockDim.x - 1) sums[nchunks] = part[threadIdx.x];
+    if (threadIdx.x == 0) sums[n] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_add(uint64_t *__restrict__ sums, uint64_t n,
+                                                     const uint64_t *__restrict__ offs) {
+    const uint64_t off = offs[blockIdx.x];
+    if (off == 0) return;
+    const uint64_t base = uint64_t(blockIdx.x) * SCAN_TILE + uint64_t(threadIdx.x) * SCAN_PER;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k)
+        if (base + k < n) sums[base + k] += off;
 }
 
 // one warp per shot: binary search over the chunk prefix, then a warp scan
@@ -605,7 +924,7 @@ __global__ void __launch_bounds__(256) k_sample_draw(const void *__restrict__ sr
     uint64_t found = ((x0 + CHUNK < N) ? x0 + CHUNK : N) - 1;
     for (int j = 0; j < CHUNK / 32; ++j) {
         const uint64_t x = x0 + uint64_t(j) * 32 + lane;
-        uint64_t w = x < N ? weight_of(src_prob<SRC>(src, x)) : 0;
+        uint64_t w = x < N ? src_weight<SRC>(src, x) : 0;
         // inclusive warp scan
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -624,10 +943,11 @@ __global__ void __launch_bounds__(256) k_sample_draw(const void *__restrict__ sr
 }
 
 size_t sample_scratch_u64(uint64_t N) { return size_t((N + CHUNK - 1) / CHUNK) + 1; }
+size_t sample_offsets_u64(uint64_t N) { return size_t(((N + CHUNK - 1) / CHUNK + SCAN_TILE - 1) / SCAN_TILE); }
 
 template <int SRC>
 static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_t seed, uint64_t counter0,
-                           uint64_t *out, uint64_t *scratch, double *psum, cudaStream_t st) {
+                           uint64_t *out, uint64_t *scratch, uint64_t *offs, double *psum, cudaStream_t st) {
     const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
     const double S = SRC == SRC_C64 ? 8 : 16;
     QSIM_CUDA_TRY(cudaMemsetAsync(psum, 0, sizeof(double), st), "sampler zero");
@@ -638,7 +958,10 @@ static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_
     }
     {
         LaunchScope ls(K_SAMPLE_SCAN, st, double(nchunks) * 16);
-        k_sample_scan<<<1, 1024, 0, st>>>(scratch, nchunks);
+        const uint64_t ntiles = (nchunks + SCAN_TILE - 1) / SCAN_TILE;
+        k_scan_tiles<<<unsigned(ntiles), SCAN_T, 0, st>>>(scratch, nchunks);
+        k_scan_offsets<<<1, SCAN_T, 0, st>>>(scratch, nchunks, ntiles, offs);
+        k_scan_add<<<unsigned(ntiles), SCAN_T, 0, st>>>(scratch, nchunks, offs);
         QSIM_CUDA_TRY(cudaGetLastError(), "sampler scan launch");
     }
     if (nshots) {
@@ -652,12 +975,12 @@ static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_
 }
 
 int launch_sample(const void *src, int src_kind, uint64_t N, uint64_t nshots, uint64_t seed, uint64_t counter0,
-                  uint64_t *out_dev, uint64_t *scratch, double *psum_dev, cudaStream_t st) {
+                  uint64_t *out_dev, uint64_t *scratch, uint64_t *offs, double *psum_dev, cudaStream_t st) {
     if (nshots > (uint64_t(1) << 30)) return set_error(QSIM_EINVAL, "at most 2^30 shots per call");
     switch (src_kind) {
-        case SRC_C64: return launch_sample_t<SRC_C64>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
-        case SRC_C128: return launch_sample_t<SRC_C128>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
-        default: return launch_sample_t<SRC_PROBS>(src, N, nshots, seed, counter0, out_dev, scratch, psum_dev, st);
+        case SRC_C64: return launch_sample_t<SRC_C64>(src, N, nshots, seed, counter0, out_dev, scratch, offs, psum_dev, st);
+        case SRC_C128: return launch_sample_t<SRC_C128>(src, N, nshots, seed, counter0, out_dev, scratch, offs, psum_dev, st);
+        default: return launch_sample_t<SRC_PROBS>(src, N, nshots, seed, counter0, out_dev, scratch, offs, psum_dev, st);
     }
 }
 
@@ -679,6 +1002,9 @@ constexpr uint64_t STATIC_SAMPLE_MAX_N = uint64_t(1) << 27;         // probabili
 constexpr size_t STATIC_SAMPLE_CHUNKS = size_t(STATIC_SAMPLE_MAX_N / CHUNK);
 // [0, chunks]: inclusive chunk prefix + total; [chunks + 1]: probability sum
 constexpr size_t STATIC_SAMPLE_WORDS = (STATIC_SAMPLE_CHUNKS + 2 + 31) / 32 * 32;  // 512.25 KiB
+// the scan's tile offsets use the array's last words (the padding above)
+constexpr size_t STATIC_SCAN_TILES = (STATIC_SAMPLE_CHUNKS + SCAN_TILE - 1) / SCAN_TILE;
+static_assert(STATIC_SAMPLE_CHUNKS + 2 + STATIC_SCAN_TILES <= STATIC_SAMPLE_WORDS, "static sampler scratch too small");
 
 static __device__ __align__(256) uint64_t g_sample_scratch[STATIC_SAMPLE_WORDS];
 
@@ -719,9 +1045,10 @@ extern "C" QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N
     QSIM_TRY(static_scratch(&scratch));
     const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
     double *psum = reinterpret_cast<double *>(scratch + STATIC_SAMPLE_CHUNKS + 1);
+    uint64_t *offs = scratch + STATIC_SAMPLE_WORDS - STATIC_SCAN_TILES;
     // the chunk kernel overwrites every prefix entry it uses; the probability
     // sum is accumulated and is cleared by the launcher's memset
-    QSIM_TRY(launch_sample(p_dev, SRC_PROBS, N, nshots, seed, counter0, out_dev, scratch, psum, st));
+    QSIM_TRY(launch_sample(p_dev, SRC_PROBS, N, nshots, seed, counter0, out_dev, scratch, offs, psum, st));
     double hp = 0.0;
     uint64_t total = 0;
     QSIM_CUDA_TRY(cudaMemcpyAsync(&hp, psum, sizeof(double), cudaMemcpyDeviceToHost, st), "psum copy");
@@ -772,6 +1099,9 @@ __global__ void __launch_bounds__(256) k_collapse(C *__restrict__ psi, uint64_t 
 
 }  // namespace
 }  // namespace qsim
+
+// test support: the complex64 sampler weight rule evaluated on the host
+extern "C" uint64_t qsim_sampler_weight_c64(float re, float im) { return qsim::weight_c64(re, im); }
 
 extern "C" QSIM_API int qsim_collapse(qsim_state *s, const int *qubits, int m, uint64_t outcome, double *prob_out) {
     using namespace qsim;

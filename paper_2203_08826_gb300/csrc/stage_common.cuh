@@ -472,6 +472,8 @@ struct Stage {
 // Split a circuit into stages for tiles of 2^(9 + W) amplitudes.  With
 // `limits` the op, phase and pool counts of a stage stay within one kernel
 // parameter block.
+// useful flops per amplitude of a planned stage (host)
+double stage_flops_per_amp(const Stage &st);
 int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out);
 
 // Kernel parameter block of one tile stage.

@@ -330,6 +330,21 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
 
 }  // namespace
 
+// Useful flops per amplitude of a stage (a complex multiply-add is 8 flops;
+// a controlled op counts for the fraction of amplitudes it touches).
+double stage_flops_per_amp(const Stage &st) {
+    double f = 0;
+    if (st.plain) return st.op.type == Op::DENSE ? 8.0 * double(1 << st.op.k) / double(1ull << st.op.c) : 0.0;
+    for (const StageOp &o : st.ops) {
+        const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
+        if (o.type == SOP_U1) f += 16.0 * frac;
+        else if (o.type == SOP_U1R || o.type == SOP_U1L) f += 16.0 * __builtin_popcount(unsigned(o.a));
+        else if (o.type == SOP_U2) f += 32.0 * frac;
+        else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
+    }
+    return f;
+}
+
 int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out) {
     const int n = c.n;
     const int cap = REG_BITS + W;
@@ -483,22 +498,7 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
     // kmax selects the tile: 2^(9 + W) amplitudes with W = min(kmax, 4) warp qubits
     sp->W = std::min(std::min(p.kmax, MAX_WARP_BITS), n - LANE_BITS - REG_BITS);
     QSIM_TRY(plan_stage_list(c, sp->W, true, sp->stages));
-    // useful flops per amplitude: a complex multiply-add is 8 flops
-    for (const Stage &st : sp->stages) {
-        double f = 0;
-        if (st.plain) {
-            f = st.op.type == Op::DENSE ? 8.0 * double(1 << st.op.k) / double(1ull << st.op.c) : 0.0;
-        } else {
-            for (const StageOp &o : st.ops) {
-                const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
-                if (o.type == SOP_U1) f += 16.0 * frac;
-                else if (o.type == SOP_U1R || o.type == SOP_U1L) f += 16.0 * __builtin_popcount(unsigned(o.a));
-                else if (o.type == SOP_U2) f += 32.0 * frac;
-                else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
-            }
-        }
-        sp->flops_per_amp.push_back(f);
-    }
+    for (const Stage &st : sp->stages) sp->flops_per_amp.push_back(stage_flops_per_amp(st));
     return QSIM_OK;
 }
 

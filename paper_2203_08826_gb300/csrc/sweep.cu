@@ -87,7 +87,7 @@ template <typename R> struct Mat2 {
 // the single-qubit listing, Sec. 2, with controls folded into the index map.
 template <typename R, int PER>
 __global__ void __launch_bounds__(256) k_dense1(typename CT<R>::T *__restrict__ psi, uint64_t npairs,
-                                                IndexMap map, uint64_t stride, Mat2<R> m) {
+                                                const __grid_constant__ IndexMap map, uint64_t stride, Mat2<R> m) {
     using C = typename CT<R>::T;
     const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
     C a[PER], b[PER];
@@ -124,7 +124,7 @@ template <typename R, int K> struct SmallDense {
 
 template <typename R, int K, int PER>
 __global__ void __launch_bounds__(256) k_dense_small(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
-                                                     IndexMap map, const __grid_constant__ SmallDense<R, K> G) {
+                                                     const __grid_constant__ IndexMap map, const __grid_constant__ SmallDense<R, K> G) {
     using C = typename CT<R>::T;
     constexpr int D = 1 << K;
     const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
@@ -152,13 +152,51 @@ __global__ void __launch_bounds__(256) k_dense_small(typename CT<R>::T *__restri
     }
 }
 
+// ------------------------------------------------------------------ dense k = 4..6
+// Register form for wide blocks: the matrix is staged once per CTA in shared
+// memory (every thread reads the same element: a broadcast); each thread
+// loads a whole group of 2^K amplitudes into registers, then forms and stores
+// the outputs one row at a time (two accumulators per row for ILP).
+template <typename R, int K>
+__global__ void __launch_bounds__(128) k_dense_big(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
+                                                   const __grid_constant__ IndexMap map,
+                                                   const typename CT<R>::T *__restrict__ mat,
+                                                   const __grid_constant__ Offsets offs) {
+    using C = typename CT<R>::T;
+    constexpr int D = 1 << K;
+    extern __shared__ unsigned char dense_smem[];
+    C *gm = reinterpret_cast<C *>(dense_smem);
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) gm[i] = mat[i];
+    __syncthreads();
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const uint64_t x = expand_index(g, map);
+        C v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = psi[x | offs.o[c]];
+#pragma unroll 1
+        for (int r = 0; r < D; ++r) {
+            const C *row = gm + r * D;
+            C a0 = cmul(row[0], v[0]), a1 = cmul(row[1], v[1]);
+#pragma unroll
+            for (int c = 2; c < D; c += 2) {
+                a0 = cfma(row[c], v[c], a0);
+                a1 = cfma(row[c + 1], v[c + 1], a1);
+            }
+            a0.x += a1.x;
+            a0.y += a1.y;
+            psi[x | offs.o[r]] = a0;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ dense k
 // CTA stages GPB groups of 2^K amplitudes in shared memory (coalesced loads:
 // consecutive threads take consecutive groups for the same matrix column),
 // then each thread produces outputs (group, row) = sum_j G[row, j] v[group, j].
 template <typename R, int K, int GPB>
 __global__ void __launch_bounds__(256) k_densek(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
-                                                IndexMap map, const typename CT<R>::T *__restrict__ mat,
+                                                const __grid_constant__ IndexMap map, const typename CT<R>::T *__restrict__ mat,
                                                 Offsets offs) {
     using C = typename CT<R>::T;
     constexpr int D = 1 << K;
@@ -195,7 +233,7 @@ template <typename R> struct DiagParams {
 
 template <typename R, int PER>
 __global__ void __launch_bounds__(256) k_diag(typename CT<R>::T *__restrict__ psi, uint64_t count,
-                                              IndexMap map, DiagParams<R> p) {
+                                              const __grid_constant__ IndexMap map, const __grid_constant__ DiagParams<R> p) {
     using C = typename CT<R>::T;
     const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
     C a[PER];
@@ -225,20 +263,33 @@ template <typename R> struct MonoParams {
     typename CT<R>::T ph[8];
 };
 
-template <typename R>
+// NA rows move per group; each thread takes PER groups (loads first, then
+// stores) so that several loads per thread are in flight.
+template <typename R, int NA, int PER>
 __global__ void __launch_bounds__(256) k_mono(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
-                                              IndexMap map, MonoParams<R> p) {
+                                              const __grid_constant__ IndexMap map,
+                                              const __grid_constant__ MonoParams<R> p) {
     using C = typename CT<R>::T;
-    const uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
-    const uint64_t x = expand_index(g, map);
-    C v[8];
+    const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
+    C v[PER][NA];
+    uint64_t x[PER];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-        if (a < p.na) v[a] = psi[x | p.src[a]];
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t g = base + uint64_t(j) * blockDim.x;
+        x[j] = g < ngroups ? expand_index(g, map) : ~uint64_t(0);
+        if (g < ngroups) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-        if (a < p.na) psi[x | p.dst[a]] = cmul(p.ph[a], v[a]);
+            for (int a = 0; a < NA; ++a)
+                if (a < p.na) v[j][a] = psi[x[j] | p.src[a]];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (x[j] == ~uint64_t(0)) continue;
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+            if (a < p.na) psi[x[j] | p.dst[a]] = cmul(p.ph[a], v[j][a]);
+    }
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -293,6 +344,29 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                     for (int j = 0; j < 8; ++j) G.off[j] = target_offset(j, op.targets, k);
                     k_dense_small<R, 3, 1><<<unsigned((ngroups + T - 1) / T), T, 0, st>>>(psi, ngroups, map, G);
                 }
+            } else if (k <= (sizeof(R) == 4 ? 6 : 5)) {
+                if (!mat_dev) return set_error(QSIM_EINVAL, "dense k>3 needs the matrix on the device");
+                Offsets offs{};
+                for (int j = 0; j < (1 << k); ++j) offs.o[j] = target_offset(j, op.targets, k);
+                const C *mat = static_cast<const C *>(mat_dev);
+                const size_t smem = (size_t(1) << (2 * k)) * sizeof(C);
+                const int T = 128;
+                const uint64_t want = (ngroups + T - 1) / T;
+                const unsigned blocks = unsigned(std::min<uint64_t>(want, uint64_t(sm_count()) * 8));
+                LaunchScope ls(K_DENSEK, st, bytes, 8.0 * double(1 << k) * double(ngroups << k));
+                auto launch = [&](auto kern) -> int {
+                    static bool attr[7] = {};
+                    if (!attr[k]) {
+                        QSIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                                      "dense smem attribute");
+                        attr[k] = true;
+                    }
+                    kern<<<blocks, T, smem, st>>>(psi, ngroups, map, mat, offs);
+                    return QSIM_OK;
+                };
+                if (k == 4) QSIM_TRY(launch(k_dense_big<R, 4>));
+                else if (k == 5) QSIM_TRY(launch(k_dense_big<R, 5>));
+                else QSIM_TRY(launch(k_dense_big<R, (sizeof(R) == 4 ? 6 : 5)>));
             } else {
                 if (!mat_dev) return set_error(QSIM_EINVAL, "dense k>1 needs the matrix on the device");
                 Offsets offs{};
@@ -337,9 +411,13 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 ++p.na;
             }
             const int T = 256;
-            const uint64_t blocks = (ngroups + T - 1) / T;
             LaunchScope ls(K_MONO, st, 2.0 * S * double(ngroups) * p.na);
-            k_mono<R><<<unsigned(blocks), T, 0, st>>>(psi, ngroups, map, p);
+            if (p.na <= 2) {
+                constexpr int PER = 4;
+                k_mono<R, 2, PER><<<unsigned((ngroups + T * PER - 1) / (T * PER)), T, 0, st>>>(psi, ngroups, map, p);
+            } else {
+                k_mono<R, 8, 1><<<unsigned((ngroups + T - 1) / T), T, 0, st>>>(psi, ngroups, map, p);
+            }
             break;
         }
     }

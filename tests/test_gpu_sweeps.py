@@ -257,3 +257,17 @@ def test_sampler_end_to_end_match_rate(q, orc, dtype, rate):
     want = orc.sample(orc.probabilities(orc.simulate(circ)), shots, seed=99, counter0=5)
     match = float(np.mean(got == want))
     assert match >= rate, f"match rate {match:.6f}"
+
+
+def test_sampler_prefix_over_several_scan_tiles(q, orc):
+    """2^24 + 12345 probabilities: 8198 chunk sums, three scan tiles (the last
+    ragged), bit-exact against the oracle's sampler."""
+    import torch
+    from paper_2203_08826_gb300 import binding
+    N = (1 << 24) + 12345
+    rng = np.random.default_rng(17)
+    p = rng.random(N) ** 4
+    p[rng.random(N) < 0.3] = 0.0
+    p /= p.sum()
+    got = binding.sample_probs(torch.from_numpy(p).cuda(), 6000, seed=123, counter0=9)
+    np.testing.assert_array_equal(got, orc.sample(p, 6000, seed=123, counter0=9))

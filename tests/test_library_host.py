@@ -127,3 +127,33 @@ def test_staged_and_tc_plans_describe(q):
     assert "3xTF32" in q.Plan(c, kmax=5, mode=q.FUSE_TC).describe()
     with pytest.raises(q.QsimError):
         q.Plan(inputs.random_circuit(10, 2, seed=1), kmax=6, mode=q.FUSE_TC)
+
+
+def test_complex64_sampler_weights_match_their_definition():
+    """The sampler computes complex64 weights with integer arithmetic only;
+    they must equal floor(RN_double(re^2 + im^2) * 2^62) exactly (exact
+    rational arithmetic here), across magnitudes, subnormals and specials."""
+    import math
+    from fractions import Fraction
+    from paper_2203_08826_gb300 import binding
+    lib = binding.lib()
+
+    def want(re, im):
+        x, y = float(np.float32(re)), float(np.float32(im))
+        if math.isnan(x) or math.isnan(y):
+            return 0
+        if math.isinf(x) or math.isinf(y):
+            return 1 << 62
+        p = float(Fraction(x) ** 2 + Fraction(y) ** 2)  # one correct rounding to double
+        return 1 << 62 if p >= 1.0 else int(Fraction(p) * (1 << 62))
+
+    cases = [(0.0, 0.0), (1.0, 0.0), (-0.0, 1.0), (0.6, 0.8), (1e-45, 0.0), (1e-45, 1e-45), (3e-39, 1e-45),
+             (2.0 ** -75, 2.0 ** -100), (0.70710677, 0.70710677), (float("inf"), 0.0), (float("nan"), 1.0),
+             (-0.5, -0.5), (1.0000001, 0.0)]
+    rng = np.random.default_rng(3)
+    for scale in (1.0, 1e-5, 1e-12, 1e-30, 1e-40):
+        xs = (rng.standard_normal(1500) * scale).astype(np.float32)
+        ys = (rng.standard_normal(1500) * scale * rng.choice([1, 1e-3, 1e-9], 1500)).astype(np.float32)
+        cases += list(zip(xs.tolist(), ys.tolist()))
+    for re, im in cases:
+        assert lib.qsim_sampler_weight_c64(re, im) == want(re, im), (re, im)

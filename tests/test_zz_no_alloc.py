@@ -39,7 +39,8 @@ def test_static_sampler_matches_allocating_sampler_on_consecutive_calls(env):
     rng = np.random.default_rng(2024)
     # two calls in a row with different sizes: the second must not see the
     # first call's leftovers in the shared scratch
-    for N, nshots, seed, c0 in ((300_001, 50_000, 11, 5), (4_099, 20_000, 12, 2**32 - 3)):
+    # 20_000_001 probabilities: 9766 chunk sums, three scan tiles
+    for N, nshots, seed, c0 in ((20_000_001, 30_000, 13, 7), (300_001, 50_000, 11, 5), (4_099, 20_000, 12, 2**32 - 3)):
         p = rng.dirichlet(np.full(N, 0.3))
         p_dev = torch.from_numpy(p).cuda()
         got = _static_shots(torch, binding, p_dev, nshots, seed, c0)
