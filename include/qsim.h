@@ -416,6 +416,9 @@ QSIM_API int qsim_slice_run(const qsim_slice_plan *p, int dtype, void *const *sl
  * qsim_sample draws complex64 shots from), 2^62 for p >= 1 or an infinite
  * part, 0 for a NaN.  Pure function, no device work. */
 QSIM_API uint64_t qsim_sampler_weight_c64(float re, float im);
+/* The complex64 probability re^2 + im^2 rounded once to double, by the
+ * integer rule qsim_probabilities uses for complex64 states (host). */
+QSIM_API double qsim_prob_c64(float re, float im);
 
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each

@@ -91,6 +91,7 @@ _SIGS = {
     "qsim_slice_unpack": ([P, I, I, I, I, P, P], I),
     "qsim_slice_run": ([P, I, P, I, P], I),
     "qsim_sampler_weight_c64": ([ctypes.c_float, ctypes.c_float], U64),
+    "qsim_prob_c64": ([ctypes.c_float, ctypes.c_float], D),
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),

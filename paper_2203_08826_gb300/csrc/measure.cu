@@ -18,6 +18,127 @@ __device__ __forceinline__ double prob_of(double2 a) {
     return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
 }
 
+// ---- complex64 weights in integer arithmetic
+// floor(p * 2^62) for p = RN_double(re^2 + im^2), the value prob_of gives,
+// without fp64 (GB300's fp64 rate made the fp64 form the sampler's limit).
+// re^2 and im^2 are exact products of the 24-bit significands (subnormals
+// normalised first); the two are aligned in 128 bits (a gap above 79 bits
+// leaves the larger square exactly representable: the smaller one is below
+// half its unit in the last place) and rounded to 53 bits, nearest-even.
+__host__ __device__ inline int clz64_hd(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll(static_cast<long long>(v));
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+__host__ __device__ inline void square_of_float(uint32_t u, uint64_t &M, int &E) {
+    const uint32_t e = u >> 23, m = u & 0x7FFFFFu;
+    uint64_t mant;
+    int ex;
+    if (e == 0) {
+        const int sh = (clz64_hd(m) - 32) - 8;  // leading bit to position 23
+        mant = uint64_t(m) << sh;
+        ex = -149 - sh;
+    } else {
+        mant = m | 0x800000u;
+        ex = int(e) - 150;
+    }
+    M = mant * mant;
+    E = 2 * ex;
+}
+
+// RN_double(re^2 + im^2) as M53 * 2^E53 (M53 < 2^53); returns 0 for zero,
+// 1 for a finite positive value, 2 for NaN, 3 for infinity.
+__host__ __device__ inline int sumsq_rn(float re, float im, uint64_t &M53, int &E53) {
+    uint32_t ux, uy;
+    memcpy(&ux, &re, 4);
+    memcpy(&uy, &im, 4);
+    ux &= 0x7FFFFFFFu;
+    uy &= 0x7FFFFFFFu;
+    if (ux > 0x7F800000u || uy > 0x7F800000u) return 2;
+    if (ux == 0x7F800000u || uy == 0x7F800000u) return 3;
+    if (ux == 0 && uy == 0) return 0;
+    if (ux == 0 || uy == 0) {
+        square_of_float(ux ? ux : uy, M53, E53);
+        return 1;
+    }
+    uint64_t M1, M2;
+    int E1, E2;
+    square_of_float(ux, M1, E1);
+    square_of_float(uy, M2, E2);
+    if (E1 < E2) {
+        const uint64_t tm = M1;
+        M1 = M2;
+        M2 = tm;
+        const int te = E1;
+        E1 = E2;
+        E2 = te;
+    }
+    const int d = E1 - E2;
+    if (d > 79) {
+        M53 = M1;
+        E53 = E1;
+        return 1;
+    }
+    const unsigned __int128 T = (static_cast<unsigned __int128>(M1) << d) + M2;
+    const uint64_t hi = uint64_t(T >> 64), lo = uint64_t(T);
+    const int L = hi ? 128 - clz64_hd(hi) : 64 - clz64_hd(lo);
+    if (L <= 53) {
+        M53 = lo;
+        E53 = E2;
+        return 1;
+    }
+    int sh = L - 53;
+    M53 = uint64_t(T >> sh);
+    const unsigned __int128 rem = T & ((static_cast<unsigned __int128>(1) << sh) - 1);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (M53 & 1))) ++M53;
+    if (M53 == (uint64_t(1) << 53)) {
+        M53 >>= 1;
+        ++sh;
+    }
+    E53 = E2 + sh;
+    return 1;
+}
+
+__host__ __device__ inline uint64_t weight_c64(float re, float im) {
+    uint64_t M53;
+    int E53;
+    const int kind = sumsq_rn(re, im, M53, E53);
+    if (kind == 0 || kind == 2) return 0;
+    if (kind == 3) return uint64_t(1) << 62;
+    if ((64 - clz64_hd(M53)) + E53 > 0) return uint64_t(1) << 62;  // p >= 1
+    const int s = E53 + 62;
+    return s >= 0 ? (M53 << s) : (-s < 64 ? (M53 >> -s) : 0);
+}
+
+// The same value as a double, assembled from its bits (complex64 inputs give
+// normal doubles: a nonzero square is at least 2^-298).
+__host__ __device__ inline double prob_c64(float re, float im) {
+    uint64_t M53;
+    int E53;
+    const int kind = sumsq_rn(re, im, M53, E53);
+    uint64_t bits;
+    if (kind == 0) {
+        bits = 0;
+    } else if (kind == 2) {
+        bits = 0x7FF8000000000000ull;
+    } else if (kind == 3) {
+        bits = 0x7FF0000000000000ull;
+    } else {
+        const int lz = clz64_hd(M53) - 11;  // shift the leading bit to position 52
+        const uint64_t M = M53 << lz;
+        const int E = E53 - lz;             // value = M 2^E, 2^52 <= M < 2^53
+        bits = (uint64_t(E + 1075) << 52) | (M & ((uint64_t(1) << 52) - 1));
+    }
+    double p;
+    memcpy(&p, &bits, 8);
+    return p;
+}
+
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -77,12 +198,25 @@ __global__ void k_probs(const C *__restrict__ psi, uint64_t N, double *__restric
         out[i] = prob_of(psi[i]);
 }
 
+// complex64: the same doubles as prob_of, formed with integer operations
+// (no fp64 per amplitude), two amplitudes per 16-byte load
+__global__ void __launch_bounds__(256) k_probs_c64(const float4 *__restrict__ psi4, uint64_t n4,
+                                                   double2 *__restrict__ out2) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 v = psi4[i];
+        out2[i] = make_double2(prob_c64(v.x, v.y), prob_c64(v.z, v.w));
+    }
+}
+
 int launch_probs(const void *psi, int n, int dtype, double *out, cudaStream_t st) {
     const uint64_t N = uint64_t(1) << n;
     const int T = 256;
     const int blocks = int(std::min<uint64_t>((N + T - 1) / T, uint64_t(sm_count()) * 16));
     LaunchScope ls(K_PROBS, st, double(N) * ((dtype == QSIM_C64 ? 8 : 16) + 8));
-    if (dtype == QSIM_C64)
+    if (dtype == QSIM_C64 && N >= 2 && (reinterpret_cast<uintptr_t>(out) & 15) == 0)
+        k_probs_c64<<<blocks, T, 0, st>>>(static_cast<const float4 *>(psi), N / 2, reinterpret_cast<double2 *>(out));
+    else if (dtype == QSIM_C64)
         k_probs<<<blocks, T, 0, st>>>(static_cast<const float2 *>(psi), N, out);
     else
         k_probs<<<blocks, T, 0, st>>>(static_cast<const double2 *>(psi), N, out);
@@ -659,93 +793,6 @@ __device__ __forceinline__ uint64_t weight_of(double p) {
     return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0);
 }
 
-// ---- complex64 weights in integer arithmetic
-// floor(p * 2^62) for p = RN_double(re^2 + im^2), the value prob_of gives,
-// without fp64 (GB300's fp64 rate made the fp64 form the sampler's limit).
-// re^2 and im^2 are exact products of the 24-bit significands (subnormals
-// normalised first); the two are aligned in 128 bits (a gap above 79 bits
-// leaves the larger square exactly representable: the smaller one is below
-// half its unit in the last place) and rounded to 53 bits, nearest-even.
-__host__ __device__ inline int clz64_hd(uint64_t v) {
-#ifdef __CUDA_ARCH__
-    return __clzll(static_cast<long long>(v));
-#else
-    return v ? __builtin_clzll(v) : 64;
-#endif
-}
-
-__host__ __device__ inline void square_of_float(uint32_t u, uint64_t &M, int &E) {
-    const uint32_t e = u >> 23, m = u & 0x7FFFFFu;
-    uint64_t mant;
-    int ex;
-    if (e == 0) {
-        const int sh = (clz64_hd(m) - 32) - 8;  // leading bit to position 23
-        mant = uint64_t(m) << sh;
-        ex = -149 - sh;
-    } else {
-        mant = m | 0x800000u;
-        ex = int(e) - 150;
-    }
-    M = mant * mant;
-    E = 2 * ex;
-}
-
-__host__ __device__ inline uint64_t weight_c64(float re, float im) {
-    uint32_t ux, uy;
-    memcpy(&ux, &re, 4);
-    memcpy(&uy, &im, 4);
-    ux &= 0x7FFFFFFFu;
-    uy &= 0x7FFFFFFFu;
-    if (ux > 0x7F800000u || uy > 0x7F800000u) return 0;                       // NaN
-    if (ux == 0x7F800000u || uy == 0x7F800000u) return uint64_t(1) << 62;     // infinite
-    if (ux == 0 && uy == 0) return 0;
-    uint64_t M53;
-    int E53;
-    if (ux == 0 || uy == 0) {
-        square_of_float(ux ? ux : uy, M53, E53);
-    } else {
-        uint64_t M1, M2;
-        int E1, E2;
-        square_of_float(ux, M1, E1);
-        square_of_float(uy, M2, E2);
-        if (E1 < E2) {
-            const uint64_t tm = M1;
-            M1 = M2;
-            M2 = tm;
-            const int te = E1;
-            E1 = E2;
-            E2 = te;
-        }
-        const int d = E1 - E2;
-        if (d > 79) {
-            M53 = M1;
-            E53 = E1;
-        } else {
-            const unsigned __int128 T = (static_cast<unsigned __int128>(M1) << d) + M2;
-            const uint64_t hi = uint64_t(T >> 64), lo = uint64_t(T);
-            const int L = hi ? 128 - clz64_hd(hi) : 64 - clz64_hd(lo);
-            if (L <= 53) {
-                M53 = lo;
-                E53 = E2;
-            } else {
-                int sh = L - 53;
-                M53 = uint64_t(T >> sh);
-                const unsigned __int128 rem = T & ((static_cast<unsigned __int128>(1) << sh) - 1);
-                const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
-                if (rem > half || (rem == half && (M53 & 1))) ++M53;
-                if (M53 == (uint64_t(1) << 53)) {
-                    M53 >>= 1;
-                    ++sh;
-                }
-                E53 = E2 + sh;
-            }
-        }
-    }
-    if ((64 - clz64_hd(M53)) + E53 > 0) return uint64_t(1) << 62;  // p >= 1
-    const int s = E53 + 62;
-    return s >= 0 ? (M53 << s) : (-s < 64 ? (M53 >> -s) : 0);
-}
-
 template <int SRC>
 __device__ __forceinline__ double src_prob(const void *src, uint64_t x) {
     if (SRC == SRC_C64) return prob_of(static_cast<const float2 *>(src)[x]);
@@ -1102,6 +1149,7 @@ __global__ void __launch_bounds__(256) k_collapse(C *__restrict__ psi, uint64_t 
 
 // test support: the complex64 sampler weight rule evaluated on the host
 extern "C" uint64_t qsim_sampler_weight_c64(float re, float im) { return qsim::weight_c64(re, im); }
+extern "C" double qsim_prob_c64(float re, float im) { return qsim::prob_c64(re, im); }
 
 extern "C" QSIM_API int qsim_collapse(qsim_state *s, const int *qubits, int m, uint64_t outcome, double *prob_out) {
     using namespace qsim;

@@ -140,6 +140,8 @@ def test_probabilities_and_norm(q, orc, dtype):
     amps = s.to_host().astype(np.complex128)
     rtol = 1e-13 if dtype == "c128" else 1e-12
     np.testing.assert_allclose(s.probabilities(), orc.probabilities(amps), rtol=rtol, atol=0)
+    if dtype == "c64":  # complex64: re^2 + im^2 exact in double, one rounding -- bit for bit
+        np.testing.assert_array_equal(s.probabilities(), amps.real ** 2 + amps.imag ** 2)
     for qubits in [(0,), (13,), (3, 9), (9, 3, 0), tuple(range(12)), (1, 5, 7, 11, 13, 0, 2, 4, 6, 8, 10, 12, 3)]:
         np.testing.assert_allclose(s.probabilities(qubits), orc.probabilities(amps, qubits),
                                    rtol=1e-11, atol=1e-15)

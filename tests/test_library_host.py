@@ -157,3 +157,8 @@ def test_complex64_sampler_weights_match_their_definition():
         cases += list(zip(xs.tolist(), ys.tolist()))
     for re, im in cases:
         assert lib.qsim_sampler_weight_c64(re, im) == want(re, im), (re, im)
+        x, y = float(np.float32(re)), float(np.float32(im))
+        if math.isinf(x) or math.isinf(y):
+            assert lib.qsim_prob_c64(re, im) == math.inf
+        elif not (math.isnan(x) or math.isnan(y)):
+            assert lib.qsim_prob_c64(re, im) == float(Fraction(x) ** 2 + Fraction(y) ** 2), (re, im)
