@@ -93,3 +93,20 @@ def test_adiabatic_steps_with_phase_kernel(q, orc):
             s.apply(inputs.Gate("rx", (qb,), (), (A * dt,)))
     want = orc.simulate(inputs.adiabatic_tfim(n, h, T, dt))
     assert np.max(np.abs(s.to_host() - want)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("nt", [5, 20, 32, 45])
+def test_pauli_phase_general_coefficients_table_and_direct(q, orc, dtype, nt):
+    """Weighted Z strings (QAOA-like costs): up to 32 terms go through
+    per-group sign-pattern tables, more through a direct sine/cosine."""
+    n = 14
+    rng = np.random.default_rng(nt)
+    psi0 = inputs.gaussian_state(n, seed=nt)
+    z = [int(v) for v in rng.integers(1, 1 << n, size=nt)]
+    c = list(rng.standard_normal(nt))
+    s = q.State(n, dtype)
+    s.from_host(psi0)
+    s.apply_pauli_phase(z, c, -0.37)
+    base = psi0.astype(np.complex64).astype(complex) if dtype == "c64" else psi0
+    assert np.max(np.abs(s.to_host() - orc.pauli_phase(base, z, c, -0.37))) <= TOL[dtype]
