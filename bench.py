@@ -41,10 +41,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # writes the whole state once per launch, so traffic scales with 2^n); see
 # profiles/.  Entries are removed whenever the kernel changes.
 NCU_TRAFFIC_30Q_C64 = {
-    "sweep_dense1": 17.6e9,   # 30-qubit capture
+    "sweep_dense1": 16.71e9,  # 27-qubit capture (2.089 GB) x 8
     "stage": 16.70e9,         # 27-qubit capture (2.087 GB) x 8
     "tc_block": 16.73e9,      # 27-qubit capture (2.091 GB) x 8
-    "sweep_densek": 19.61e9,  # 2-qubit blocks, 27-qubit capture (2.451 GB) x 8
+    "sweep_densek": 16.72e9,  # 2-qubit blocks, 27-qubit capture (2.090 GB) x 8
 }
 
 
