@@ -376,6 +376,48 @@ __global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam,
         partial[uint64_t(dp.gslot[g]) * dp.ntiles + blockIdx.x] = gacc[g];
 }
 
+// A marker evaluated after a gate h of the reverse sweep, Im<h lam| P |h psi>,
+// equals Im<lam| h^dag P h |psi> evaluated before it.  Each marker moves ahead
+// of the uncontrolled 1-qubit gates on its qubit that precede it (past other
+// markers and gates on other qubits), its operator conjugated by each, so
+// that consecutive un-applied rotations on one qubit become adjacent and the
+// stage planner merges them into one 2x2 matrix.  A multi-qubit or controlled
+// gate on the qubit stops the marker.
+void hoist_markers(std::vector<GateRec> &gates) {
+    for (size_t i = 0; i < gates.size(); ++i) {
+        if (gates[i].grad_slot < 0) continue;
+        const int q = gates[i].targets[0];
+        cd P[4] = {gates[i].grad_v[2], cd(gates[i].grad_v[0], -gates[i].grad_v[1]),
+                   cd(gates[i].grad_v[0], gates[i].grad_v[1]), -gates[i].grad_v[2]};
+        size_t dest = i;
+        for (size_t j = i; j-- > 0;) {
+            const GateRec &h = gates[j];
+            if (h.grad_slot >= 0) continue;
+            bool on_q = false;
+            for (int t = 0; t < h.k; ++t) on_q |= h.targets[t] == q;
+            for (int t = 0; t < h.nc; ++t) on_q |= h.controls[t] == q;
+            if (!on_q) continue;
+            if (h.k != 1 || h.nc != 0) break;
+            // P <- h^dag P h
+            cd T[4], R[4];
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) T[r * 2 + c] = P[r * 2] * h.m[c] + P[r * 2 + 1] * h.m[2 + c];
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) R[r * 2 + c] = std::conj(h.m[r]) * T[c] + std::conj(h.m[2 + r]) * T[2 + c];
+            std::copy(R, R + 4, P);
+            dest = j;
+        }
+        if (dest == i) continue;
+        GateRec mk = gates[i];
+        // P = [[pz, px - i py], [px + i py, -pz]]
+        mk.grad_v[0] = P[2].real();
+        mk.grad_v[1] = P[2].imag();
+        mk.grad_v[2] = P[0].real();
+        gates.erase(gates.begin() + long(i));
+        gates.insert(gates.begin() + long(dest), mk);
+    }
+}
+
 int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, const HParams &hp, double *grads,
                       double *energies, cudaStream_t st) {
     const int n = c.n;
@@ -438,7 +480,7 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
                 mk.targets[0] = g.targets[0];
                 mk.m = {1.0, 0.0, 0.0, 1.0};
                 mk.grad_slot = rot_of_gate[ii];
-                mk.grad_P = g.kind == QSIM_GATE_RX ? 0 : g.kind == QSIM_GATE_RY ? 1 : 2;
+                mk.grad_v[g.kind == QSIM_GATE_RX ? 0 : g.kind == QSIM_GATE_RY ? 1 : 2] = 1.0;
                 bwd.gates.push_back(mk);
             }
             GateRec inv = g;
@@ -449,6 +491,7 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
                 for (size_t col = 0; col < d; ++col) inv.m[col * d + r] = std::conj(g.m[r * d + col]);
             bwd.gates.push_back(inv);
         }
+        hoist_markers(bwd.gates);
         // forward sweep (staged plan) from |0>
         qsim_plan *fp = nullptr;
         QSIM_TRY(qsim_plan_build(&fwd, DUAL_W, QSIM_FUSE_STAGED, &fp));

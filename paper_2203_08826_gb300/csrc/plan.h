@@ -17,7 +17,7 @@ struct GateRec {
     double params[4] = {};
     int pindex = -1;
     int grad_slot = -1;  // adjoint reverse sweeps only: gradient marker on targets[0]
-    int grad_P = 0;      // its Pauli (0 X, 1 Y, 2 Z)
+    double grad_v[3] = {0, 0, 0};  // its operator px X + py Y + pz Z
     std::vector<cd> m;  // the gate's matrix (2^k x 2^k), built at insertion
 };
 

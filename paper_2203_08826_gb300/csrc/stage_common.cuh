@@ -25,7 +25,7 @@ constexpr int MAX_GRAD = 96;  // gradient slots of one reverse-sweep stage
 // bits (mask in a, matrices consecutive in the pool, lowest bit first);
 // SOP_NEG: sign flips (k pairs in aux from moff): amplitude j of a thread
 // flips once per pair with (base & mask) == mask and bit j of the pattern.
-// SOP_GRAD: adjoint gradient term Im<lambda|P|psi> (a = position, k = Pauli,
+// SOP_GRAD: adjoint gradient term Im<lambda|P|psi> (a = position, k = local slot,
 // moff = slot); only the two-state executor runs it.
 enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3, SOP_U1R = 4, SOP_U1L = 5, SOP_NEG = 6, SOP_GRAD = 7 };
 
@@ -367,12 +367,12 @@ __device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 <<
     }
 }
 
-// Im<w| P |v> over the thread's 16 amplitudes for the Pauli P (0 X, 1 Y, 2 Z)
-// on register bit RB (RB < 0: lane bit a): Im(conj(w_j) (P v)_j).  The
-// register bit is a template argument so that v and w stay in registers.
+// Im<w| P |v> over the thread's 16 amplitudes for P = px X + py Y + pz Z on
+// register bit RB (RB < 0: lane bit a): Im(conj(w_j) (P v)_j).  The register
+// bit is a template argument so that v and w stay in registers.
 template <typename C, int RB>
-__device__ __forceinline__ float grad_partial_t(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int P,
-                                                int lane) {
+__device__ __forceinline__ float grad_partial_t(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a,
+                                                float px, float py, float pz, int lane) {
     constexpr int NR = 1 << REG_BITS;
     float acc = 0.f;
 #pragma unroll
@@ -386,37 +386,32 @@ __device__ __forceinline__ float grad_partial_t(const C (&v)[1 << REG_BITS], con
             partner = v[j ^ (1 << (RB < 0 ? 0 : RB))];
             bit = (j >> (RB < 0 ? 0 : RB)) & 1;
         }
-        C pv;
-        if (P == 0) {  // X
-            pv = partner;
-        } else if (P == 1) {  // Y: (P v)_x = -i v_{x^b} for bit 0, +i v_{x^b} for bit 1
-            pv.x = bit ? -partner.y : partner.y;
-            pv.y = bit ? partner.x : -partner.x;
-        } else {  // Z
-            pv.x = bit ? -v[j].x : v[j].x;
-            pv.y = bit ? -v[j].y : v[j].y;
-        }
-        acc += float(w[j].x) * float(pv.y) - float(w[j].y) * float(pv.x);
+        // X: partner; Y: -i partner (bit 0), +i partner (bit 1); Z: +-v
+        const float sy = bit ? 1.f : -1.f, sz = bit ? -1.f : 1.f;
+        const float pvx = px * float(partner.x) - sy * py * float(partner.y) + sz * pz * float(v[j].x);
+        const float pvy = px * float(partner.y) + sy * py * float(partner.x) + sz * pz * float(v[j].y);
+        acc += float(w[j].x) * pvy - float(w[j].y) * pvx;
     }
     return acc;
 }
 
 // position a: lane bit a < 8, register bit a - 8
 template <typename C>
-__device__ __forceinline__ float grad_partial(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int P,
-                                              int lane) {
+__device__ __forceinline__ float grad_partial(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a,
+                                              float px, float py, float pz, int lane) {
     switch (a - POS_REG) {
-        case 0: return grad_partial_t<C, 0>(v, w, a, P, lane);
-        case 1: return grad_partial_t<C, 1>(v, w, a, P, lane);
-        case 2: return grad_partial_t<C, 2>(v, w, a, P, lane);
-        case 3: return grad_partial_t<C, 3>(v, w, a, P, lane);
-        default: return grad_partial_t<C, -1>(v, w, a, P, lane);
+        case 0: return grad_partial_t<C, 0>(v, w, a, px, py, pz, lane);
+        case 1: return grad_partial_t<C, 1>(v, w, a, px, py, pz, lane);
+        case 2: return grad_partial_t<C, 2>(v, w, a, px, py, pz, lane);
+        case 3: return grad_partial_t<C, 3>(v, w, a, px, py, pz, lane);
+        default: return grad_partial_t<C, -1>(v, w, a, px, py, pz, lane);
     }
 }
 
 // The reverse sweep of the adjoint gradient: the same op list applied to two
-// tiles (psi in v, lambda in w); SOP_GRAD ops (a = position, k = Pauli, moff =
-// local slot) add Im<lambda|P|psi> of the CTA to gacc[slot] (shared, double).
+// tiles (psi in v, lambda in w); SOP_GRAD ops (a = position, k = local slot,
+// pool at moff: (px, py), (pz, 0)) add Im<lambda|P|psi> of the CTA to gacc[slot]
+// (shared, double).
 template <typename C, int W, typename Src>
 __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 << REG_BITS], C (&w)[1 << REG_BITS],
                                             int &ph, uint64_t &base, uint64_t tile_base, C *tile, int lane, int warp,
@@ -438,10 +433,11 @@ __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 <
             continue;
         }
         if (op.type == SOP_GRAD) {
-            double g = grad_partial<C>(v, w, op.a, op.k, lane);
+            const C pxy = src.pool(op.moff), pz = src.pool(op.moff + 1);
+            double g = grad_partial<C>(v, w, op.a, float(pxy.x), float(pxy.y), float(pz.x), lane);
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) g += __shfl_xor_sync(0xffffffffu, g, s);
-            if (lane == 0) atomicAdd(&gacc[op.moff], g);
+            if (lane == 0) atomicAdd(&gacc[op.k], g);
             continue;
         }
         apply_op<C>(op, src, v, base, lane);
@@ -454,7 +450,7 @@ struct GateClass {
     enum { DIAG, DENSE1, DENSE2, OTHER } kind;
     Op op;            // classified form (targets reduced, controls extended)
     int grad_slot = -1;  // >= 0: an adjoint gradient marker on op.targets[0]
-    int grad_P = 0;
+    double grad_v[3] = {0, 0, 0};  // its operator px X + py Y + pz Z
 };
 
 struct Stage {

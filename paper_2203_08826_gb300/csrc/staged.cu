@@ -130,8 +130,8 @@ void batch_ops(Stage &st) {
             }
         }
         StageOp c = o;
-        if (o.type == SOP_U1 || o.type == SOP_U2 || o.type == SOP_DIAG) {
-            const int cnt = o.type == SOP_U1 ? 4 : o.type == SOP_U2 ? 16 : (1 << o.k);
+        if (o.type == SOP_U1 || o.type == SOP_U2 || o.type == SOP_DIAG || o.type == SOP_GRAD) {
+            const int cnt = o.type == SOP_U1 ? 4 : o.type == SOP_U2 ? 16 : o.type == SOP_GRAD ? 2 : (1 << o.k);
             c.moff = int(pool.size());
             pool.insert(pool.end(), st.pool.begin() + o.moff, st.pool.begin() + o.moff + cnt);
         }
@@ -230,12 +230,17 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
                 if (so.dq[t] == (b >= 0 ? POS_REG + b : POS_BASE + q)) return true;
         return false;
     };
-    // index of a preceding uncontrolled U1 on q that nothing after it touches, or -1
-    auto mergeable_u1 = [&](int q) -> int {
+    // index of a preceding uncontrolled U1 on q (or, with `diag`, an
+    // uncontrolled 1-qubit diagonal on q) that nothing after it touches, or -1
+    auto mergeable_u1 = [&](int q, bool diag) -> int {
+        const int b = reg_bit(q);
+        const int8_t dpos = int8_t(b >= 0 ? POS_REG + b : POS_BASE + q);
         for (size_t o = st.ops.size(); o-- > phase_first_op;) {
             const StageOp &prev = st.ops[o];
             if (!touches(prev, q)) continue;
-            if (prev.type == SOP_U1 && prev.a == pos_of(q) && prev.tmask == 0 && prev.rneed == 0) return int(o);
+            if (prev.tmask != 0 || prev.rneed != 0) return -1;
+            if (prev.type == SOP_U1 && prev.a == pos_of(q)) return int(o);
+            if (diag && prev.type == SOP_DIAG && prev.k == 1 && prev.dq[0] == dpos) return int(o);
             return -1;
         }
         return -1;
@@ -245,7 +250,7 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         if (g.kind == GateClass::DIAG) {
             if (g.op.k == 1 && g.op.c == 0) {
                 // fold an uncontrolled 1-qubit diagonal into a preceding U1 on its qubit
-                const int mi = pos_of(g.op.targets[0]) >= 0 ? mergeable_u1(g.op.targets[0]) : -1;
+                const int mi = pos_of(g.op.targets[0]) >= 0 ? mergeable_u1(g.op.targets[0], false) : -1;
                 if (mi >= 0) {
                     StageOp &prev = st.ops[mi];
                     std::vector<cd> old(st.pool.begin() + prev.moff, st.pool.begin() + prev.moff + 4);
@@ -293,8 +298,8 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         if (g.grad_slot >= 0) {
             so.type = SOP_GRAD;
             so.a = int8_t(pos_of(g.op.targets[0]));
-            so.k = int8_t(g.grad_P);
-            so.moff = int(st.grad_slots.size());
+            so.k = int8_t(st.grad_slots.size());
+            so.moff = add_pool({cd(g.grad_v[0], g.grad_v[1]), cd(g.grad_v[2], 0.0)});
             st.grad_slots.push_back(g.grad_slot);
             st.ops.push_back(so);
             continue;
@@ -303,9 +308,17 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
             so.type = SOP_U1;
             so.a = int8_t(pos_of(g.op.targets[0]));
             if (so.tmask == 0 && so.rneed == 0) {
-                const int mi = mergeable_u1(g.op.targets[0]);
+                const int mi = mergeable_u1(g.op.targets[0], true);
                 if (mi >= 0) {
                     StageOp &prev = st.ops[mi];
+                    if (prev.type == SOP_DIAG) {  // U diag(d0, d1) becomes one U1
+                        const cd d0 = st.pool[prev.moff], d1 = st.pool[prev.moff + 1];
+                        const std::vector<cd> &u = g.op.m;
+                        StageOp m1 = so;
+                        m1.moff = add_pool({u[0] * d0, u[1] * d1, u[2] * d0, u[3] * d1});
+                        prev = m1;
+                        continue;
+                    }
                     std::vector<cd> old(st.pool.begin() + prev.moff, st.pool.begin() + prev.moff + 4);
                     std::vector<cd> nw = matmul(g.op.m, old, 2);
                     std::copy(nw.begin(), nw.end(), st.pool.begin() + prev.moff);
@@ -360,7 +373,7 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
             cls[i].op.targets[0] = g.targets[0];
             cls[i].op.m = {1.0, 0.0, 0.0, 1.0};
             cls[i].grad_slot = g.grad_slot;
-            cls[i].grad_P = g.grad_P;
+            for (int t = 0; t < 3; ++t) cls[i].grad_v[t] = g.grad_v[t];
             continue;
         }
         QSIM_TRY(classify(g.m, g.targets, g.k, g.controls, g.nc, cls[i].op));

@@ -93,12 +93,37 @@ def test_adjoint_24q_config_properties(q):
         assert abs((ep[0] - em[0]) / (2 * h) - g128[0, p_]) < 1e-6
 
 
-@pytest.mark.parametrize("maker", ["variational", "mixed"])
+def stacked_ansatz(n, layers, seed):
+    """Runs of rotations on one qubit separated by fixed SU(2) gates and
+    Hadamards (the reverse sweep moves each gradient term ahead of them,
+    conjugating its Pauli), with controlled gates on the same qubits (which
+    stop it) and CZ layers."""
+    rng = np.random.default_rng(seed)
+    gates, p = [], 0
+    for _ in range(layers):
+        for q_ in range(n):
+            for name in ("rx", "ry", "rz", "rx"):
+                gates.append(inputs.Gate(name, (q_,), (), (float(rng.uniform(0, 6.28)),), p)); p += 1
+                if rng.uniform() < 0.3:
+                    gates.append(inputs.Gate("su2", (q_,), (), inputs.haar_su2_quaternion(rng)))
+            if q_ % 3 == 0:
+                gates.append(inputs.Gate("h", (q_,)))
+        for i in range(0, n - 1, 2):
+            gates.append(inputs.Gate("cz", (i, i + 1)))
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        gates.append(inputs.Gate("x", (a,), (b,)))
+        gates.append(inputs.Gate("ry", (b,), (), (float(rng.uniform(0, 6.28)),), p)); p += 1
+    return inputs.Circuit(n, gates)
+
+
+@pytest.mark.parametrize("maker", ["variational", "mixed", "stacked"])
 def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker):
     """complex64 from 12 qubits runs the reverse sweep as two-state register
     tiles (gradient terms accumulated per CTA): all gradients vs the oracle."""
-    circ = inputs.variational(13, 2, seed=7) if maker == "variational" else mixed_ansatz(13, 2, seed=8)
-    ham = inputs.tfim(13)
+    circ = {"variational": lambda: inputs.variational(13, 2, seed=7),
+            "mixed": lambda: mixed_ansatz(13, 2, seed=8),
+            "stacked": lambda: stacked_ansatz(12, 2, seed=10)}[maker]()
+    ham = inputs.tfim(circ.n)
     rng = np.random.default_rng(9)
     thetas = rng.uniform(0, 2 * np.pi, size=(2, circ.nparams))
     grads, en = q.adjoint_grad(circ, ham, thetas, "c64")
