@@ -122,10 +122,21 @@ struct HParams {
     int t0[HAPPLY_GROUPS + 1];
     uint64_t Z[HAPPLY_TERMS];
     double cr[HAPPLY_TERMS], ci[HAPPLY_TERMS];
+    float fr[HAPPLY_TERMS], fi[HAPPLY_TERMS];  // the same, rounded once for complex64
 };
 
+__device__ __forceinline__ void hcoef(const HParams &h, int t, float &r, float &i) {
+    r = h.fr[t];
+    i = h.fi[t];
+}
+__device__ __forceinline__ void hcoef(const HParams &h, int t, double &r, double &i) {
+    r = h.cr[t];
+    i = h.ci[t];
+}
+
 // Arithmetic in the state's own precision (fp32 for complex64: lambda is
-// stored in complex64 anyway), so the fp64 units are not on this path.
+// stored in complex64 anyway; the coefficients are rounded to fp32 on the
+// host), so the fp64 units are not on this path.
 template <typename C>
 __global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__restrict__ lam, uint64_t N,
                                                 const __grid_constant__ HParams h) {
@@ -140,8 +151,10 @@ __global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__
             R fr = 0, fi = 0;
             for (int t = h.t0[g]; t < h.t0[g + 1]; ++t) {
                 const bool odd = __popcll(x & h.Z[t]) & 1;
-                fr += odd ? -R(h.cr[t]) : R(h.cr[t]);
-                fi += odd ? -R(h.ci[t]) : R(h.ci[t]);
+                R cr, ci;
+                hcoef(h, t, cr, ci);
+                fr += odd ? -cr : cr;
+                fi += odd ? -ci : ci;
             }
             sr += fr * a.x - fi * a.y;
             si += fr * a.y + fi * a.x;
@@ -158,8 +171,22 @@ __global__ void __launch_bounds__(256) k_dot_re(const C *__restrict__ a, const C
                                                 double *__restrict__ partial) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     double acc = 0;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-        acc += double(a[i].x) * b[i].x + double(a[i].y) * b[i].y;
+    if constexpr (sizeof(a[0].x) == 4) {
+        // complex64: fp32 sums of 8 terms, added in double (fp64 runs at 1/64
+        // of the fp32 rate)
+        for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < N; i0 += 8 * stride) {
+            float f = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t i = i0 + uint64_t(u) * stride;
+                if (i < N) f = fmaf(a[i].x, b[i].x, fmaf(a[i].y, b[i].y, f));
+            }
+            acc += double(f);
+        }
+    } else {
+        for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+            acc += double(a[i].x) * b[i].x + double(a[i].y) * b[i].y;
+    }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -332,8 +359,9 @@ int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HPar
 // complex64, n >= 12: the reverse sweep runs as register-tile stages over both
 // states at once (tiles of 2^12 amplitudes, the forward sweep as a staged
 // plan).  Each rotation's gradient is a SOP_GRAD op of the stage holding its
-// qubit; the CTA sums it in shared memory (double) and writes one partial per
-// tile, reduced per rotation afterwards.
+// qubit; each warp sums it in fp32 into its own shared-memory slot, the CTA
+// adds its warps' sums in double and writes one partial per tile, reduced per
+// rotation afterwards.
 constexpr int DUAL_W = 3;
 
 struct DualParams {
@@ -357,9 +385,9 @@ __global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam,
     using namespace stage;
     extern __shared__ unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ double gacc[MAX_GRAD];
+    __shared__ float gw[MAX_GRAD << W];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x) gacc[g] = 0.0;
+    for (int g = threadIdx.x; g < (dp.ngrad << W); g += blockDim.x) gw[g] = 0.f;
     __syncthreads();
     const uint64_t tile_base = expand(blockIdx.x, dp.sp.outer);
     int ph = dp.sp.phase0;
@@ -368,12 +396,16 @@ __global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam,
     tile_global<float2, W, false>(psi, v, dp.sp.phases[ph], base);
     tile_global<float2, W, false>(lam, w, dp.sp.phases[ph], base);
     const DualSrc src{dp.sp};
-    stage_exec2<float2, W>(src, dp.sp.nops, v, w, ph, base, tile_base, tile, lane, warp, gacc);
+    stage_exec2<float2, W>(src, dp.sp.nops, v, w, ph, base, tile_base, tile, lane, warp, gw);
     tile_global<float2, W, true>(psi, v, dp.sp.phases[ph], base);
     tile_global<float2, W, true>(lam, w, dp.sp.phases[ph], base);
     __syncthreads();
-    for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x)
-        partial[uint64_t(dp.gslot[g]) * dp.ntiles + blockIdx.x] = gacc[g];
+    for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < (1 << W); ++i) t += double(gw[(g << W) + i]);
+        partial[uint64_t(dp.gslot[g]) * dp.ntiles + blockIdx.x] = t;
+    }
 }
 
 // A marker evaluated after a gate h of the reverse sweep, Im<h lam| P |h psi>,
@@ -583,6 +615,8 @@ extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, co
             hp.Z[nt] = zmask[t];
             hp.cr[nt] = coeff[t] * re[ny & 3];
             hp.ci[nt] = coeff[t] * im[ny & 3];
+            hp.fr[nt] = float(hp.cr[nt]);
+            hp.fi[nt] = float(hp.ci[nt]);
             ++nt;
         }
         ++hp.ngroups;

@@ -410,12 +410,15 @@ __device__ __forceinline__ float grad_partial(const C (&v)[1 << REG_BITS], const
 
 // The reverse sweep of the adjoint gradient: the same op list applied to two
 // tiles (psi in v, lambda in w); SOP_GRAD ops (a = position, k = local slot,
-// pool at moff: (px, py), (pz, 0)) add Im<lambda|P|psi> of the CTA to gacc[slot]
-// (shared, double).
+// pool at moff: (px, py), (pz, 0)) add the warp's share of Im<lambda|P|psi>
+// to gw[slot * 2^W + warp] (shared; each entry belongs to one warp, so no
+// atomics).  The sums stay in fp32 up to the warp: fp64 runs at 1/64 of the
+// fp32 rate here, and a per-lane conversion plus a five-step fp64 shuffle
+// tree per gradient op cost more than all the gate arithmetic of a stage.
 template <typename C, int W, typename Src>
 __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 << REG_BITS], C (&w)[1 << REG_BITS],
                                             int &ph, uint64_t &base, uint64_t tile_base, C *tile, int lane, int warp,
-                                            double *gacc) {
+                                            float *gw) {
     for (int o = 0; o < nops; ++o) {
         const StageOp &op = src.op(o);
         if (op.type == SOP_EXCHANGE) {
@@ -434,10 +437,10 @@ __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 <
         }
         if (op.type == SOP_GRAD) {
             const C pxy = src.pool(op.moff), pz = src.pool(op.moff + 1);
-            double g = grad_partial<C>(v, w, op.a, float(pxy.x), float(pxy.y), float(pz.x), lane);
+            float g = grad_partial<C>(v, w, op.a, float(pxy.x), float(pxy.y), float(pz.x), lane);
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) g += __shfl_xor_sync(0xffffffffu, g, s);
-            if (lane == 0) atomicAdd(&gacc[op.k], g);
+            if (lane == 0) gw[(op.k << W) + warp] += g;
             continue;
         }
         apply_op<C>(op, src, v, base, lane);
