@@ -366,10 +366,13 @@ constexpr int DUAL_W = 3;
 
 struct DualParams {
     stage::StageParams<float2> sp;
-    int ngrad;
-    int gslot[stage::MAX_GRAD];
+    int ngrad, ngradops;
+    int gslot[stage::MAX_GRAD];     // gradient term g: global slot,
+    int gop[stage::MAX_GRAD];       // the SOP_GRAD op whose sums it combines,
+    float gv[stage::MAX_GRAD][3];   // and its Pauli vector
     uint64_t ntiles;
 };
+static_assert(sizeof(DualParams) <= 32764, "two-state stage parameters exceed the kernel parameter limit");
 
 struct DualSrc {
     const stage::StageParams<float2> &p;
@@ -385,9 +388,9 @@ __global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam,
     using namespace stage;
     extern __shared__ unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ float gw[MAX_GRAD << W];
+    __shared__ float gw[(3 * MAX_GRAD) << W];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int g = threadIdx.x; g < (dp.ngrad << W); g += blockDim.x) gw[g] = 0.f;
+    for (int g = threadIdx.x; g < ((3 * dp.ngradops) << W); g += blockDim.x) gw[g] = 0.f;
     __syncthreads();
     const uint64_t tile_base = expand(blockIdx.x, dp.sp.outer);
     int ph = dp.sp.phase0;
@@ -401,9 +404,11 @@ __global__ void __launch_bounds__(32 << W) k_adj_stage(float2 *psi, float2 *lam,
     tile_global<float2, W, true>(lam, w, dp.sp.phases[ph], base);
     __syncthreads();
     for (int g = threadIdx.x; g < dp.ngrad; g += blockDim.x) {
+        const float *s = gw + ((3 * dp.gop[g]) << W);
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < (1 << W); ++i) t += double(gw[(g << W) + i]);
+        for (int i = 0; i < (1 << W); ++i)
+            t += double(dp.gv[g][0]) * s[i] + double(dp.gv[g][1]) * s[(1 << W) + i] + double(dp.gv[g][2]) * s[(2 << W) + i];
         partial[uint64_t(dp.gslot[g]) * dp.ntiles + blockIdx.x] = t;
     }
 }
@@ -557,8 +562,13 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
             DualParams dp;
             memset(&dp, 0, sizeof dp);
             stage::make_params<float2>(sg, dp.sp);
-            dp.ngrad = int(sg.grad_slots.size());
-            for (int g = 0; g < dp.ngrad; ++g) dp.gslot[g] = sg.grad_slots[g];
+            dp.ngrad = int(sg.grads.size());
+            dp.ngradops = sg.ngradops;
+            for (int g = 0; g < dp.ngrad; ++g) {
+                dp.gslot[g] = sg.grads[g].slot;
+                dp.gop[g] = sg.grads[g].op;
+                for (int c = 0; c < 3; ++c) dp.gv[g][c] = float(sg.grads[g].v[c]);
+            }
             dp.ntiles = ntiles;
             LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2));
             k_adj_stage<DUAL_W><<<unsigned(ntiles), 32 << DUAL_W, smem, st>>>(psi, lam, dp, partial);

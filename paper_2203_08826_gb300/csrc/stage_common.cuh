@@ -19,14 +19,15 @@ constexpr int MAX_OPS = 192;
 constexpr int MAX_PHASES = 24;
 constexpr int MAX_POOL = 768;
 constexpr int MAX_AUX = 192;  // (thread mask, register pattern) pairs of batched sign flips
-constexpr int MAX_GRAD = 96;  // gradient slots of one reverse-sweep stage
+constexpr int MAX_GRAD = 96;  // gradient terms (and SOP_GRAD ops) of one reverse-sweep stage
 
 // SOP_U1R / SOP_U1L: uncontrolled 1-qubit gates on distinct register / lane
 // bits (mask in a, matrices consecutive in the pool, lowest bit first);
 // SOP_NEG: sign flips (k pairs in aux from moff): amplitude j of a thread
 // flips once per pair with (base & mask) == mask and bit j of the pattern.
-// SOP_GRAD: adjoint gradient term Im<lambda|P|psi> (a = position, k = local slot,
-// moff = slot); only the two-state executor runs it.
+// SOP_GRAD: the sums from which the adjoint gradient terms Im<lambda|P|psi> on
+// one qubit follow (a = position, k = local index); only the two-state
+// executor runs it.
 enum SopType : int8_t { SOP_U1 = 0, SOP_U2 = 1, SOP_DIAG = 2, SOP_EXCHANGE = 3, SOP_U1R = 4, SOP_U1L = 5, SOP_NEG = 6, SOP_GRAD = 7 };
 
 // Position codes: 0..4 lane bit, 8 + b register bit b, 32 + q bit q of the
@@ -367,54 +368,64 @@ __device__ __forceinline__ void stage_exec(const Src &src, int nops, C (&v)[1 <<
     }
 }
 
-// Im<w| P |v> over the thread's 16 amplitudes for P = px X + py Y + pz Z on
-// register bit RB (RB < 0: lane bit a): Im(conj(w_j) (P v)_j).  The register
-// bit is a template argument so that v and w stay in registers.
+// For a gradient term on qubit position a: with M[r][c] = sum conj(w_r) v_c
+// over the pairs (r, c = the qubit's value), Im<w| px X + py Y + pz Z |v> =
+// px Sx + py Sy + pz Sz with
+//   Sx = Im M01 + Im M10,  Sy = Re M10 - Re M01,  Sz = Im M00 - Im M11.
+// This adds the thread's share of (Sx, Sy, Sz) over its 16 amplitudes
+// (register bit RB; RB < 0: lane bit a, each lane taking the terms whose w
+// it holds).  Every term on one qubit at one point of the sweep shares the
+// three sums, whatever its Pauli vector.
 template <typename C, int RB>
-__device__ __forceinline__ float grad_partial_t(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a,
-                                                float px, float py, float pz, int lane) {
+__device__ __forceinline__ void grad3_t(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int lane,
+                                        float &sx, float &sy, float &sz) {
     constexpr int NR = 1 << REG_BITS;
-    float acc = 0.f;
+    if constexpr (RB >= 0) {
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        C partner;
-        int bit;
-        if (RB < 0) {
-            partner = shfl_c(v[j], 1 << a);
-            bit = (lane >> a) & 1;
-        } else {
-            partner = v[j ^ (1 << (RB < 0 ? 0 : RB))];
-            bit = (j >> (RB < 0 ? 0 : RB)) & 1;
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << RB)) continue;
+            const C p0 = v[j], p1 = v[j | (1 << RB)], l0 = w[j], l1 = w[j | (1 << RB)];
+            sz += float(l0.x) * float(p0.y) - float(l0.y) * float(p0.x) - float(l1.x) * float(p1.y) +
+                  float(l1.y) * float(p1.x);
+            sx += float(l0.x) * float(p1.y) - float(l0.y) * float(p1.x) + float(l1.x) * float(p0.y) -
+                  float(l1.y) * float(p0.x);
+            sy += float(l1.x) * float(p0.x) + float(l1.y) * float(p0.y) - float(l0.x) * float(p1.x) -
+                  float(l0.y) * float(p1.y);
         }
-        // X: partner; Y: -i partner (bit 0), +i partner (bit 1); Z: +-v
-        const float sy = bit ? 1.f : -1.f, sz = bit ? -1.f : 1.f;
-        const float pvx = px * float(partner.x) - sy * py * float(partner.y) + sz * pz * float(v[j].x);
-        const float pvy = px * float(partner.y) + sy * py * float(partner.x) + sz * pz * float(v[j].y);
-        acc += float(w[j].x) * pvy - float(w[j].y) * pvx;
+    } else {
+        float tx = 0.f, ty = 0.f, tz = 0.f;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const C p = v[j], l = w[j], q = shfl_c(v[j], 1 << a);  // q: the partner's amplitude
+            tz += float(l.x) * float(p.y) - float(l.y) * float(p.x);
+            tx += float(l.x) * float(q.y) - float(l.y) * float(q.x);
+            ty += float(l.x) * float(q.x) + float(l.y) * float(q.y);
+        }
+        const bool one = (lane >> a) & 1;
+        sx += tx;
+        sy += one ? ty : -ty;
+        sz += one ? -tz : tz;
     }
-    return acc;
 }
 
 // position a: lane bit a < 8, register bit a - 8
 template <typename C>
-__device__ __forceinline__ float grad_partial(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a,
-                                              float px, float py, float pz, int lane) {
+__device__ __forceinline__ void grad3(const C (&v)[1 << REG_BITS], const C (&w)[1 << REG_BITS], int a, int lane,
+                                      float &sx, float &sy, float &sz) {
     switch (a - POS_REG) {
-        case 0: return grad_partial_t<C, 0>(v, w, a, px, py, pz, lane);
-        case 1: return grad_partial_t<C, 1>(v, w, a, px, py, pz, lane);
-        case 2: return grad_partial_t<C, 2>(v, w, a, px, py, pz, lane);
-        case 3: return grad_partial_t<C, 3>(v, w, a, px, py, pz, lane);
-        default: return grad_partial_t<C, -1>(v, w, a, px, py, pz, lane);
+        case 0: grad3_t<C, 0>(v, w, a, lane, sx, sy, sz); break;
+        case 1: grad3_t<C, 1>(v, w, a, lane, sx, sy, sz); break;
+        case 2: grad3_t<C, 2>(v, w, a, lane, sx, sy, sz); break;
+        case 3: grad3_t<C, 3>(v, w, a, lane, sx, sy, sz); break;
+        default: grad3_t<C, -1>(v, w, a, lane, sx, sy, sz); break;
     }
 }
 
 // The reverse sweep of the adjoint gradient: the same op list applied to two
-// tiles (psi in v, lambda in w); SOP_GRAD ops (a = position, k = local slot,
-// pool at moff: (px, py), (pz, 0)) add the warp's share of Im<lambda|P|psi>
-// to gw[slot * 2^W + warp] (shared; each entry belongs to one warp, so no
-// atomics).  The sums stay in fp32 up to the warp: fp64 runs at 1/64 of the
-// fp32 rate here, and a per-lane conversion plus a five-step fp64 shuffle
-// tree per gradient op cost more than all the gate arithmetic of a stage.
+// tiles (psi in v, lambda in w); a SOP_GRAD op (a = position, k = its local
+// index) adds the warp's share of (Sx, Sy, Sz) to gw[(3k + c) * 2^W + warp]
+// (shared; each entry belongs to one warp, so no atomics).  The sums stay in
+// fp32 up to the warp: fp64 runs at 1/64 of the fp32 rate here.
 template <typename C, int W, typename Src>
 __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 << REG_BITS], C (&w)[1 << REG_BITS],
                                             int &ph, uint64_t &base, uint64_t tile_base, C *tile, int lane, int warp,
@@ -436,11 +447,20 @@ __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 <
             continue;
         }
         if (op.type == SOP_GRAD) {
-            const C pxy = src.pool(op.moff), pz = src.pool(op.moff + 1);
-            float g = grad_partial<C>(v, w, op.a, float(pxy.x), float(pxy.y), float(pz.x), lane);
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            grad3<C>(v, w, op.a, lane, sx, sy, sz);
 #pragma unroll
-            for (int s = 16; s > 0; s >>= 1) g += __shfl_xor_sync(0xffffffffu, g, s);
-            if (lane == 0) gw[(op.k << W) + warp] += g;
+            for (int s = 16; s > 0; s >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, s);
+                sy += __shfl_xor_sync(0xffffffffu, sy, s);
+                sz += __shfl_xor_sync(0xffffffffu, sz, s);
+            }
+            if (lane == 0) {
+                float *g = gw + ((3 * op.k) << W) + warp;
+                g[0] += sx;
+                g[1 << W] += sy;
+                g[2 << W] += sz;
+            }
             continue;
         }
         apply_op<C>(op, src, v, base, lane);
@@ -464,7 +484,13 @@ struct Stage {
     std::vector<Phase> phases;
     std::vector<cd> pool;
     std::vector<uint64_t> aux;
-    std::vector<int> grad_slots;  // global gradient slot of each local SOP_GRAD slot
+    struct GradRef {
+        int slot;     // global gradient slot
+        int op;       // local SOP_GRAD index whose (Sx, Sy, Sz) it combines
+        double v[3];  // its Pauli vector
+    };
+    std::vector<GradRef> grads;
+    int ngradops = 0;
     int phase0 = 0;
 };
 

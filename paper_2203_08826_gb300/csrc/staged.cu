@@ -130,8 +130,8 @@ void batch_ops(Stage &st) {
             }
         }
         StageOp c = o;
-        if (o.type == SOP_U1 || o.type == SOP_U2 || o.type == SOP_DIAG || o.type == SOP_GRAD) {
-            const int cnt = o.type == SOP_U1 ? 4 : o.type == SOP_U2 ? 16 : o.type == SOP_GRAD ? 2 : (1 << o.k);
+        if (o.type == SOP_U1 || o.type == SOP_U2 || o.type == SOP_DIAG) {
+            const int cnt = o.type == SOP_U1 ? 4 : o.type == SOP_U2 ? 16 : (1 << o.k);
             c.moff = int(pool.size());
             pool.insert(pool.end(), st.pool.begin() + o.moff, st.pool.begin() + o.moff + cnt);
         }
@@ -296,12 +296,25 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
         StageOp so{};
         split_controls(g.op, so);
         if (g.grad_slot >= 0) {
-            so.type = SOP_GRAD;
-            so.a = int8_t(pos_of(g.op.targets[0]));
-            so.k = int8_t(st.grad_slots.size());
-            so.moff = add_pool({cd(g.grad_v[0], g.grad_v[1]), cd(g.grad_v[2], 0.0)});
-            st.grad_slots.push_back(g.grad_slot);
-            st.ops.push_back(so);
+            // terms on one qubit with nothing touching it in between share one op
+            const int q = g.op.targets[0];
+            int gop = -1;
+            for (size_t o = st.ops.size(); o-- > phase_first_op;) {
+                const StageOp &prev = st.ops[o];
+                if (prev.type == SOP_GRAD && prev.a == pos_of(q) && prev.tmask == 0 && prev.rneed == 0) {
+                    gop = prev.k;
+                    break;
+                }
+                if (touches(prev, q)) break;
+            }
+            if (gop < 0) {
+                so.type = SOP_GRAD;
+                so.a = int8_t(pos_of(q));
+                so.k = int8_t(std::min(st.ngradops, 127));
+                gop = st.ngradops++;
+                st.ops.push_back(so);
+            }
+            st.grads.push_back({g.grad_slot, gop, {g.grad_v[0], g.grad_v[1], g.grad_v[2]}});
             continue;
         }
         if (g.kind == GateClass::DENSE1) {
@@ -336,7 +349,7 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
     batch_ops(st);
     if (limits && (st.ops.size() > size_t(MAX_OPS) || st.phases.size() > size_t(MAX_PHASES) ||
                    st.pool.size() > size_t(MAX_POOL) || st.aux.size() > size_t(2 * MAX_AUX) ||
-                   st.grad_slots.size() > size_t(MAX_GRAD)))
+                   st.grads.size() > size_t(MAX_GRAD)))
         return QSIM_EUNSUPPORTED;
     return QSIM_OK;
 }
