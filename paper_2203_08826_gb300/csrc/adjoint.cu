@@ -139,7 +139,7 @@ __device__ __forceinline__ void hcoef(const HParams &h, int t, double &r, double
 // host), so the fp64 units are not on this path.
 template <typename C>
 __global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__restrict__ lam, uint64_t N,
-                                                const __grid_constant__ HParams h) {
+                                                const __grid_constant__ HParams h, int accumulate) {
     using R = decltype(C::x);
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
@@ -159,12 +159,262 @@ __global__ void __launch_bounds__(256) k_happly(const C *__restrict__ psi, C *__
             sr += fr * a.x - fi * a.y;
             si += fr * a.y + fi * a.x;
         }
-        C o;
-        o.x = sr;
-        o.y = si;
+        C o = accumulate ? lam[y] : C{};
+        o.x += sr;
+        o.y += si;
         lam[y] = o;
     }
 }
+
+// Tiled form for the groups whose X mask lies inside a tile: a CTA holds
+// the 2^(5 + m) amplitudes whose index varies over bits 0..4 and the chunk
+// [c0, c0 + m) (the other bits fixed by the tile id) in shared memory, so
+// psi[y ^ X_g] is a shared-memory read; lambda is written by the first pass
+// and accumulated by the others.  Bits 0..4 in every tile keep the global
+// accesses 256-byte contiguous per warp.  Each thread holds PER amplitudes
+// and walks the groups and terms once for all of them.  The diagonal group
+// (X = 0, real coefficients, up to 64 Z strings) is evaluated from tables:
+// the parity of every term is one XOR of per-byte masks of the index,
+// P(y) = XOR_b ptab[b][byte b of y], and f(y) = sum_j stab[j][byte j of P]
+// with stab[j][m] = sum over the 8 terms of byte j of c_t (-1)^(bit of m).
+struct HTile {
+    int c0, m, first, ng;
+    int dg;                        // pass-local index of the table group, or -1
+    int nbytes, nsum;              // its table sizes (index bytes, term bytes)
+    int gidx[HAPPLY_GROUPS];       // groups of this pass (indices into HParams)
+    uint32_t xl[HAPPLY_GROUPS];    // their X masks in tile coordinates
+};
+constexpr int HTAB_TERMS = 64;
+
+template <typename C, int PER>
+__global__ void __launch_bounds__(256) k_happly_tile(const C *__restrict__ psi, C *__restrict__ lam,
+                                                     const __grid_constant__ HParams h,
+                                                     const __grid_constant__ HTile tp,
+                                                     const void *__restrict__ tabs) {
+    using R = decltype(C::x);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t TN = 1u << (5 + tp.m);
+    C *tile = reinterpret_cast<C *>(smem_raw);
+    uint64_t *ptab = reinterpret_cast<uint64_t *>(tile + TN);
+    R *stab = reinterpret_cast<R *>(ptab + tp.nbytes * 256);
+    const uint64_t t = blockIdx.x;
+    const uint64_t lowm = (uint64_t(1) << (tp.c0 - 5)) - 1;
+    const uint64_t base = ((t & lowm) << 5) | ((t >> (tp.c0 - 5)) << (tp.c0 + tp.m));
+    auto glob = [&](uint32_t l) { return base | uint64_t(l & 31u) | (uint64_t(l >> 5) << tp.c0); };
+    for (uint32_t l = threadIdx.x; l < TN; l += blockDim.x) tile[l] = psi[glob(l)];
+    if (tp.dg >= 0) {
+        const uint64_t *gp = static_cast<const uint64_t *>(tabs);
+        for (int i = threadIdx.x; i < tp.nbytes * 256; i += blockDim.x) ptab[i] = gp[i];
+        const R *gs = reinterpret_cast<const R *>(gp + tp.nbytes * 256);
+        for (int i = threadIdx.x; i < tp.nsum * 256; i += blockDim.x) stab[i] = gs[i];
+    }
+    __syncthreads();
+    uint64_t y[PER];
+    R sr[PER], si[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        y[u] = glob(threadIdx.x + uint32_t(u) * blockDim.x);
+        sr[u] = 0;
+        si[u] = 0;
+    }
+    for (int g = 0; g < tp.ng; ++g) {
+        if (g == tp.dg) {
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                uint64_t P = 0;
+                for (int b = 0; b < tp.nbytes; ++b) P ^= ptab[b * 256 + int((y[u] >> (8 * b)) & 255)];
+                R f = 0;
+                for (int j = 0; j < tp.nsum; ++j) f += stab[j * 256 + int((P >> (8 * j)) & 255)];
+                const C a = tile[threadIdx.x + uint32_t(u) * blockDim.x];
+                sr[u] += f * a.x;
+                si[u] += f * a.y;
+            }
+            continue;
+        }
+        const int gi = tp.gidx[g];
+        const uint64_t X = h.X[gi];
+        const uint32_t xl = tp.xl[g];
+        R fr[PER], fi[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) fr[u] = fi[u] = 0;
+        for (int k = h.t0[gi]; k < h.t0[gi + 1]; ++k) {
+            const uint64_t Z = h.Z[k];
+            R cr, ci;
+            hcoef(h, k, cr, ci);
+            if (Z == 0) {  // pure X string: a constant factor
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    fr[u] += cr;
+                    fi[u] += ci;
+                }
+                continue;
+            }
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const bool odd = __popcll((y[u] ^ X) & Z) & 1;
+                fr[u] += odd ? -cr : cr;
+                fi[u] += odd ? -ci : ci;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const C a = tile[(threadIdx.x + uint32_t(u) * blockDim.x) ^ xl];
+            sr[u] += fr[u] * a.x - fi[u] * a.y;
+            si[u] += fr[u] * a.y + fi[u] * a.x;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        C o = tp.first ? C{} : lam[y[u]];
+        o.x += sr[u];
+        o.y += si[u];
+        lam[y[u]] = o;
+    }
+}
+
+// lambda = H psi: tiled passes for every group whose X mask fits a tile
+// (bits 0..T-1, then bits 0..4 plus successive chunks of the high bits),
+// one gather pass for the rest.  Built once per Hamiltonian and state size.
+template <typename C>
+struct HPlan {
+    using R = decltype(C::x);
+    int n = 0;
+    std::vector<HTile> passes;
+    HParams left;
+    bool gather = false;  // the gather pass runs (groups fitting no tile)
+    void *dtabs = nullptr;
+    ~HPlan() {
+        if (dtabs) cudaFree(dtabs);
+    }
+
+    int build(const HParams &hp, int n_, cudaStream_t st) {
+        n = n_;
+        const int TBMAX = sizeof(C) == 8 ? 12 : 11;  // 32 KiB tiles
+        if (n >= TBMAX) {
+            HTile t0{};
+            t0.c0 = 5;
+            t0.m = TBMAX - 5;
+            t0.dg = -1;
+            passes.push_back(t0);
+            for (int c0 = TBMAX; c0 < n;) {
+                HTile t{};
+                t.c0 = c0;
+                t.m = std::min(TBMAX - 5, n - c0);
+                t.dg = -1;
+                passes.push_back(t);
+                c0 += t.m;
+            }
+        }
+        memset(&left, 0, sizeof left);
+        int nt = 0;
+        for (int g = 0; g < hp.ngroups; ++g) {
+            bool placed = false;
+            for (HTile &t : passes) {
+                const uint64_t B = 31u | (((uint64_t(1) << t.m) - 1) << t.c0);
+                if (hp.X[g] & ~B) continue;
+                const int nterm = hp.t0[g + 1] - hp.t0[g];
+                if (hp.X[g] == 0 && t.dg < 0 && nterm > 4 && nterm <= HTAB_TERMS) {
+                    // tables for the diagonal group
+                    t.dg = t.ng;
+                    t.nbytes = (n + 7) / 8;
+                    t.nsum = (nterm + 7) / 8;
+                    std::vector<uint64_t> pt(size_t(t.nbytes) * 256, 0);
+                    std::vector<R> sm(size_t(t.nsum) * 256, R(0));
+                    for (int b = 0; b < t.nbytes; ++b)
+                        for (int v = 0; v < 256; ++v)
+                            for (int k = 0; k < nterm; ++k)
+                                if (__builtin_popcountll((hp.Z[hp.t0[g] + k] >> (8 * b)) & uint64_t(v)) & 1)
+                                    pt[size_t(b) * 256 + size_t(v)] |= uint64_t(1) << k;
+                    for (int j = 0; j < t.nsum; ++j)
+                        for (int v = 0; v < 256; ++v) {
+                            double f = 0;
+                            for (int k = 8 * j; k < std::min(nterm, 8 * j + 8); ++k)
+                                f += ((v >> (k - 8 * j)) & 1) ? -hp.cr[hp.t0[g] + k] : hp.cr[hp.t0[g] + k];
+                            sm[size_t(j) * 256 + size_t(v)] = R(f);
+                        }
+                    const size_t pb = pt.size() * sizeof(uint64_t), sb = sm.size() * sizeof(R);
+                    QSIM_CUDA_TRY(cudaMalloc(&dtabs, pb + sb), "hamiltonian tables");
+                    QSIM_CUDA_TRY(cudaMemcpyAsync(dtabs, pt.data(), pb, cudaMemcpyHostToDevice, st), "hamiltonian tables");
+                    QSIM_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(dtabs) + pb, sm.data(), sb,
+                                                  cudaMemcpyHostToDevice, st),
+                                  "hamiltonian tables");
+                    QSIM_CUDA_TRY(cudaStreamSynchronize(st), "hamiltonian tables");
+                }
+                t.gidx[t.ng] = g;
+                t.xl[t.ng] = uint32_t((hp.X[g] & 31u) | ((hp.X[g] >> t.c0) << 5));
+                ++t.ng;
+                placed = true;
+                break;
+            }
+            if (placed) continue;
+            left.X[left.ngroups] = hp.X[g];
+            left.t0[left.ngroups] = nt;
+            for (int k = hp.t0[g]; k < hp.t0[g + 1]; ++k, ++nt) {
+                left.Z[nt] = hp.Z[k];
+                left.cr[nt] = hp.cr[k];
+                left.ci[nt] = hp.ci[k];
+                left.fr[nt] = hp.fr[k];
+                left.fi[nt] = hp.fi[k];
+            }
+            ++left.ngroups;
+            left.t0[left.ngroups] = nt;
+        }
+        bool first = true;
+        for (HTile &t : passes) {
+            if (t.ng == 0) continue;
+            t.first = first ? 1 : 0;
+            first = false;
+        }
+        gather = left.ngroups > 0;
+        return QSIM_OK;
+    }
+
+    static size_t smem_of(const HTile &t) {
+        return (size_t(1) << (5 + t.m)) * sizeof(C) +
+               (t.dg >= 0 ? size_t(t.nbytes) * 256 * 8 + size_t(t.nsum) * 256 * sizeof(R) : 0);
+    }
+
+    template <int PER>
+    int launch(const C *psi, C *lam, const HParams &hp, const HTile &t, unsigned threads, cudaStream_t st) {
+        static bool attr = false;
+        if (!attr) {
+            QSIM_CUDA_TRY(cudaFuncSetAttribute(k_happly_tile<C, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               64 * 1024),
+                          "hamiltonian apply smem");
+            attr = true;
+        }
+        const uint64_t ntiles = (uint64_t(1) << n) >> (5 + t.m);
+        k_happly_tile<C, PER><<<unsigned(ntiles), threads, smem_of(t), st>>>(psi, lam, hp, t, dtabs);
+        QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+        return QSIM_OK;
+    }
+
+    int run(const C *psi, C *lam, const HParams &hp, cudaStream_t st) {
+        const uint64_t N = uint64_t(1) << n;
+        bool wrote = false;
+        for (const HTile &t : passes) {
+            if (t.ng == 0) continue;
+            const uint32_t TN = 1u << (5 + t.m);
+            const unsigned threads = std::min<uint32_t>(256, TN);
+            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(C) * (t.first ? 2.0 : 3.0));
+            switch (TN / threads) {
+                case 16: QSIM_TRY(launch<16>(psi, lam, hp, t, threads, st)); break;
+                case 8: QSIM_TRY(launch<8>(psi, lam, hp, t, threads, st)); break;
+                case 4: QSIM_TRY(launch<4>(psi, lam, hp, t, threads, st)); break;
+                case 2: QSIM_TRY(launch<2>(psi, lam, hp, t, threads, st)); break;
+                default: QSIM_TRY(launch<1>(psi, lam, hp, t, threads, st)); break;
+            }
+            wrote = true;
+        }
+        if (gather) {
+            const int blocks = sm_count_a() * ADJ_BLOCKS_PER_SM;
+            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(C) * (left.ngroups + (wrote ? 2 : 1)));
+            k_happly<C><<<blocks, 256, 0, st>>>(psi, lam, N, left, wrote ? 1 : 0);
+            QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+        }
+        return QSIM_OK;
+    }
+};
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_dot_re(const C *__restrict__ a, const C *__restrict__ b, uint64_t N,
@@ -245,6 +495,8 @@ int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HPar
     if (e != cudaSuccess) return cuda_error(e, "adjoint buffers");
     std::vector<double> host_rows(size_t(nrot) + 1);
     std::vector<void *> mats;  // dense k >= 2 matrices (uploaded per set)
+    HPlan<C> hplan;
+    QSIM_TRY(hplan.build(hp, n, st));
     for (int set = 0; set < nsets; ++set) {
         const double *th = params + size_t(set) * size_t(c.nparams);
         // forward and inverse ops with this set's angles
@@ -301,9 +553,7 @@ int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HPar
             QSIM_TRY(launch_op(psi, n, dtype, gs[i].fwd, st, mptr(moff_f[i])));
         // lambda = H psi, energy = Re <psi|lambda>
         {
-            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(C) * (hp.ngroups + 1));
-            k_happly<C><<<blocks, 256, 0, st>>>(psi, lam, N, hp);
-            QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+            QSIM_TRY(hplan.run(psi, lam, hp, st));
         }
         double *prow_e = partial + size_t(nrot) * prow;
         {
@@ -499,6 +749,8 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
                       "adjoint stage smem");
         attr = true;
     }
+    HPlan<float2> hplan;
+    QSIM_TRY(hplan.build(hp, n, st));
     for (int set = 0; set < nsets; ++set) {
         const double *th = params + size_t(set) * size_t(c.nparams);
         // forward circuit with this set's angles, and the reverse sweep:
@@ -539,9 +791,7 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
         QSIM_TRY(launch_init(psi, n, QSIM_C64, 0, st));
         QSIM_TRY(qsim_apply_fused(ps, fp));
         {
-            LaunchScope ls(K_HAPPLY, st, double(N) * sizeof(float2) * (hp.ngroups + 1));
-            k_happly<float2><<<blocks, 256, 0, st>>>(psi, lam, N, hp);
-            QSIM_CUDA_TRY(cudaGetLastError(), "hamiltonian apply launch");
+            QSIM_TRY(hplan.run(psi, lam, hp, st));
         }
         {
             LaunchScope ls(K_REDUCE, st, 2.0 * double(N) * sizeof(float2));

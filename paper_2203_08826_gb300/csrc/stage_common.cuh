@@ -186,11 +186,13 @@ __device__ __forceinline__ void tile_shared(C *tile, C (&v)[1 << REG_BITS], cons
 }
 
 
-// One non-exchange op on the 16 amplitudes v of a thread whose register 0
-// sits at global index `base`.
-template <typename C, typename Src>
-__device__ __forceinline__ void apply_op(const StageOp &op, const Src &src, C (&v)[1 << REG_BITS], uint64_t base,
-                                         int lane) {
+// One non-exchange op on the 16 amplitudes of a thread whose register 0
+// sits at global index `base`, applied to NS tiles at once (v, and w when
+// NS = 2: the op is decoded once for both).
+#define QSIM_EACH(S, X) for (int S = 0; S < NS; ++S) if (auto &X = S ? w : v; true)
+template <typename C, int NS, typename Src>
+__device__ __forceinline__ void apply_op2(const StageOp &op, const Src &src, C (&v)[1 << REG_BITS],
+                                          C (&w)[1 << REG_BITS], uint64_t base, int lane) {
     constexpr int NR = 1 << REG_BITS;
     const int type = op.type;
     if (type == SOP_U1R) {
@@ -198,7 +200,8 @@ __device__ __forceinline__ void apply_op(const StageOp &op, const Src &src, C (&
         const int mask = op.a;
 #define QSIM_U1R_BIT(J)                                                                                        \
 if (mask & (1 << J)) {                                                                                     \
-    u1_reg<C, J, false>(v, src.pool(off), src.pool(off + 1), src.pool(off + 2), src.pool(off + 3), 0);     \
+    const C m00 = src.pool(off), m01 = src.pool(off + 1), m10 = src.pool(off + 2), m11 = src.pool(off + 3);  \
+    _Pragma("unroll") QSIM_EACH(s, x) u1_reg<C, J, false>(x, m00, m01, m10, m11, 0);                         \
     off += 4;                                                                                              \
 }
         QSIM_U1R_BIT(0)
@@ -216,7 +219,10 @@ if (mask & (1 << J)) {                                                          
             const C cs = bit ? src.pool(off + 3) : src.pool(off), co = bit ? src.pool(off + 2) : src.pool(off + 1);
             off += 4;
 #pragma unroll
-            for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], 1 << l), cmul(cs, v[j]));
+            QSIM_EACH(s, x) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) x[j] = cmad(co, shfl_c(x[j], 1 << l), cmul(cs, x[j]));
+            }
         }
         return;
     }
@@ -227,11 +233,14 @@ if (mask & (1 << J)) {                                                          
             if ((base & tm) == tm) flip ^= uint32_t(src.aux(op.moff + 2 * e + 1));
         }
 #pragma unroll
-        for (int j = 0; j < NR; ++j)
-            if ((flip >> j) & 1) {
-                v[j].x = -v[j].x;
-                v[j].y = -v[j].y;
-            }
+        QSIM_EACH(s, x) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if ((flip >> j) & 1) {
+                    x[j].x = -x[j].x;
+                    x[j].y = -x[j].y;
+                }
+        }
         return;
     }
     // controls on lane / warp / tile qubits: one test per thread (a lane
@@ -243,11 +252,14 @@ if (mask & (1 << J)) {                                                          
         const C m00 = src.pool(op.moff), m01 = src.pool(op.moff + 1);
         const C m10 = src.pool(op.moff + 2), m11 = src.pool(op.moff + 3);
         if (op.a >= POS_REG) {
-            switch (op.a - POS_REG) {
-                case 0: u1_reg_dispatch<C, 0>(v, m00, m01, m10, m11, rneed); break;
-                case 1: u1_reg_dispatch<C, 1>(v, m00, m01, m10, m11, rneed); break;
-                case 2: u1_reg_dispatch<C, 2>(v, m00, m01, m10, m11, rneed); break;
-                default: u1_reg_dispatch<C, 3>(v, m00, m01, m10, m11, rneed); break;
+#pragma unroll
+            QSIM_EACH(s, x) {
+                switch (op.a - POS_REG) {
+                    case 0: u1_reg_dispatch<C, 0>(x, m00, m01, m10, m11, rneed); break;
+                    case 1: u1_reg_dispatch<C, 1>(x, m00, m01, m10, m11, rneed); break;
+                    case 2: u1_reg_dispatch<C, 2>(x, m00, m01, m10, m11, rneed); break;
+                    default: u1_reg_dispatch<C, 3>(x, m00, m01, m10, m11, rneed); break;
+                }
             }
         } else {
             const int bit = (lane >> op.a) & 1;
@@ -255,12 +267,18 @@ if (mask & (1 << J)) {                                                          
             const int lm = 1 << op.a;
             if (tok && rneed == 0) {
 #pragma unroll
-                for (int j = 0; j < NR; ++j) v[j] = cmad(co, shfl_c(v[j], lm), cmul(cs, v[j]));
+                QSIM_EACH(s, x) {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) x[j] = cmad(co, shfl_c(x[j], lm), cmul(cs, x[j]));
+                }
             } else {
 #pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    const C other = shfl_c(v[j], lm);
-                    if (tok && (j & rneed) == rneed) v[j] = cmad(co, other, cmul(cs, v[j]));
+                QSIM_EACH(s, x) {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) {
+                        const C other = shfl_c(x[j], lm);
+                        if (tok && (j & rneed) == rneed) x[j] = cmad(co, other, cmul(cs, x[j]));
+                    }
                 }
             }
         }
@@ -268,41 +286,42 @@ if (mask & (1 << J)) {                                                          
         C m[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) m[e] = src.pool(op.moff + e);
-        switch ((op.a - POS_REG) * 4 + (op.b - POS_REG)) {
-            case 1: u2_reg<C, 0, 1>(v, m, rneed); break;
-            case 2: u2_reg<C, 0, 2>(v, m, rneed); break;
-            case 3: u2_reg<C, 0, 3>(v, m, rneed); break;
-            case 4: u2_reg<C, 1, 0>(v, m, rneed); break;
-            case 6: u2_reg<C, 1, 2>(v, m, rneed); break;
-            case 7: u2_reg<C, 1, 3>(v, m, rneed); break;
-            case 8: u2_reg<C, 2, 0>(v, m, rneed); break;
-            case 9: u2_reg<C, 2, 1>(v, m, rneed); break;
-            case 11: u2_reg<C, 2, 3>(v, m, rneed); break;
-            case 12: u2_reg<C, 3, 0>(v, m, rneed); break;
-            case 13: u2_reg<C, 3, 1>(v, m, rneed); break;
-            default: u2_reg<C, 3, 2>(v, m, rneed); break;
+#pragma unroll
+        QSIM_EACH(s, x) {
+            switch ((op.a - POS_REG) * 4 + (op.b - POS_REG)) {
+                case 1: u2_reg<C, 0, 1>(x, m, rneed); break;
+                case 2: u2_reg<C, 0, 2>(x, m, rneed); break;
+                case 3: u2_reg<C, 0, 3>(x, m, rneed); break;
+                case 4: u2_reg<C, 1, 0>(x, m, rneed); break;
+                case 6: u2_reg<C, 1, 2>(x, m, rneed); break;
+                case 7: u2_reg<C, 1, 3>(x, m, rneed); break;
+                case 8: u2_reg<C, 2, 0>(x, m, rneed); break;
+                case 9: u2_reg<C, 2, 1>(x, m, rneed); break;
+                case 11: u2_reg<C, 2, 3>(x, m, rneed); break;
+                case 12: u2_reg<C, 3, 0>(x, m, rneed); break;
+                case 13: u2_reg<C, 3, 1>(x, m, rneed); break;
+                default: u2_reg<C, 3, 2>(x, m, rneed); break;
+            }
         }
     } else if (op.k == 0) {  // SOP_DIAG, one factor on the control subspace
         if (op.flags & 1) {
-            if (rneed == 0) {
 #pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    v[j].x = -v[j].x;
-                    v[j].y = -v[j].y;
-                }
-            } else {
+            QSIM_EACH(s, x) {
 #pragma unroll
                 for (int j = 0; j < NR; ++j)
                     if ((j & rneed) == rneed) {
-                        v[j].x = -v[j].x;
-                        v[j].y = -v[j].y;
+                        x[j].x = -x[j].x;
+                        x[j].y = -x[j].y;
                     }
             }
         } else {
             const C f = src.pool(op.moff);
 #pragma unroll
-            for (int j = 0; j < NR; ++j)
-                if ((j & rneed) == rneed) v[j] = cmul(f, v[j]);
+            QSIM_EACH(s, x) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j)
+                    if ((j & rneed) == rneed) x[j] = cmul(f, x[j]);
+            }
         }
     } else {  // SOP_DIAG with selector qubits
         // selector bits from the thread's base index (lane / warp / tile
@@ -331,7 +350,8 @@ if (mask & (1 << J)) {                                                          
                 for (int r = 0; r < REG_BITS; ++r)
                     if ((j >> r) & 1) sel |= rm[r];
                 const C f = (sel & 2) ? ((sel & 1) ? f3 : f2) : ((sel & 1) ? f1 : f0);
-                v[j] = cmul(f, v[j]);
+#pragma unroll
+                QSIM_EACH(s, x) x[j] = cmul(f, x[j]);
             }
         } else {
 #pragma unroll
@@ -341,10 +361,19 @@ if (mask & (1 << J)) {                                                          
 #pragma unroll
                 for (int r = 0; r < REG_BITS; ++r)
                     if ((j >> r) & 1) sel |= rm[r];
-                v[j] = cmul(src.pool(op.moff + sel), v[j]);
+                const C f = src.pool(op.moff + sel);
+#pragma unroll
+                QSIM_EACH(s, x) x[j] = cmul(f, x[j]);
             }
         }
     }
+}
+#undef QSIM_EACH
+
+template <typename C, typename Src>
+__device__ __forceinline__ void apply_op(const StageOp &op, const Src &src, C (&v)[1 << REG_BITS], uint64_t base,
+                                         int lane) {
+    apply_op2<C, 1>(op, src, v, v, base, lane);
 }
 
 // One pass of the op list over the tile held in v (16 amplitudes per thread).
@@ -463,8 +492,7 @@ __device__ __forceinline__ void stage_exec2(const Src &src, int nops, C (&v)[1 <
             }
             continue;
         }
-        apply_op<C>(op, src, v, base, lane);
-        apply_op<C>(op, src, w, base, lane);
+        apply_op2<C, 2>(op, src, v, w, base, lane);
     }
 }
 

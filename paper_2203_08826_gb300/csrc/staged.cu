@@ -82,17 +82,38 @@ void batch_ops(Stage &st) {
     auto plain_u1 = [](const StageOp &o) { return o.type == SOP_U1 && o.tmask == 0 && o.rneed == 0; };
     while (i < in.size()) {
         const StageOp &o = in[i];
-        if (plain_u1(o)) {
-            const bool reg = o.a >= POS_REG;
-            int mask = 0;
+        if (plain_u1(o) || o.type == SOP_GRAD) {
+            // a run of uncontrolled 1-qubit gates on distinct positions
+            // commutes: one batched op for its register targets, one for its
+            // lane targets.  Gradient ops in the run go first (each commutes
+            // with the gates on other positions; the run ends before one
+            // whose position a gate of the run already touched).
             size_t j = i;
-            while (j < in.size() && plain_u1(in[j]) && ((in[j].a >= POS_REG) == reg)) {
+            int rmask = 0, lmask = 0;
+            while (j < in.size() && (plain_u1(in[j]) || in[j].type == SOP_GRAD)) {
+                const bool reg = in[j].a >= POS_REG;
                 const int b = reg ? in[j].a - POS_REG : in[j].a;
+                int &mask = reg ? rmask : lmask;
                 if (mask & (1 << b)) break;
-                mask |= 1 << b;
+                if (in[j].type != SOP_GRAD) mask |= 1 << b;
                 ++j;
             }
-            if (j - i >= 2) {
+            for (size_t t = i; t < j; ++t)
+                if (in[t].type == SOP_GRAD) out.push_back(in[t]);
+            for (int cls = 0; cls < 2; ++cls) {
+                const bool reg = cls == 0;
+                const int mask = reg ? rmask : lmask;
+                if (!mask) continue;
+                if (__builtin_popcount(unsigned(mask)) == 1) {
+                    for (size_t t = i; t < j; ++t)
+                        if (in[t].type == SOP_U1 && (in[t].a >= POS_REG) == reg) {
+                            StageOp c = in[t];
+                            c.moff = int(pool.size());
+                            pool.insert(pool.end(), st.pool.begin() + in[t].moff, st.pool.begin() + in[t].moff + 4);
+                            out.push_back(c);
+                        }
+                    continue;
+                }
                 StageOp m{};
                 m.type = reg ? SOP_U1R : SOP_U1L;
                 m.a = int8_t(mask);
@@ -100,13 +121,14 @@ void batch_ops(Stage &st) {
                 // matrices in increasing bit order
                 for (int b = 0; b < 8; ++b)
                     for (size_t t = i; t < j; ++t) {
+                        if (in[t].type != SOP_U1 || (in[t].a >= POS_REG) != reg) continue;
                         const int tb = reg ? in[t].a - POS_REG : in[t].a;
                         if (tb == b) pool.insert(pool.end(), st.pool.begin() + in[t].moff, st.pool.begin() + in[t].moff + 4);
                     }
                 out.push_back(m);
-                i = j;
-                continue;
             }
+            i = j;
+            continue;
         }
         if (o.type == SOP_DIAG && o.k == 0 && (o.flags & 1)) {
             size_t j = i;

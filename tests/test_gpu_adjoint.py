@@ -133,3 +133,29 @@ def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker):
         np.testing.assert_allclose(grads[s], want, atol=2e-4)
         np.testing.assert_allclose(g128[s], want, atol=1e-10)
         assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < 2e-4
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-4), ("c128", 1e-10)])
+def test_adjoint_general_pauli_hamiltonian(q, orc, dtype, tol):
+    """A Hamiltonian of mixed Pauli strings on 14 qubits: X masks inside the
+    low 12 qubits, across qubits 0..4 and the top chunk, and across both
+    (handled by different passes of lambda = H psi), with Y and Z factors."""
+    n = 14
+    terms = [  # (x mask, z mask, coefficient)
+        (0, 0b11 << 3, 0.7),
+        (1 << 2, 0, -0.4),
+        ((1 << 2) | (1 << 13), 1 << 5, 0.3),        # X2 X13 Z5
+        ((1 << 7) | (1 << 13), (1 << 7), 0.25),     # Y7 X13: spans the chunks
+        ((1 << 12), (1 << 12) | (1 << 0), -0.6),    # Z0 Y12
+        ((1 << 11) | (1 << 4), 1 << 11, 0.45),      # X4 Y11
+        (0, (1 << 13) | 1, 0.2),
+    ]
+    ham = inputs.PauliSum(np.array([t[0] for t in terms], dtype=np.uint64),
+                          np.array([t[1] for t in terms], dtype=np.uint64),
+                          np.array([t[2] for t in terms]))
+    circ = mixed_ansatz(n, 2, seed=12)
+    th = np.random.default_rng(13).uniform(0, 2 * np.pi, size=(1, circ.nparams))
+    grads, en = q.adjoint_grad(circ, ham, th, dtype)
+    want = orc.parameter_shift_gradient(circ, ham, th[0])
+    np.testing.assert_allclose(grads[0], want, atol=tol)
+    assert abs(en[0] - orc.energy(circ, ham, th[0])) < tol
