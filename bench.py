@@ -220,7 +220,7 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_byt
     common = {"kernel": name, "avg_launch_ms": avg_ms, "launch_share": round(share, 4),
               "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
               "flops_per_launch": d.get("flops", 0.0) / d["launches"]}
-    if name in ("stage", "batch"):
+    if name in ("stage", "batch", "adjoint_step"):
         # register-tile interpreter: bound by the FP32 pipe / issue, not HBM
         tf = d["flops"] / d["launches"] / (avg_ms / 1e3) / 1e12
         pk = fp32_peak_tflops(sm_max_mhz)
@@ -348,7 +348,6 @@ def run_qsim(args, ws, rank, local):
         amp_bytes = (8 if args.dtype == "c64" else 16) << n
         h_in = torch.zeros(1 << n, dtype=state.tensor.dtype).pin_memory()
         h_in[0] = 1
-        h_out = torch.empty_like(h_in).pin_memory()
 
         def e2e_step():
             qc_e = q.QCircuit(circ)  # the gate list travels from the host every step
@@ -357,9 +356,9 @@ def run_qsim(args, ws, rank, local):
                 state.run(qc_e)
             else:
                 state.run_fused(q.Plan(qc_e, kmax=kmax_chosen, mode=mode_ids[chosen]))
-            e = state.expectation(ham)
-            state.to_host_into(h_out)
-            return e
+            e = state.expectation(ham)  # the step's results, read back to the host
+            shots = state.sample(SHOTS, seed=7, counter0=0)
+            return e, shots
 
         e2e_steps = max(1, min(args.steps, 3))
         for _ in range(max(1, min(args.warmup, 3))):
@@ -371,11 +370,37 @@ def run_qsim(args, ws, rank, local):
             e2e_step()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        # one more step, synchronised between its parts, for the breakdown
+        parts = {}
+        tp = time.perf_counter()
+
+        def mark(name):
+            nonlocal tp
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            parts[name] = round(1e3 * (t - tp), 2)
+            tp = t
+
+        qc_e = q.QCircuit(circ)
+        mark("marshal_ms")
+        state.from_host_async(h_in)
+        mark("h2d_ms")
+        pl_e = None if chosen == "plain" else q.Plan(qc_e, kmax=kmax_chosen, mode=mode_ids[chosen])
+        mark("plan_ms")
+        if pl_e is None:
+            state.run(qc_e)
+        else:
+            state.run_fused(pl_e)
+        mark("circuit_ms")
+        state.expectation(ham)
+        state.sample(SHOTS, seed=7, counter0=0)
+        mark("results_ms")
         e2e = {"value": ngates * e2e_steps * ws / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": amp_bytes,
-               "d2h_bytes_per_step": amp_bytes + 8,
+               "d2h_bytes_per_step": 8 + 8 * SHOTS, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+               "breakdown_one_step": parts,
                "includes": "gate-list marshalling + plan build, H2D of the initial state from pinned memory, "
-                           "circuit, expectation, D2H of the final state"}
-        del h_in, h_out
+                           "circuit, expectation and 1024 shots read back to the host"}
+        del h_in
     del state
     plans.clear()
     torch.cuda.empty_cache()
@@ -520,7 +545,16 @@ def other_workloads(q, torch, peak, peak_src):
     t0 = time.perf_counter()
     q.adjoint_grad(qc, ham, th, "c64")
     dt = (time.perf_counter() - t0) / len(th)
+    q.profile_enable(True)
+    q.profile_reset()
+    q.adjoint_grad(qc, ham, th[:4], "c64")
+    torch.cuda.synchronize()
+    aprof = q.profile_read()
+    q.profile_enable(False)
     out["adjoint24_c64"] = {"s_per_parameter_set": dt, "gradients_per_s": c.nparams / dt,
+                            "roofline": roofline_of(aprof, peak, peak_src, 2070.0, 24, 8),
+                            "kernels_per_set": {k: {"launches": v["launches"] / 4, "ms": v["ms"] / 4}
+                                                for k, v in aprof.items()},
                             "workload": "24 qubits, 10 layers RY/RZ + CZ ladder, 480 parameters, "
                                         "H = sum(Z_i Z_i+1 + 0.5 X_i), 64 parameter sets"}
     # adiabatic evolution (Sec. 3.3): -sum X -> TFIM target, 30 qubits, second-order Trotter circuit

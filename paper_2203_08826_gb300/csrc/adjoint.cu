@@ -820,7 +820,10 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
                 for (int c = 0; c < 3; ++c) dp.gv[g][c] = float(sg.grads[g].v[c]);
             }
             dp.ntiles = ntiles;
-            LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2));
+            // useful flops: the stage's gates on both states, 6 FMAs per
+            // amplitude for each gradient op's three sums
+            LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2),
+                           (2.0 * stage::stage_flops_per_amp(sg) + 12.0 * sg.ngradops) * double(N));
             k_adj_stage<DUAL_W><<<unsigned(ntiles), 32 << DUAL_W, smem, st>>>(psi, lam, dp, partial);
             QSIM_CUDA_TRY(cudaGetLastError(), "adjoint stage launch");
         }

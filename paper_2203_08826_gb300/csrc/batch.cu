@@ -67,13 +67,23 @@ __device__ __forceinline__ float zz_chain(uint64_t x, int n) {
     return float(n - 1 - 2 * __popcll((x ^ (x >> 1)) & m));
 }
 
-__device__ __forceinline__ uint64_t reg_offset(int j, const Phase &P) {
-    uint64_t o = 0;
+// Index bits of the register qubits of phase P, read once: the phases live
+// in global memory, which the stage's own stores may alias, so offsets
+// computed from P directly would reload it for every amplitude.
+struct RegMasks {
+    uint64_t m[REG_BITS];
+    __device__ __forceinline__ explicit RegMasks(const Phase &P) {
 #pragma unroll
-    for (int b = 0; b < REG_BITS; ++b)
-        if ((j >> b) & 1) o |= uint64_t(1) << P.rq[b];
-    return o;
-}
+        for (int b = 0; b < REG_BITS; ++b) m[b] = uint64_t(1) << P.rq[b];
+    }
+    __device__ __forceinline__ uint64_t operator()(int j) const {
+        uint64_t o = 0;
+#pragma unroll
+        for (int b = 0; b < REG_BITS; ++b)
+            if ((j >> b) & 1) o |= m[b];
+        return o;
+    }
+};
 
 template <int W>
 __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
@@ -107,25 +117,29 @@ __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
                 const GSrc src{bp.ops + S.op0, bp.phases + S.phase_base, bp.pool + S.pool0, bp.aux + S.aux0};
                 ph = S.phase0;
                 base = thread_base<W>(src.phase(ph), 0, lane, warp);
+                {
+                    const RegMasks rm(src.phase(ph));
 #pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    const uint64_t x = base | reg_offset(j, src.phase(ph));
-                    if (s == 0) v[j] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
-                    else v[j] = tile[x];
+                    for (int j = 0; j < NR; ++j) {
+                        const uint64_t x = base | rm(j);
+                        if (s == 0) v[j] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
+                        else v[j] = tile[x];
+                    }
                 }
                 if (s > 0) __syncthreads();  // hand-over reads before any exchange writes
                 stage_exec<C, W>(src, S.nops, v, ph, base, 0, tile, lane, warp);
+                const RegMasks rm(src.phase(ph));
                 if (s + 1 < bc.nstages) {
                     // hand over through shared memory, indexed by the amplitude index
                     __syncthreads();
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) tile[base | reg_offset(j, src.phase(ph))] = v[j];
+                    for (int j = 0; j < NR; ++j) tile[base | rm(j)] = v[j];
                     __syncthreads();
                 } else {
                     float f = 0.f;
 #pragma unroll
                     for (int j = 0; j < NR; ++j) {
-                        const uint64_t x = base | reg_offset(j, src.phase(ph));
+                        const uint64_t x = base | rm(j);
                         f = fmaf(fmaf(v[j].x, v[j].x, v[j].y * v[j].y), zz_chain(x, n), f);
                     }
                     acc = double(f);
@@ -148,11 +162,15 @@ __global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
                     int ph = S.phase0;
                     uint64_t base = thread_base<W>(src.phase(ph), tb, lane, warp);
                     C v[NR];
+                    {
+                        const RegMasks rm(src.phase(ph));
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) v[j] = slot[base | reg_offset(j, src.phase(ph))];
+                        for (int j = 0; j < NR; ++j) v[j] = slot[base | rm(j)];
+                    }
                     stage_exec<C, W>(src, S.nops, v, ph, base, tb, tile, lane, warp);
+                    const RegMasks rm(src.phase(ph));
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) slot[base | reg_offset(j, src.phase(ph))] = v[j];
+                    for (int j = 0; j < NR; ++j) slot[base | rm(j)] = v[j];
                 }
                 __syncthreads();  // the next stage reads what other threads wrote
             }
