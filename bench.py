@@ -442,6 +442,42 @@ def run_qsim(args, ws, rank, local):
         pg.destroy_process_group()
 
 
+def run_only(args):
+    """One of the other workloads alone, --warmup untimed and --steps timed
+    repetitions (adjoint24: one parameter set per step; batch4096: one
+    launch of the whole batch per step), printed as one JSON line."""
+    import torch
+    from paper_2203_08826_gb300 import binding as q
+    th = None
+    if args.only == "adjoint24":
+        c = inputs.variational(24, 10, seed=5)
+        qc = q.QCircuit(c)
+        ham = inputs.tfim(24)
+        th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(args.warmup + args.steps, c.nparams))
+
+        def run(i):
+            q.adjoint_grad(qc, ham, th[i:i + 1], "c64")
+        unit = "s per parameter set"
+    else:
+        circs = inputs.batch_circuits(4096, seed=2024)
+        b = q.Batch(circs)
+        o = torch.zeros(len(circs), dtype=torch.float64, device="cuda")
+
+        def run(i):
+            b.run(o)
+        unit = "s per batch"
+    for i in range(args.warmup):
+        run(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        run(args.warmup + i)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    print(json.dumps({"only": args.only, "value": dt, "unit": unit, "steps": args.steps, "warmup": args.warmup}),
+          flush=True)
+
+
 def other_workloads(q, torch, peak, peak_src):
     """The scope's other workloads, each timed with CUDA events (W warm-up, K timed)."""
     out = {}
@@ -624,9 +660,13 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--quick", action="store_true",
                     help="headline mode only (no other modes, end-to-end or CPU legs): for profiling runs")
+    ap.add_argument("--only", choices=["adjoint24", "batch4096"], default=None,
+                    help="run one of the other workloads alone (small runs for profiling)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_qsim(args, ws, rank, local)

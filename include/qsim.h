@@ -299,8 +299,13 @@ QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *x
  * for nsets parameter vectors: params is nsets x nparams (host, row-major).
  * Writes grads (nsets x nparams, host) and energies (nsets, host; may be NULL).
  * One forward sweep, then one reverse sweep that un-applies each gate to the
- * state and to lambda = H psi and accumulates 2 Re<lambda|dU psi> in double.
- * dtype: QSIM_C64 or QSIM_C128.  Allocates three states per set in flight.
+ * state and to lambda = H psi and accumulates 2 Re<lambda|dU psi> (for
+ * U = exp(-i theta P / 2): Im<lambda|P psi>); complex64 from 12 qubits sums
+ * in fp32 within a warp and in double beyond it, otherwise in double.
+ * H: nterms Pauli strings as for qsim_expectation_pauli, at most 64 distinct
+ * X masks and 128 terms (QSIM_EUNSUPPORTED beyond).  dtype: QSIM_C64 or
+ * QSIM_C128.  Allocates psi, lambda and the per-rotation partial sums for the
+ * duration of the call; synchronous.
  * (The paper obtains gradients only through TensorFlow autodiff, Sec. 2.) */
 QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, const double *params,
                       int nterms, const uint64_t *xmask, const uint64_t *zmask,
