@@ -86,7 +86,7 @@ struct RegMasks {
 };
 
 template <int W>
-__global__ void __launch_bounds__(32 << W) k_batch(const BatchParams bp) {
+__global__ void __launch_bounds__(32 << W, W <= 3 ? 3 : 1) k_batch(const BatchParams bp) {
     using C = float2;
     constexpr int NR = 1 << REG_BITS;
     constexpr int TB = LANE_BITS + REG_BITS + W;  // tile qubits
