@@ -19,12 +19,13 @@ __device__ __forceinline__ double prob_of(double2 a) {
 }
 
 // ---- complex64 weights in integer arithmetic
-// floor(p * 2^62) for p = RN_double(re^2 + im^2), the value prob_of gives,
+// floor(p * 2^62) for p = RN_double(re^2 + im^2), the value prob_c64 gives,
 // without fp64 (GB300's fp64 rate made the fp64 form the sampler's limit).
 // re^2 and im^2 are exact products of the 24-bit significands (subnormals
-// normalised first); the two are aligned in 128 bits (a gap above 79 bits
-// leaves the larger square exactly representable: the smaller one is below
-// half its unit in the last place) and rounded to 53 bits, nearest-even.
+// normalised first); the larger is shifted left by at most 15 bits onto the
+// smaller, bits of the smaller that fall below the 64-bit window are kept as
+// one sticky bit, and the sum is rounded to 53 bits, nearest-even.  Every
+// step is 64-bit integer arithmetic.
 __host__ __device__ inline int clz64_hd(uint64_t v) {
 #ifdef __CUDA_ARCH__
     return __clzll(static_cast<long long>(v));
@@ -59,59 +60,99 @@ __host__ __device__ inline int sumsq_rn(float re, float im, uint64_t &M53, int &
     uy &= 0x7FFFFFFFu;
     if (ux > 0x7F800000u || uy > 0x7F800000u) return 2;
     if (ux == 0x7F800000u || uy == 0x7F800000u) return 3;
-    if (ux == 0 && uy == 0) return 0;
-    if (ux == 0 || uy == 0) {
-        square_of_float(ux ? ux : uy, M53, E53);
-        return 1;
+    if (ux < uy) {  // |re| >= |im|, which orders the normalised exponents too
+        const uint32_t t = ux;
+        ux = uy;
+        uy = t;
     }
+    if (ux == 0) return 0;
     uint64_t M1, M2;
     int E1, E2;
     square_of_float(ux, M1, E1);
-    square_of_float(uy, M2, E2);
-    if (E1 < E2) {
-        const uint64_t tm = M1;
-        M1 = M2;
-        M2 = tm;
-        const int te = E1;
-        E1 = E2;
-        E2 = te;
-    }
-    const int d = E1 - E2;
-    if (d > 79) {
+    if (uy == 0) {
         M53 = M1;
         E53 = E1;
         return 1;
     }
-    const unsigned __int128 T = (static_cast<unsigned __int128>(M1) << d) + M2;
-    const uint64_t hi = uint64_t(T >> 64), lo = uint64_t(T);
-    const int L = hi ? 128 - clz64_hd(hi) : 64 - clz64_hd(lo);
-    if (L <= 53) {
-        M53 = lo;
-        E53 = E2;
+    square_of_float(uy, M2, E2);
+    // re^2 + im^2 = 2^(E1 - c) (M1 2^c + M2 2^-r + ...) with c = min(d, 15),
+    // r = d - c: the M2 bits shifted out only decide ties, so they are folded
+    // into bit 0 (a sticky bit; when r > 0, T >= 2^61 keeps >= 9 bits below
+    // the rounding point).  T < 2^63 + 2^48.
+    const int d = E1 - E2;
+    const int c = d < 15 ? d : 15;
+    const int r = d - c < 63 ? d - c : 63;
+    const uint64_t sticky = (M2 & ((uint64_t(1) << r) - 1)) != 0 ? 1 : 0;
+    const uint64_t T = ((M1 << c) + (M2 >> r)) | sticky;
+    const int L = 64 - clz64_hd(T);
+    if (L <= 53) {  // exact (no sticky bit is possible here)
+        M53 = T;
+        E53 = E1 - c;
         return 1;
     }
     int sh = L - 53;
-    M53 = uint64_t(T >> sh);
-    const unsigned __int128 rem = T & ((static_cast<unsigned __int128>(1) << sh) - 1);
-    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
-    if (rem > half || (rem == half && (M53 & 1))) ++M53;
-    if (M53 == (uint64_t(1) << 53)) {
-        M53 >>= 1;
+    uint64_t q = T >> sh;
+    const uint64_t rem = T & ((uint64_t(1) << sh) - 1), half = uint64_t(1) << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    if (q >> 53) {
+        q >>= 1;
         ++sh;
     }
-    E53 = E2 + sh;
+    M53 = q;
+    E53 = E1 - c + sh;
     return 1;
 }
 
-__host__ __device__ inline uint64_t weight_c64(float re, float im) {
+__host__ __device__ inline uint64_t weight_c64_exact(float re, float im) {
+    uint32_t ux, uy;
+    memcpy(&ux, &re, 4);
+    memcpy(&uy, &im, 4);
+    ux &= 0x7FFFFFFFu;
+    uy &= 0x7FFFFFFFu;
+    if (ux > 0x7F800000u || uy > 0x7F800000u) return 0;         // NaN
+    const uint32_t big = ux > uy ? ux : uy;
+    if (big >= 0x3F800000u) return uint64_t(1) << 62;           // a part >= 1 (or infinite): p >= 1
+    if (big < (95u << 23)) return 0;                             // both parts < 2^-32: p <= 2^-63
     uint64_t M53;
     int E53;
-    const int kind = sumsq_rn(re, im, M53, E53);
-    if (kind == 0 || kind == 2) return 0;
-    if (kind == 3) return uint64_t(1) << 62;
-    if ((64 - clz64_hd(M53)) + E53 > 0) return uint64_t(1) << 62;  // p >= 1
+    sumsq_rn(re, im, M53, E53);
     const int s = E53 + 62;
-    return s >= 0 ? (M53 << s) : (-s < 64 ? (M53 >> -s) : 0);
+    if (s >= 0) return (64 - clz64_hd(M53)) + s > 62 ? uint64_t(1) << 62 : (M53 << s);  // p >= 1: 2^62
+    return -s < 64 ? (M53 >> -s) : 0;
+}
+
+// The same weight by a shorter route where it applies.  With |re|, |im|
+// below 2^-10, A = (re^2 + im^2) 2^62 is below 2^43, so rounding to double
+// moves it by at most 2^-11 and changes floor(A) only if A's fraction is at
+// least 1 - 2^-11.  V = floor(re^2 2^73) + floor(im^2 2^73) is floor(A 2^11)
+// or one less; when V's low 11 bits are below 0x7FE, both candidates have
+// the same floor(A) and a fraction below 1 - 2^-11, so the weight is V >> 11.
+// Otherwise (about one element in a thousand), and for larger parts, the
+// exact rule above decides.  Parts below 2^-32 give p <= 2^-63: weight 0.
+__host__ __device__ inline uint64_t weight_c64(float re, float im) {
+    uint32_t ux, uy;
+    memcpy(&ux, &re, 4);
+    memcpy(&uy, &im, 4);
+    ux &= 0x7FFFFFFFu;
+    uy &= 0x7FFFFFFFu;
+    if (ux < uy) {  // a NaN or infinity ends up in ux and goes to the exact rule
+        const uint32_t t = ux;
+        ux = uy;
+        uy = t;
+    }
+    const uint32_t ex = ux >> 23, ey = uy >> 23;
+    if (ex < 95) return 0;
+    if (ex > 116) return weight_c64_exact(re, im);
+    // significands and the exponents of their squares in units of 2^-73
+    // (a subnormal im has no implicit bit and the scale of exponent 1)
+    const uint64_t mx = (ux & 0x7FFFFFu) | 0x800000u, my = (uy & 0x7FFFFFu) | (ey ? 0x800000u : 0u);
+    const int u1 = 2 * int(ex) - 227, u2 = 2 * int(ey ? ey : 1) - 227;
+    const uint64_t M1 = mx * mx, M2 = my * my;
+    const uint64_t t1 = u1 >= 0 ? (M1 << u1) : (M1 >> -u1);
+    const uint64_t t2 = u2 >= 0 ? (M2 << u2) : (-u2 < 64 ? (M2 >> -u2) : 0);
+    const uint64_t V = t1 + t2;
+    if ((V & 0x7FFu) >= 0x7FEu) return weight_c64_exact(re, im);
+    return V >> 11;
 }
 
 // The same value as a double, assembled from its bits (complex64 inputs give

@@ -151,9 +151,13 @@ def test_complex64_sampler_weights_match_their_definition():
              (2.0 ** -75, 2.0 ** -100), (0.70710677, 0.70710677), (float("inf"), 0.0), (float("nan"), 1.0),
              (-0.5, -0.5), (1.0000001, 0.0)]
     rng = np.random.default_rng(3)
-    for scale in (1.0, 1e-5, 1e-12, 1e-30, 1e-40):
-        xs = (rng.standard_normal(1500) * scale).astype(np.float32)
-        ys = (rng.standard_normal(1500) * scale * rng.choice([1, 1e-3, 1e-9], 1500)).astype(np.float32)
+    # 2^-15: amplitudes of a 30-qubit state (about one in a thousand of these
+    # takes the exact route after the short one); 2^-10 and 2^-32 straddle the
+    # bounds of the short route
+    for scale, count in ((1.0, 1500), (1e-5, 1500), (2.0 ** -15, 12000), (2.0 ** -10, 3000),
+                         (2.0 ** -32, 3000), (1e-12, 1500), (1e-30, 1500), (1e-40, 1500)):
+        xs = (rng.standard_normal(count) * scale).astype(np.float32)
+        ys = (rng.standard_normal(count) * scale * rng.choice([1, 1e-3, 1e-9], count)).astype(np.float32)
         cases += list(zip(xs.tolist(), ys.tolist()))
     for re, im in cases:
         assert lib.qsim_sampler_weight_c64(re, im) == want(re, im), (re, im)
