@@ -158,11 +158,19 @@ def oracle_qubits() -> int:
     return N_QUBITS if host_mem_bytes() > 3 * (16 << 30) else 26
 
 
+def workload_config(n: int) -> dict:
+    """The headline workload's description, shared by both arms' JSON lines."""
+    return {"workload": f"random circuit, {n} qubits, depth {DEPTH} (Haar SU(2) on every qubit + "
+                        f"CZ on a random perfect matching per layer), |0> start, "
+                        f"<sum Z_i Z_i+1> + {SHOTS} shots per step",
+            "qubits": n, "depth": DEPTH, "gates": n * DEPTH + (n // 2) * DEPTH}
+
+
 def run_reference(args, ws, rank):
     """The oracle as it stands, on the host cores, on a bounded sample."""
     if rank != 0:
         return
-    n = oracle_qubits()
+    n = min(args.qubits, oracle_qubits())
     circ = inputs.random_circuit(n, DEPTH, seed=2022)
     import oracle
     psi = oracle.zero_state(n)
@@ -189,7 +197,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"random circuit {n} qubits depth {DEPTH} (oracle sample)", "qubits": n},
+            "config": dict(workload_config(n), state="c128 (oracle)"),
             "cpu_baseline": {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -426,12 +434,8 @@ def run_qsim(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.dtype == "c64" else "f64", "data": "synthetic",
-            "config": {"workload": f"random circuit, {n} qubits, depth {DEPTH} (Haar SU(2) on every qubit + "
-                                   f"CZ on a random perfect matching per layer), |0> start, "
-                                   f"<sum Z_i Z_i+1> + {SHOTS} shots per step",
-                       "qubits": n, "depth": DEPTH, "gates": ngates, "state": args.dtype, "mode": chosen,
-                       "kmax": kmax_chosen, "autotune": tune,
-                       "l2": "inputs larger than L2 (state >= 8 GiB vs 129 MB L2)"},
+            "config": dict(workload_config(n), gates=ngates, state=args.dtype, mode=chosen, kmax=kmax_chosen,
+                           autotune=tune, l2="inputs larger than L2 (state >= 8 GiB vs 129 MB L2)"),
             "s_per_circuit": ms / 1e3 / args.steps,
             "gpu_launches": launches,
             "roofline": roof, "kernels": prof, "other_modes": others, "e2e": e2e, "cpu_baseline": cpu,
