@@ -355,6 +355,49 @@ def test_sampler_boundary_rule_by_hand(orc):
         assert int(got[s]) == want
 
 
+def test_sampler_matches_integer_inverse_cdf_at_scale(orc):
+    """The same rule on 3001 outcomes (a quarter of them impossible, so runs
+    of equal CDF values occur) and 3000 shots whose counters wrap past 2^64:
+    weights floor(p 2^62) and the search are redone with Python integers
+    (bisect over the CDF), the uniforms from the Philox outputs."""
+    import bisect
+    rng = np.random.default_rng(8)
+    p = rng.dirichlet(np.full(3001, 0.5))
+    p[rng.random(3001) < 0.25] = 0.0
+    p /= p.sum() * (1 + 1e-12)
+    w = [int(v * 2.0 ** 62) for v in p]  # exact scaling, then floor
+    cdf = list(itertools.accumulate(w))
+    T = cdf[-1]
+    seed, c0 = 0xDEADBEEF_0BADF00D, 2**64 - 1000
+    got = orc.sample(p, 3000, seed=seed, counter0=c0)
+    for s in range(3000):
+        cs = (c0 + s) % 2**64
+        o = orc.philox4x32_10([cs & 0xFFFFFFFF, cs >> 32, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        r = (((int(o[1]) << 32) | int(o[0])) * T) >> 64
+        want = bisect.bisect_right(cdf, r)  # smallest x with cdf[x] > r
+        assert int(got[s]) == want, s
+        assert p[want] > 0
+
+
+def tie_probabilities(orc, seed, counter0):
+    """Two outcomes whose first draw r lands exactly on cdf[0]: with integer
+    weights summing to T = 2^40, r = floor(u T / 2^64) = u >> 24 for the
+    shot's 64-bit uniform u, so weights (u >> 24, 2^40 - (u >> 24)) -- exact
+    as doubles w 2^-62 -- put r on the boundary.  The rule (smallest x with
+    CDF(x) > r) must then give outcome 1."""
+    o = orc.philox4x32_10([counter0 & 0xFFFFFFFF, counter0 >> 32, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+    u = (int(o[1]) << 32) | int(o[0])
+    w0 = u >> 24
+    return np.array([w0 * 2.0 ** -62, ((1 << 40) - w0) * 2.0 ** -62])
+
+
+def test_sampler_draw_on_a_cdf_value_takes_the_next_outcome(orc):
+    for seed, c0 in ((1, 0), (0xFEED, 2**32 - 1), (2**63 + 5, 2**64 - 1)):
+        p = tie_probabilities(orc, seed, c0)
+        assert 0 < p[0] < p.sum()
+        assert int(orc.sample(p, 1, seed=seed, counter0=c0)[0]) == 1
+
+
 def test_sampler_rejects_bad_probabilities(orc):
     with pytest.raises(ValueError):
         orc.sample(np.zeros(8), 10, seed=1)
