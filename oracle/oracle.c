@@ -148,8 +148,10 @@ static uint64_t prob_weight(double p) {
 }
 
 /*
- * Shot sampling by inverse CDF (the library's replacement for the Metropolis
- * sampler mentioned in Sec. 2; see the sampling reading in the design notes).
+ * Shot sampling by inverse CDF.  Sec. 2 samples shots with a Metropolis
+ * chain, whose output is not unique; inverse-CDF sampling over integer
+ * weights with a counter-based generator gives shots that two
+ * implementations can reproduce bit for bit.
  *   w(x)   = floor(p(x) 2^62)              (integer weights)
  *   CDF(x) = w(0) + ... + w(x),  T = CDF(N-1)
  *   shot s: (o0,o1,o2,o3) = Philox4x32-10(counter = (lo32(c0+s), hi32(c0+s), 0, 0),
