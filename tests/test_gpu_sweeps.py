@@ -207,18 +207,20 @@ def test_sampler_ragged_sizes(q, orc, N):
     np.testing.assert_array_equal(got, orc.sample(p, 5000, seed=N, counter0=3))
 
 
+@pytest.mark.parametrize("frac", [(0.0, 0.0), (0.75, 0.25)])
 @pytest.mark.parametrize("pad", [0, 2047])
-def test_sampler_draw_on_a_cdf_value(q, orc, pad):
+def test_sampler_draw_on_a_cdf_value(q, orc, pad, frac):
     """The first draw lands exactly on a CDF value (weights built from the
     shot's own Philox output, as in the oracle's pin); the next outcome must
     be drawn.  pad = 0: both outcomes in one chunk, the in-chunk scan decides;
     pad = 2047: the boundary is the last element of the first 2048-element
-    chunk, so the search over the chunk sums decides."""
+    chunk, so the search over the chunk sums decides.  frac: fractional
+    weight bits that floor(p 2^62) must drop."""
     import torch
     from paper_2203_08826_gb300 import binding
     from tests.test_oracle_pins import tie_probabilities
     seed, c0 = 0xFEED, 2**32 - 1
-    two = tie_probabilities(orc, seed, c0)
+    two = tie_probabilities(orc, seed, c0, frac)
     p = np.zeros(pad + 2 + (2048 if pad else 0))
     p[pad], p[pad + 1] = two
     want = orc.sample(p, 4, seed=seed, counter0=c0)

@@ -379,23 +379,25 @@ def test_sampler_matches_integer_inverse_cdf_at_scale(orc):
         assert p[want] > 0
 
 
-def tie_probabilities(orc, seed, counter0):
+def tie_probabilities(orc, seed, counter0, frac=(0.0, 0.0)):
     """Two outcomes whose first draw r lands exactly on cdf[0]: with integer
     weights summing to T = 2^40, r = floor(u T / 2^64) = u >> 24 for the
     shot's 64-bit uniform u, so weights (u >> 24, 2^40 - (u >> 24)) -- exact
     as doubles w 2^-62 -- put r on the boundary.  The rule (smallest x with
-    CDF(x) > r) must then give outcome 1."""
+    CDF(x) > r) must then give outcome 1.  `frac` adds fractions of 2^-62
+    (still exact doubles) that the weights floor(p 2^62) must drop."""
     o = orc.philox4x32_10([counter0 & 0xFFFFFFFF, counter0 >> 32, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
     u = (int(o[1]) << 32) | int(o[0])
     w0 = u >> 24
-    return np.array([w0 * 2.0 ** -62, ((1 << 40) - w0) * 2.0 ** -62])
+    return np.array([(w0 + frac[0]) * 2.0 ** -62, ((1 << 40) - w0 + frac[1]) * 2.0 ** -62])
 
 
 def test_sampler_draw_on_a_cdf_value_takes_the_next_outcome(orc):
     for seed, c0 in ((1, 0), (0xFEED, 2**32 - 1), (2**63 + 5, 2**64 - 1)):
-        p = tie_probabilities(orc, seed, c0)
-        assert 0 < p[0] < p.sum()
-        assert int(orc.sample(p, 1, seed=seed, counter0=c0)[0]) == 1
+        for frac in ((0.0, 0.0), (0.75, 0.25)):  # weights are floored, not rounded
+            p = tie_probabilities(orc, seed, c0, frac)
+            assert 0 < p[0] < p.sum()
+            assert int(orc.sample(p, 1, seed=seed, counter0=c0)[0]) == 1
 
 
 def test_sampler_rejects_bad_probabilities(orc):
