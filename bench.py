@@ -138,6 +138,85 @@ def oracle_gates_per_s(circuit, budget_s: float = 20.0, n_override: int | None =
     return done / dt, done, n, cores
 
 
+def oracle_baselines(budget_s: float = 2.0, widths: dict | None = None) -> dict:
+    """The oracle as it stands, timed beside the other workloads on bounded
+    samples of each (host cores; all threads, and one thread where noted).
+    Keys match the GPU arm's `other_workloads`; each value is a cpu_baseline
+    object whose `sample` says what was timed."""
+    import oracle
+    w = {"qft_small": 10, "qft": oracle_qubits(), "random": oracle_qubits(), "variational": 26,
+         "adjoint": 24, "batch": 4096}
+    w.update(widths or {})
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def rate(circ, threads=0, budget=budget_s):
+        """Gates per second applying the circuit's gates in order (cycling if
+        it ends first) until `budget` seconds have passed (at least one gate)."""
+        prev = oracle.set_threads(threads)
+        try:
+            psi = oracle.zero_state(circ.n)
+            psi[1:] = 0.0  # touch every page before the clock starts
+            done, t0 = 0, time.perf_counter()
+            while done == 0 or time.perf_counter() - t0 < budget:
+                oracle.apply_gate(psi, circ.gates[done % len(circ.gates)])
+                done += 1
+            return done / (time.perf_counter() - t0), done
+        finally:
+            oracle.set_threads(prev)
+
+    def entry(value, unit, sample, threads=None, **more):
+        return dict({"value": value, "unit": unit, "cores": threads or cores, "kind": "oracle", "sample": sample},
+                    **more)
+
+    def gates(n, circ):
+        return f"first {n} gates" if n <= len(circ) else f"{n} gates ({len(circ)}-gate circuit repeated)"
+
+    out = {}
+    c = inputs.qft(w["qft_small"])
+    all_r, n_all = rate(c)
+    one_r, n_one = rate(c, threads=1)
+    out[f"qft{c.n}_c128"] = entry(all_r, "gates/s", f"{c.n}-qubit QFT ({len(c)} gates) repeated for "
+                                  f"{budget_s:g} s: {n_all} gates on {cores} threads, {n_one} on one",
+                                  single_thread=one_r)
+    c = inputs.qft(w["qft"])
+    r, n = rate(c)
+    out[f"qft{w['qft']}_c64"] = entry(r, "gates/s", f"{gates(n, c)} of the {c.n}-qubit QFT, complex128")
+    c = inputs.random_circuit(w["random"], DEPTH, seed=2022)
+    r, n = rate(c, threads=1, budget=0.0)
+    out[f"random{w['random']}_c128_plain"] = entry(
+        r, "gates/s", f"first gate of the {c.n}-qubit depth-{DEPTH} random circuit on one thread "
+                      f"(the all-thread figure is the main line's cpu_baseline)", threads=1)
+    c = inputs.variational(w["variational"], 20, seed=1)
+    all_r, n_all = rate(c)
+    one_r, n_one = rate(c, threads=1)
+    out["variational32_c64"] = entry(all_r, "gates/s", f"{c.n}-qubit 20-layer variational circuit (the width "
+                                     f"of the fused-error check; 32 qubits would need 64 GiB in complex128): "
+                                     f"{gates(n_all, c)} on {cores} threads, {gates(n_one, c)} on one",
+                                     single_thread=one_r)
+    circs = inputs.batch_circuits(w["batch"], seed=2024, nmax=w.get("batch_nmax", 20), limit=64)
+    zz = {}
+    done, t0 = 0, time.perf_counter()
+    upd = 0
+    while done < len(circs) and (done == 0 or time.perf_counter() - t0 < budget_s):
+        cc = circs[done]
+        ham = zz.setdefault(cc.n, inputs.zz_chain(cc.n))
+        oracle.expectation(oracle.simulate(cc), ham)
+        upd += (1 << cc.n) * len(cc)
+        done += 1
+    dt = time.perf_counter() - t0
+    out[f"batch{w['batch']}_c64"] = entry(done / dt, "circuits/s", f"first {done} circuits of the batch, "
+                                          f"each simulated and its <sum Z_i Z_i+1> evaluated, complex128",
+                                          amp_gate_updates_per_s=upd / dt)
+    c = inputs.variational(w["adjoint"], 10, seed=5)
+    r, n = rate(c)
+    out[f"adjoint{w['adjoint']}_c64"] = entry(
+        r / (2 * len(c)), "gradients/s",
+        f"derived: the oracle's gradient is the parameter-shift rule, two runs of the {len(c)}-gate circuit "
+        f"per parameter; its gate rate at {c.n} qubits ({r:.3g} gates/s over {gates(n, c)}) / "
+        f"(2 x {len(c)})", gates_per_s=r)
+    return out
+
+
 def host_mem_bytes() -> int:
     try:
         import psutil
@@ -427,6 +506,12 @@ def run_qsim(args, ws, rank, local):
         cpu = {"value": gps, "unit": "gates/s", "cores": cores, "kind": "oracle",
                "sample": f"first {done} gates of a {nq}-qubit depth-{DEPTH} random circuit, complex128, "
                          f"gate by gate on the host (OpenMP)"}
+        if extra:  # the oracle beside the other workloads; never at the cost of the GPU numbers
+            try:
+                for k, v in oracle_baselines().items():
+                    extra.setdefault(k, {})["cpu_baseline"] = v
+            except Exception as e:
+                extra["cpu_baselines_error"] = repr(e)
 
     if rank == 0:
         line = {

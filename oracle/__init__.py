@@ -63,6 +63,8 @@ def _load():
             lib.orc_philox4x32_10.restype = None
             lib.orc_sample.argtypes = [P, U64, U64, U64, U64, P]
             lib.orc_sample.restype = I
+            lib.orc_set_threads.argtypes = [I]
+            lib.orc_set_threads.restype = I
             _lib = lib
     return _lib
 
@@ -164,6 +166,12 @@ def run_inverse(psi: np.ndarray, gates: Sequence) -> np.ndarray:
     for g in reversed(list(gates)):
         apply_matrix(psi, inverse_gate_matrix(g), g.targets, g.controls)
     return psi
+
+
+def set_threads(nthreads: int) -> int:
+    """Threads of the Eq. (1) loop from now on (0 keeps the setting); returns
+    the previous count.  Used to time the oracle on one core."""
+    return int(_load().orc_set_threads(int(nthreads)))
 
 
 def zero_state(n: int) -> np.ndarray:

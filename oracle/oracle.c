@@ -17,6 +17,7 @@
  *   - a control qubit must be 1 for the gate to act.
  */
 #include <complex.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -197,4 +198,12 @@ int orc_sample(const double *p, uint64_t N, uint64_t nshots, uint64_t seed,
     }
     free(cdf);
     return 0;
+}
+
+/* Threads used by the Eq. (1) loop from now on (timing the oracle on one core
+ * or on all of them); returns the previous setting. */
+int orc_set_threads(int nthreads) {
+    const int prev = omp_get_max_threads();
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return prev;
 }

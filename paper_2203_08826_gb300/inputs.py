@@ -157,14 +157,16 @@ def ghz(n: int) -> Circuit:
 
 
 def batch_circuits(count: int, seed: int, nmin: int = 12, nmax: int = 20,
-                   lmin: int = 4, lmax: int = 12) -> List[Circuit]:
+                   lmin: int = 4, lmax: int = 12, limit: int | None = None) -> List[Circuit]:
     """Many small uneven circuits: n ~ U{nmin..nmax}, layers ~ U{lmin..lmax}
-    (both inclusive), each a variational ansatz with its own angles."""
+    (both inclusive), each a variational ansatz with its own angles.  With
+    `limit`, only the first `limit` circuits of the same batch are built."""
     rng = _rng(seed)
     ns = rng.integers(nmin, nmax + 1, size=count)
     ls = rng.integers(lmin, lmax + 1, size=count)
     seeds = rng.integers(0, 2**63 - 1, size=count)
-    return [variational(int(n), int(l), int(s)) for n, l, s in zip(ns, ls, seeds)]
+    k = count if limit is None else min(limit, count)
+    return [variational(int(n), int(l), int(s)) for n, l, s in zip(ns[:k], ls[:k], seeds[:k])]
 
 
 def gaussian_state(n: int, seed: int) -> np.ndarray:

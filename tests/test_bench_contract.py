@@ -38,3 +38,22 @@ def test_reference_arm_other_ranks_exit_without_output():
     r = _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_oracle_baselines_beside_the_other_workloads():
+    """The oracle timings reported beside the GPU arm's other workloads, on
+    narrow stand-ins of each (the bench runs them at full width)."""
+    import bench
+    out = bench.oracle_baselines(budget_s=0.05, widths={"qft": 12, "random": 12, "variational": 10,
+                                                        "adjoint": 10, "batch": 16, "batch_nmax": 13})
+    assert set(out) == {"qft10_c128", "qft12_c64", "random12_c128_plain", "variational32_c64", "batch16_c64",
+                        "adjoint10_c64"}
+    units = {"qft10_c128": "gates/s", "qft12_c64": "gates/s", "random12_c128_plain": "gates/s",
+             "variational32_c64": "gates/s", "batch16_c64": "circuits/s", "adjoint10_c64": "gradients/s"}
+    for k, v in out.items():
+        assert v["kind"] == "oracle" and v["unit"] == units[k] and v["value"] > 0 and v["sample"], k
+    assert out["qft10_c128"]["single_thread"] > 0 and out["variational32_c64"]["single_thread"] > 0
+    assert out["random12_c128_plain"]["cores"] == 1
+    a = out["adjoint10_c64"]
+    # two runs of the 290-gate circuit (10 layers of 10 RY, 10 RZ, 9 CZ) per gradient
+    assert abs(a["value"] - a["gates_per_s"] / (2 * 290)) < 1e-9 * a["gates_per_s"]
