@@ -185,9 +185,12 @@ QSIM_API int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_pla
 QSIM_API int qsim_plan_destroy(qsim_plan *p);
 /* Number of sweeps (HBM passes) and of source gates the plan covers. */
 QSIM_API int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode);
-/* Fused matrix of block i for QSIM_FUSE_GREEDY2 / QSIM_FUSE_TC plans:
+/* Fused matrix of block i of a QSIM_FUSE_GREEDY2 plan (0 <= i < nsweeps):
  * writes k and the targets (targets[0] = MSB) and, if matrix_out is non-NULL,
- * the 2^k x 2^k row-major complex128 matrix.  Host-only; no GPU needed. */
+ * the 2^k x 2^k row-major complex128 matrix.  Staged and tensor-core plans
+ * keep their work in other forms (stage op lists; window blocks with
+ * diagonal epilogues) and return QSIM_EINVAL here.  Host-only; no GPU
+ * needed. */
 QSIM_API int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *matrix_out);
 /* Human-readable summary of a plan (stages, tile qubits, op counts),
  * NUL-terminated and truncated to len bytes.  Host-only. */

@@ -111,6 +111,18 @@ def test_greedy2_blocks_equal_product_of_oracle_gates(q, orc):
     assert plan.info()["sweeps"] < len(circ)
 
 
+def test_plan_block_only_for_greedy_plans(q):
+    c = inputs.random_circuit(14, 3, seed=1)
+    for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
+        with pytest.raises(q.QsimError):
+            q.Plan(c, kmax=k, mode=mode).block(0)
+    g = q.Plan(c, kmax=2, mode=q.FUSE_GREEDY2)
+    t, m = g.block(g.info()["sweeps"] - 1)
+    assert m.shape == (1 << len(t), 1 << len(t))
+    with pytest.raises(q.QsimError):
+        g.block(g.info()["sweeps"])
+
+
 def test_plan_rejects_bad_mode(q):
     with pytest.raises(q.QsimError):
         q.Plan(inputs.qft(4), kmax=2, mode=7)
