@@ -317,12 +317,15 @@ QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, cons
 /* ---------------------------------------------------------------- batches */
 typedef struct qsim_batch qsim_batch;
 
-/* A batch of many small circuits (9 <= n <= 20 qubits each, complex64 states)
- * run by one persistent kernel: each CTA takes the next circuit from a device
- * work counter (largest first), simulates it with its state resident in
- * shared memory (n <= 14) or in a per-CTA global slot streamed through shared
- * memory tiles (n > 14), and writes <sum_i Z_i Z_{i+1}> of its final state.
- * The plan (gate tables) is uploaded once at creation. */
+/* A batch of many small circuits (9 <= n <= 20 qubits each, gates of at most
+ * 2 targets, complex64 states) run by one persistent kernel: each CTA takes
+ * the next circuit from a device work counter (largest first) and simulates
+ * it with the staged register-tile interpreter.  A circuit as wide as the
+ * tile (2^(tile_qubits) amplitudes) stays in the CTA's registers for its whole
+ * run; a wider one lives in a per-CTA global slot (at most 8 MiB, mostly
+ * L2-resident) that each stage streams through the registers tile by tile.
+ * The CTA then writes <sum_i Z_i Z_{i+1}> of its final state.  The plan
+ * (gate tables) is uploaded once at creation. */
 QSIM_API int qsim_batch_create(int ncircuits, const qsim_circuit *const *circuits, qsim_batch **out);
 QSIM_API int qsim_batch_destroy(qsim_batch *b);
 /* Run every circuit from |0...0> on `cuda_stream`; out_dev: device array of
@@ -412,9 +415,10 @@ QSIM_API int qsim_slice_unpack(void *slice, int n_local, int dtype, int local_po
  * aligned, distinct).  QSIM_SLICES_DEVICE: in place in device memory, on
  * `stream`.  QSIM_SLICES_HOST: slices stay in page-locked host memory; each
  * pass (a run of SWAP steps and the segment after it) streams groups of
- * slices through two device staging buffers on two internal streams (the
- * upload of one group overlaps the work on the other) and returns after the
- * last download.  QSIM_ENOMEM when the staging buffers do not fit. */
+ * slices through two sets of device staging slots on three internal streams
+ * (uploads, compute, downloads), so the upload of one slice overlaps the work
+ * on another and the download of a third; the call returns after the last
+ * download.  QSIM_ENOMEM when two staging slots per set do not fit. */
 QSIM_API int qsim_slice_run(const qsim_slice_plan *p, int dtype, void *const *slices, int location, void *stream);
 
 /* ---------------------------------------------------------------- test support
