@@ -171,12 +171,17 @@ typedef struct qsim_plan qsim_plan;
  *                      diagonal, or through their controls), and writes the
  *                      tile back: one HBM pass per stage.  Needs n >= 9;
  *                      smaller circuits get a QSIM_FUSE_GREEDY2 plan.
- *   QSIM_FUSE_TC       dense k-qubit blocks (kmax = 4..6) applied on the
- *                      tensor cores as split-precision real GEMMs
- *                      (complex64 states only), with the qubit order rotated
- *                      by each pass so every block's targets are the low bits.
- * kmax bounds the targets of a fused block (2..6).  The plan copies what it
- * needs from the circuit; it does not depend on the circuit afterwards.
+ *   QSIM_FUSE_TC       dense blocks on windows of 6 consecutive qubits
+ *                      (kmax >= 6, BF16x3 split) or 5 (kmax <= 5, 3xTF32
+ *                      split) applied on the tensor cores as real GEMMs
+ *                      (complex64 states only; n >= window + 7), with the
+ *                      qubit order rotated by each pass so every block's
+ *                      targets are the low bits; diagonal gates that straddle
+ *                      a window are applied in the pass's epilogue.
+ * kmax (1..6): for QSIM_FUSE_GREEDY2 the most qubits a fused gate may act on;
+ * for QSIM_FUSE_STAGED the tile's warp qubits (at most 4); for QSIM_FUSE_TC
+ * the window width as above.  The plan copies what it needs from the circuit;
+ * it does not depend on the circuit afterwards.
  * Citation: Sec. 3.2 (gate fusion; fusing up to about five qubits may help). */
 #define QSIM_FUSE_GREEDY2 0
 #define QSIM_FUSE_STAGED 1
