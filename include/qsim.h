@@ -311,7 +311,9 @@ QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *x
  * U = exp(-i theta P / 2): Im<lambda|P psi>); complex64 from 12 qubits sums
  * in fp32 within a warp and in double beyond it, otherwise in double.
  * H: nterms Pauli strings as for qsim_expectation_pauli, at most 64 distinct
- * X masks and 128 terms (QSIM_EUNSUPPORTED beyond).  dtype: QSIM_C64 or
+ * X masks and 128 terms (QSIM_EUNSUPPORTED beyond).  Trainable rotations must
+ * be uncontrolled 1-qubit gates, and the complex64 path from 12 qubits takes
+ * dense gates of at most 2 targets (QSIM_EUNSUPPORTED otherwise).  dtype: QSIM_C64 or
  * QSIM_C128.  Allocates psi, lambda and the per-rotation partial sums for the
  * duration of the call; synchronous.
  * (The paper obtains gradients only through TensorFlow autodiff, Sec. 2.) */
