@@ -495,7 +495,10 @@ def run_qsim(args, ws, rank, local):
     # ---- other workloads of the scope (rank 0 only, informational)
     extra = {}
     if rank == 0 and not (args.quick or args.no_extra):
-        extra = other_workloads(q, torch, peak, peak_src)
+        try:  # informational: a failure here must not cost the headline line
+            extra = other_workloads(q, torch, peak, peak_src)
+        except Exception as e:
+            extra = {"error": repr(e)}
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None

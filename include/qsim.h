@@ -109,6 +109,8 @@ QSIM_API int qsim_state_info(const qsim_state *s, int *n, int *dtype, void **dev
 #define QSIM_INIT_BASIS 1  /* |basis>                                      */
 #define QSIM_INIT_HOST 2   /* copy 2^n amplitudes (state precision) from host `src` */
 #define QSIM_INIT_DEVICE 3 /* copy 2^n amplitudes (state precision) from device `src` */
+#define QSIM_INIT_NULL 4   /* every amplitude 0 (a slice of a larger state that
+                              holds none of its weight, Sec. 3.1 slices)   */
 QSIM_API int qsim_state_init(qsim_state *s, int kind, uint64_t basis, const void *src);
 /* Copy all 2^n amplitudes (state precision) to host memory `dst`; synchronous. */
 QSIM_API int qsim_state_copy_to_host(qsim_state *s, void *dst);

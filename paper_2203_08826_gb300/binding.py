@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
 
 C64, C128 = 0, 1
 FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
-INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE = 0, 1, 2, 3
+INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE, INIT_NULL = 0, 1, 2, 3, 4
 SLICE_SEGMENT, SLICE_SWAP = 0, 1
 SLICES_DEVICE, SLICES_HOST = 0, 1
 GATE_KIND = {"matrix": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "t": 6, "rx": 7, "ry": 8,
@@ -376,6 +376,10 @@ class State:
     # -- initialisation / transfer
     def init_zero(self):
         _check(lib().qsim_state_init(self.handle, INIT_ZERO, 0, None)); return self
+
+    def init_null(self):
+        """Every amplitude 0 (a slice that holds none of the state's weight)."""
+        _check(lib().qsim_state_init(self.handle, INIT_NULL, 0, None)); return self
 
     def init_basis(self, b: int):
         _check(lib().qsim_state_init(self.handle, INIT_BASIS, b, None)); return self

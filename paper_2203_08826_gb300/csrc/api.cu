@@ -383,6 +383,8 @@ int qsim_state_init(qsim_state *s, int kind, uint64_t basis, const void *src) {
         case QSIM_INIT_BASIS:
             if (basis >= s->size()) return set_error(QSIM_EINVAL, "basis index outside the state");
             return launch_init(s->amps, s->n, s->dtype, basis, s->stream);
+        case QSIM_INIT_NULL:  // no index equals the marker: every amplitude is written 0
+            return launch_init(s->amps, s->n, s->dtype, ~uint64_t(0), s->stream);
         case QSIM_INIT_HOST:
         case QSIM_INIT_DEVICE: {
             if (!src) return set_error(QSIM_EINVAL, "src is NULL");

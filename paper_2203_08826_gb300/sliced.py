@@ -48,9 +48,22 @@ class SlicedState:
             self.slices = [torch.empty(1 << self.L, dtype=tdt, pin_memory=True) for _ in range(1 << self.g)]
 
     def init_zero(self):
-        for t in self.slices:
-            t.zero_()
-        self.slices[0][0] = 1.0
+        """|0...0>: slice 0 starts at its first amplitude, every other slice is 0.
+        Device slices are written by the library's init kernel (on the current
+        stream, which the plan's run uses too); page-locked host slices are
+        filled on the host."""
+        if self.location == _b.SLICES_DEVICE:
+            kind = "c64" if self.dtype == _b.C64 else "c128"
+            for i, t in enumerate(self.slices):
+                st = _b.State(self.L, kind, tensor=t)
+                if i == 0:
+                    st.init_zero()
+                else:
+                    st.init_null()
+        else:
+            for t in self.slices:
+                t.zero_()
+            self.slices[0][0] = 1.0
         return self
 
     def from_host(self, amps: np.ndarray):
