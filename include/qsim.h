@@ -18,7 +18,8 @@
  *     doubles, re then im), and targets[0] is the MOST significant bit of its
  *     row/column index: G(tau_1..tau_k, tau_1'..tau_k') of Eq. (1) takes tau_1
  *     from targets[0].
- *   - Controls (Sec. 2, "controlled gates") act when all control bits are 1.
+ *   - Controls (the controlled-gate operators of Sec. 2) act when all control
+ *     bits are 1.
  *   - Host arrays passed in are read during the call and may be reused when it
  *     returns.  Device work runs asynchronously on the state's CUDA stream;
  *     calls that return host values synchronise that stream.
@@ -160,10 +161,11 @@ QSIM_API int qsim_run(qsim_state *s, const qsim_circuit *c);
 typedef struct qsim_plan qsim_plan;
 
 /* Fusion modes.
- *   QSIM_FUSE_GREEDY2  the paper's fusion (Sec. 3.2): greedily multiply 1- and
- *                      2-qubit gates that act on the same targets; one sweep
- *                      per fused gate (kmax = 1 merges only 1-qubit gates on
- *                      the same qubit).
+ *   QSIM_FUSE_GREEDY2  the paper's fusion (Sec. 3.2): one pass over the gates
+ *                      multiplies each 1- or 2-qubit gate into the fused
+ *                      gate on its qubits while their union stays within
+ *                      kmax qubits; one sweep per fused gate (kmax = 1 merges
+ *                      only 1-qubit gates on the same qubit).
  *   QSIM_FUSE_STAGED   cache-blocked stages: each stage loads tiles of 2^m
  *                      amplitudes spanning a chosen qubit set into registers
  *                      (qubits 0..4 across the lanes of a warp, 4 qubits per

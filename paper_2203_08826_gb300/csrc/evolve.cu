@@ -1,6 +1,6 @@
 // Diagonal Pauli-sum evolution: psi <- exp(-i theta D) psi with
-// D = sum_t c_t Z(z_t), the diagonal factor of a Trotter step (Sec. 3.3: the
-// time evolution is decomposed into a circuit of unitary gates; for the TFIM
+// D = sum_t c_t Z(z_t), the diagonal factor of a Trotter step (Sec. 3.3
+// turns the evolution into a circuit by the Trotter product; for the TFIM
 // the sum of Z_i Z_{i+1} terms is diagonal and its exponential is one phase
 // per amplitude).  One HBM pass per call whatever the number of terms:
 // D(x) = sum_t c_t (-1)^popcount(x & z_t).
