@@ -28,16 +28,7 @@ constexpr int ADJ_BLOCKS_PER_SM = 4;
 constexpr int HAPPLY_GROUPS = 64;
 constexpr int HAPPLY_TERMS = 128;
 
-int sm_count_a() {
-    static int v = 0;
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        if (v <= 0) v = 148;
-    }
-    return v;
-}
+int sm_count_a() { return device_sm_count(); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -42,6 +42,24 @@ static const char *k_names[K_NUM_KINDS] = {
 
 const char *kernel_name(int kind) { return (kind >= 0 && kind < K_NUM_KINDS) ? k_names[kind] : "?"; }
 
+int device_sm_count() {
+    constexpr int MAX_DEV = 64;
+    static std::atomic<int> cache[MAX_DEV];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < MAX_DEV) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 148;
+    }
+    if (dev >= 0 && dev < MAX_DEV) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 namespace {
 struct ProfSlot {
     int kind;
@@ -49,7 +67,7 @@ struct ProfSlot {
     double bytes, flops;
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 std::vector<ProfSlot> g_slots;
 size_t g_used = 0;
 std::atomic<uint64_t> g_launches{0};

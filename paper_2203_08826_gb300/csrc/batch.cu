@@ -236,16 +236,7 @@ struct Packed {
     }
 };
 
-int sm_count_b() {
-    static int v = 0;
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        if (v <= 0) v = 148;
-    }
-    return v;
-}
+int sm_count_b() { return device_sm_count(); }
 
 }  // namespace
 }  // namespace qsim

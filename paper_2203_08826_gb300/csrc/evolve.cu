@@ -167,9 +167,7 @@ int launch_pauli_phase(qsim_state *s, int nterms, const uint64_t *zmask, const d
     }
     const uint64_t N = uint64_t(1) << n;
     constexpr int PER = 4, T = 256;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
     const uint64_t blocks = std::min<uint64_t>((N + T * PER - 1) / (T * PER), uint64_t(std::max(sms, 1)) * 8);
     LaunchScope ls(K_PAULI_PHASE, s->stream, 2.0 * double(N) * sizeof(C), 6.0 * double(N));
     k_pauli_phase<R, PER><<<unsigned(blocks), T, 0, s->stream>>>(static_cast<C *>(s->amps), N, p);

@@ -58,6 +58,9 @@ enum KernelKind {
 };
 const char *kernel_name(int kind);
 
+// SM count of the current device, queried once per device (thread-safe).
+int device_sm_count();
+
 // RAII bracket around one launch: counts it (copies are not counted as
 // kernel launches) and, when profiling is on, records CUDA events on `stream`
 // before and after.

@@ -180,16 +180,7 @@ __host__ __device__ inline double prob_c64(float re, float im) {
 }
 
 
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
+static int sm_count() { return device_sm_count(); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

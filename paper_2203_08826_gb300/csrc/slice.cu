@@ -30,16 +30,7 @@ namespace {
 
 constexpr int SLICE_THREADS = 256;
 
-int sm_count_s() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
+int sm_count_s() { return device_sm_count(); }
 
 __device__ __forceinline__ uint64_t insert_bit(uint64_t g, int l, uint64_t bit) {
     const uint64_t low = g & ((uint64_t(1) << l) - 1);

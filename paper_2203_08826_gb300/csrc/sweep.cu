@@ -52,16 +52,7 @@ __global__ void k_init(C *psi, uint64_t N, uint64_t basis) {
     }
 }
 
-static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
+static int sm_count() { return device_sm_count(); }
 
 int launch_init(void *psi, int n, int dtype, uint64_t basis, cudaStream_t st) {
     const uint64_t N = uint64_t(1) << n;

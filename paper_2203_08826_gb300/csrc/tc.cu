@@ -776,16 +776,7 @@ int prepare_tc(qsim_plan &p, int n) {
     return QSIM_OK;
 }
 
-int sm_count_tc() {
-    static int v = 0;
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        if (v <= 0) v = 148;
-    }
-    return v;
-}
+int sm_count_tc() { return device_sm_count(); }
 
 template <int K, int PREC>
 int launch_tc_k(const TcParams &prm, cudaStream_t st) {
