@@ -23,6 +23,9 @@
  *   - Host arrays passed in are read during the call and may be reused when it
  *     returns.  Device work runs asynchronously on the state's CUDA stream;
  *     calls that return host values synchronise that stream.
+ *   - One process drives one device (the multi-GPU paths run one rank per
+ *     GPU): the kernels' shared-memory limits are raised once per process,
+ *     on the device current at the first launch.
  *
  * Errors: every int-returning call returns QSIM_OK (0) or a negative code;
  * qsim_last_error() returns a thread-local message for the last failure.
