@@ -734,7 +734,7 @@ def other_workloads(q, torch, peak, peak_src):
     return out
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -754,7 +754,11 @@ def main():
                     help="headline mode only (no other modes, end-to-end or CPU legs): for profiling runs")
     ap.add_argument("--only", choices=["adjoint24", "batch4096"], default=None,
                     help="run one of the other workloads alone (small runs for profiling)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     ws, rank, local = dist_env()
     if args.only:
         run_only(args)

@@ -57,3 +57,20 @@ def test_oracle_baselines_beside_the_other_workloads():
     a = out["adjoint10_c64"]
     # two runs of the 290-gate circuit (10 layers of 10 RY, 10 RZ, 9 CZ) per gradient
     assert abs(a["value"] - a["gates_per_s"] / (2 * 290)) < 1e-9 * a["gates_per_s"]
+
+
+def test_profile_commands_parse():
+    """Every bench.py command line quoted in profiles/ is accepted by the
+    current argument parser (the summaries give the commands that made them)."""
+    import glob
+    import re
+    import shlex
+    import bench
+    seen = 0
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(f):
+            m = re.match(r"\s*python bench\.py(.*?)(?:\s*&&.*)?\s*\\?$", line)
+            if m:
+                bench.build_parser().parse_args(shlex.split(m.group(1)))
+                seen += 1
+    assert seen >= 8
