@@ -207,6 +207,21 @@ QSIM_API int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, do
 /* Human-readable summary of a plan (stages, tile qubits, op counts),
  * NUL-terminated and truncated to len bytes.  Host-only. */
 QSIM_API int qsim_plan_describe(const qsim_plan *p, char *buf, size_t len);
+/* Pass i of a QSIM_FUSE_TC plan (0 <= i < nsweeps) as the gates it applies,
+ * on the circuit's own qubits (host-only; for checking the planner against
+ * the gate-by-gate product of Eq. (1)).  *plain = 1: a gate no window holds,
+ * applied by a plain sweep: its k targets (targets[0] = MSB), nc controls and
+ * 2^k x 2^k row-major complex128 matrix (controls needs room for
+ * QSIM_MAX_CONTROLS + QSIM_MAX_TARGETS entries).  *plain = 0: the fused block
+ * on the window's k qubits (targets[0] = MSB), nc = 0, followed by *nepi
+ * diagonal gates (qsim_plan_tc_epilogue) that the pass applies after it.
+ * Outputs may be NULL; QSIM_EINVAL for other plans or i out of range. */
+QSIM_API int qsim_plan_tc_pass(const qsim_plan *p, int i, int *plain, int *k, int *targets, int *nc, int *controls,
+                               double *matrix, int *nepi);
+/* Epilogue gate e of pass i: k targets (targets[0] = MSB), nc controls and
+ * its 2^k diagonal entries (complex128, interleaved).  Host-only. */
+QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int *targets, int *nc, int *controls,
+                                   double *diag);
 /* Autotuner: builds the candidate plans (staged tiles of 2^12 and 2^13
  * amplitudes; for complex64 also tensor-core blocks of 5 and 6 qubits, for
  * complex128 one sweep per gate (greedy fusion with kmax = 1)), runs each on

@@ -62,6 +62,8 @@ _SIGS = {
     "qsim_plan_info": ([P, P, P, P], I),
     "qsim_plan_block": ([P, I, P, P, P], I),
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
+    "qsim_plan_tc_pass": ([P, I, P, P, P, P, P, P, P], I),
+    "qsim_plan_tc_epilogue": ([P, I, I, P, P, P, P, P], I),
     "qsim_apply_fused": ([P, P], I),
     "qsim_plan_autotune": ([P, P, I, P, P, P, P], I),
     "qsim_plan_autotune_ex": ([P, P, I, D, P, P, I, P], I),
@@ -275,6 +277,35 @@ class Plan:
         _check(lib().qsim_plan_block(self.handle, i, ctypes.byref(k), _p(t), _p(m)))
         d = 1 << k.value
         return tuple(int(v) for v in t[: k.value]), m.view(np.complex128).reshape(d, d)
+
+    def tc_passes(self) -> list:
+        """The passes of a tensor-core plan as gates on the circuit's qubits:
+        dicts with `plain`, `targets`, `controls`, `matrix` and, for fused
+        blocks, the diagonal `epilogue` gates applied after the block."""
+        out = []
+        C = 32  # room for QSIM_MAX_CONTROLS + QSIM_MAX_TARGETS entries
+        for i in range(self.info()["sweeps"]):
+            plain, k, nc, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            t, c = np.zeros(8, dtype=np.int32), np.zeros(C, dtype=np.int32)
+            _check(lib().qsim_plan_tc_pass(self.handle, i, ctypes.byref(plain), ctypes.byref(k), _p(t),
+                                           ctypes.byref(nc), _p(c), None, ctypes.byref(ne)))
+            d = 1 << k.value
+            m = np.zeros(2 * d * d, dtype=np.float64)
+            _check(lib().qsim_plan_tc_pass(self.handle, i, None, None, None, None, None, _p(m), None))
+            epi = []
+            for e in range(ne.value):
+                ek, enc = ctypes.c_int(), ctypes.c_int()
+                et, ec = np.zeros(C, dtype=np.int32), np.zeros(C, dtype=np.int32)
+                _check(lib().qsim_plan_tc_epilogue(self.handle, i, e, ctypes.byref(ek), _p(et), ctypes.byref(enc),
+                                                   _p(ec), None))
+                dg = np.zeros(2 << ek.value, dtype=np.float64)
+                _check(lib().qsim_plan_tc_epilogue(self.handle, i, e, None, None, None, None, _p(dg)))
+                epi.append({"targets": tuple(int(v) for v in et[: ek.value]),
+                            "controls": tuple(int(v) for v in ec[: enc.value]), "diag": dg.view(np.complex128)})
+            out.append({"plain": bool(plain.value), "targets": tuple(int(v) for v in t[: k.value]),
+                        "controls": tuple(int(v) for v in c[: nc.value]),
+                        "matrix": m.view(np.complex128).reshape(d, d), "epilogue": epi})
+        return out
 
 
 class SlicePlan:

@@ -869,6 +869,76 @@ void tc_describe(const qsim_plan &p, std::string &out) {
 
 }  // namespace qsim
 
+// ------------------------------------------------------------------ host inspection
+extern "C" {
+
+QSIM_API int qsim_plan_tc_pass(const qsim_plan *p, int i, int *plain, int *k, int *targets, int *nc, int *controls,
+                               double *matrix, int *nepi) {
+    using namespace qsim;
+    if (!p || !p->tc) return set_error(QSIM_EINVAL, "not a tensor-core plan");
+    if (i < 0 || i >= int(p->tc->passes.size())) return set_error(QSIM_EINVAL, "pass %d outside the plan", i);
+    const TcPass &ps = p->tc->passes[size_t(i)];
+    std::vector<int> t, c;
+    std::vector<cd> m;
+    if (ps.plain) {
+        const Op &op = ps.op;
+        t.assign(op.targets, op.targets + op.k);
+        c.assign(op.controls, op.controls + op.c);
+        const size_t d = size_t(1) << op.k;
+        m.assign(d * d, cd(0.0));
+        if (op.type == Op::DENSE) {
+            m = op.m;
+        } else {
+            for (size_t r = 0; r < d; ++r) {
+                if (op.type == Op::DIAG) m[r * d + r] = op.m[r];
+                else if (op.type == Op::MONO) m[r * d + size_t(op.perm[r])] = op.phase[r];
+                else m[r * d + r] = 1.0;
+            }
+        }
+    } else {
+        for (int j = ps.k - 1; j >= 0; --j) t.push_back((ps.off + j) % p->n);  // window, MSB first
+        m = ps.block;
+    }
+    if (plain) *plain = ps.plain ? 1 : 0;
+    if (k) *k = int(t.size());
+    if (targets)
+        for (size_t j = 0; j < t.size(); ++j) targets[j] = t[j];
+    if (nc) *nc = int(c.size());
+    if (controls)
+        for (size_t j = 0; j < c.size(); ++j) controls[j] = c[j];
+    if (matrix)
+        for (size_t j = 0; j < m.size(); ++j) {
+            matrix[2 * j] = m[j].real();
+            matrix[2 * j + 1] = m[j].imag();
+        }
+    if (nepi) *nepi = ps.plain ? 0 : int(ps.epi.size());
+    return QSIM_OK;
+}
+
+QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int *targets, int *nc, int *controls,
+                                   double *diag) {
+    using namespace qsim;
+    if (!p || !p->tc) return set_error(QSIM_EINVAL, "not a tensor-core plan");
+    if (i < 0 || i >= int(p->tc->passes.size())) return set_error(QSIM_EINVAL, "pass %d outside the plan", i);
+    const TcPass &ps = p->tc->passes[size_t(i)];
+    if (e < 0 || e >= int(ps.epi.size())) return set_error(QSIM_EINVAL, "epilogue gate %d outside pass %d", e, i);
+    const TcPass::Diag &dg = ps.epi[size_t(e)];
+    if (k) *k = int(dg.targets.size());
+    if (targets)
+        for (size_t j = 0; j < dg.targets.size(); ++j) targets[j] = dg.targets[j];
+    if (nc) *nc = int(dg.controls.size());
+    if (controls)
+        for (size_t j = 0; j < dg.controls.size(); ++j) controls[j] = dg.controls[j];
+    if (diag)
+        for (size_t j = 0; j < dg.d.size(); ++j) {
+            diag[2 * j] = dg.d[j].real();
+            diag[2 * j + 1] = dg.d[j].imag();
+        }
+    return QSIM_OK;
+}
+
+}  // extern "C"
+
 void qsim_plan::release_tc() {
     delete tc;
     tc = nullptr;

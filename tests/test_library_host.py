@@ -111,6 +111,57 @@ def test_greedy2_blocks_equal_product_of_oracle_gates(q, orc):
     assert plan.info()["sweeps"] < len(circ)
 
 
+def _tc_mixed_circuit(n, seed):
+    """Dense 1- and 2-qubit gates on near and distant qubits, controlled and
+    diagonal gates across windows, distant SWAPs and 3-qubit dense gates
+    (the last two need plain passes)."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(4):
+        for q_ in range(n):
+            gates.append(inputs.Gate("su2", (q_,), (), inputs.haar_su2_quaternion(rng)))
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        gates.append(inputs.Gate("matrix", (a, b), (), (), -1, inputs.random_dense_gate(rng, 2)))
+        gates.append(inputs.Gate("phase", (a,), (b,), (float(rng.uniform(0, 6)),)))
+        gates.append(inputs.Gate("cz", (0, n - 1)))
+        gates.append(inputs.Gate("rzz", (1, n - 2), (), (float(rng.uniform(0, 6)),)))
+        gates.append(inputs.Gate("x", (2,), (n - 3, 5)))
+        gates.append(inputs.Gate("swap", (3, n - 4)))
+        c3 = tuple(int(v) for v in rng.choice(n, 3, replace=False))
+        gates.append(inputs.Gate("matrix", c3, (), (), -1, inputs.random_dense_gate(rng, 3)))
+    return inputs.Circuit(n, gates, "tc-mixed")
+
+
+@pytest.mark.parametrize("kmax", [5, 6])
+@pytest.mark.parametrize("maker", ["random", "variational", "qft", "mixed"])
+def test_tensor_core_plan_replays_the_circuit(q, orc, maker, kmax):
+    """The tensor-core planner's passes -- fused window blocks, their diagonal
+    epilogues and plain passes -- applied in order by the oracle in complex128
+    give the circuit's own gate-by-gate result (Eq. (1)) to rounding: the
+    planner's fusion, deferral and commutation choices, checked without a GPU
+    and without the split precision of the tensor cores."""
+    n = 14
+    circ = {"random": lambda: inputs.random_circuit(n, 5, seed=3),
+            "variational": lambda: inputs.variational(n, 3, seed=4),
+            "qft": lambda: inputs.qft(n),
+            "mixed": lambda: _tc_mixed_circuit(n, seed=5)}[maker]()
+    psi0 = inputs.gaussian_state(n, seed=6)
+    want = orc.simulate(circ, psi0)
+    plan = q.Plan(circ, kmax=kmax, mode=q.FUSE_TC)
+    psi = psi0.copy()
+    passes = plan.tc_passes()
+    for ps in passes:
+        orc.apply_matrix(psi, ps["matrix"], ps["targets"], ps["controls"])
+        for e in ps["epilogue"]:
+            orc.apply_matrix(psi, np.diag(e["diag"]), e["targets"], e["controls"])
+    assert np.max(np.abs(psi - want)) < 1e-12
+    assert len(passes) == plan.info()["sweeps"]
+    # windows of kmax qubits; 6-wide plans close the rotation with 5s and 6s
+    assert {len(p["targets"]) for p in passes if not p["plain"]} <= ({5, 6} if kmax == 6 else {5})
+    if maker == "mixed":
+        assert any(p["plain"] for p in passes) and any(p["epilogue"] for p in passes)
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
