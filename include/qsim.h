@@ -222,6 +222,14 @@ QSIM_API int qsim_plan_tc_pass(const qsim_plan *p, int i, int *plain, int *k, in
  * its 2^k diagonal entries (complex128, interleaved).  Host-only. */
 QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int *targets, int *nc, int *controls,
                                    double *diag);
+/* Stage i of a QSIM_FUSE_STAGED plan (0 <= i < nsweeps; host-only, for
+ * checking the planner): *plain = 1 for a gate applied by a plain sweep;
+ * otherwise the tile's qubits beyond the lanes (nslots of them, in slot
+ * order; the lanes hold qubits 0..4).  gates receives the indices of the
+ * circuit's gates the stage applies (ngates of them, room for the circuit's
+ * gate count), in the order it applies them.  QSIM_EINVAL for other plans
+ * (a staged request on fewer than 9 qubits builds a greedy plan). */
+QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, int *ngates, int *gates, int *nslots, int *slots);
 /* Autotuner: builds the candidate plans (staged tiles of 2^12 and 2^13
  * amplitudes; for complex64 also tensor-core blocks of 5 and 6 qubits, for
  * complex128 one sweep per gate (greedy fusion with kmax = 1)), runs each on

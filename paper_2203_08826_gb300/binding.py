@@ -64,6 +64,7 @@ _SIGS = {
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
     "qsim_plan_tc_pass": ([P, I, P, P, P, P, P, P, P], I),
     "qsim_plan_tc_epilogue": ([P, I, I, P, P, P, P, P], I),
+    "qsim_plan_stage": ([P, I, P, P, P, P, P], I),
     "qsim_apply_fused": ([P, P], I),
     "qsim_plan_autotune": ([P, P, I, P, P, P, P], I),
     "qsim_plan_autotune_ex": ([P, P, I, D, P, P, I, P], I),
@@ -277,6 +278,21 @@ class Plan:
         _check(lib().qsim_plan_block(self.handle, i, ctypes.byref(k), _p(t), _p(m)))
         d = 1 << k.value
         return tuple(int(v) for v in t[: k.value]), m.view(np.complex128).reshape(d, d)
+
+    def stages(self) -> list:
+        """The stages of a staged plan: dicts with `plain`, `gates` (indices of
+        the circuit's gates, in the order applied) and `slots` (tile qubits
+        beyond the lanes 0..4)."""
+        out = []
+        ng = self.info()["gates"]
+        for i in range(self.info()["sweeps"]):
+            plain, k, ns = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            g, sl = np.zeros(max(ng, 1), dtype=np.int32), np.zeros(64, dtype=np.int32)
+            _check(lib().qsim_plan_stage(self.handle, i, ctypes.byref(plain), ctypes.byref(k), _p(g),
+                                         ctypes.byref(ns), _p(sl)))
+            out.append({"plain": bool(plain.value), "gates": [int(v) for v in g[: k.value]],
+                        "slots": [int(v) for v in sl[: ns.value]]})
+        return out
 
     def tc_passes(self) -> list:
         """The passes of a tensor-core plan as gates on the circuit's qubits:

@@ -461,6 +461,7 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
                     Stage st;
                     st.plain = true;
                     st.op = g.op;
+                    st.gates = {gi};
                     out.push_back(std::move(st));
                     plain_emitted = true;
                     continue;
@@ -491,6 +492,7 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
             if (std::find(tile.begin(), tile.end(), q) == tile.end()) tile.push_back(q);
         Stage st;
         st.slots = tile;
+        st.gates = sched;
         std::vector<const GateClass *> gl;
         for (int gi : sched) gl.push_back(&cls[gi]);
         const int rc = emit_stage_ops(st, gl, W, limits);
@@ -683,4 +685,22 @@ int qsim_plan::nsweeps() const {
     if (mode == QSIM_FUSE_STAGED) return qsim::staged_nsweeps(*this);
     if (mode == QSIM_FUSE_TC) return qsim::tc_nsweeps(*this);
     return int(blocks.size());
+}
+
+// ------------------------------------------------------------------ host inspection
+extern "C" QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, int *ngates, int *gates, int *nslots,
+                                        int *slots) {
+    using namespace qsim;
+    if (!p || !p->staged) return set_error(QSIM_EINVAL, "not a staged plan");
+    const std::vector<stage::Stage> &stages = p->staged->stages;
+    if (i < 0 || i >= int(stages.size())) return set_error(QSIM_EINVAL, "stage %d outside the plan", i);
+    const stage::Stage &st = stages[size_t(i)];
+    if (plain) *plain = st.plain ? 1 : 0;
+    if (ngates) *ngates = int(st.gates.size());
+    if (gates)
+        for (size_t j = 0; j < st.gates.size(); ++j) gates[j] = st.gates[j];
+    if (nslots) *nslots = int(st.slots.size());
+    if (slots)
+        for (size_t j = 0; j < st.slots.size(); ++j) slots[j] = st.slots[j];
+    return QSIM_OK;
 }

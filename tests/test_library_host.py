@@ -162,6 +162,40 @@ def test_tensor_core_plan_replays_the_circuit(q, orc, maker, kmax):
         assert any(p["plain"] for p in passes) and any(p["epilogue"] for p in passes)
 
 
+@pytest.mark.parametrize("kmax", [1, 3, 4])
+@pytest.mark.parametrize("maker", ["random", "variational", "qft", "mixed"])
+def test_staged_plan_schedule_replays_the_circuit(q, orc, maker, kmax):
+    """The staged planner's schedule (which of the circuit's gates each stage
+    applies, in which order, on which tile): every gate is applied exactly
+    once, the oracle replaying the gates in that order gives the gate-by-gate
+    result (so no reordering crosses a gate it does not commute with), and a
+    tile stage applies a non-diagonal gate only to qubits of its tile (lanes
+    0..4 and the stage's 4 + min(kmax, 4) slots)."""
+    n = 14
+    circ = {"random": lambda: inputs.random_circuit(n, 5, seed=3),
+            "variational": lambda: inputs.variational(n, 3, seed=4),
+            "qft": lambda: inputs.qft(n),
+            "mixed": lambda: _tc_mixed_circuit(n, seed=5)}[maker]()
+    psi0 = inputs.gaussian_state(n, seed=6)
+    stages = q.Plan(circ, kmax=kmax, mode=q.FUSE_STAGED).stages()
+    order = [gi for st in stages for gi in st["gates"]]
+    assert sorted(order) == list(range(len(circ)))
+    psi = psi0.copy()
+    for gi in order:
+        orc.apply_gate(psi, circ.gates[gi])
+    assert np.max(np.abs(psi - orc.simulate(circ, psi0))) < 1e-12
+    for st in stages:
+        if st["plain"]:
+            assert len(st["gates"]) == 1 and not st["slots"]
+            continue
+        assert len(st["slots"]) == 4 + min(kmax, 4)
+        tile = set(range(5)) | set(st["slots"])
+        for gi in st["gates"]:
+            m = orc.gate_matrix(circ.gates[gi])
+            if not np.array_equal(m, np.diag(np.diag(m))):
+                assert set(circ.gates[gi].targets) <= tile, (gi, circ.gates[gi])
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
