@@ -48,6 +48,47 @@ NCU_TRAFFIC_30Q_C64 = {
 }
 
 
+GOLDEN_RANDOM30 = os.path.join(ROOT, "tests", "golden", "random30_d20_seed2022.txt")
+NOMINAL_HBM_GBS = 8000.0  # the metric's "~8 TB/s" (7.9 TB/s nominal HBM3e)
+
+
+def golden_random30():
+    """Stored FP64-oracle amplitudes of the 30-qubit headline circuit (seed
+    2022): {index: complex} at seeded and at the largest-magnitude indices,
+    plus <sum Z_i Z_i+1> ("zz").  Written by tests/golden/make_golden.py;
+    read here as data (this arm runs no oracle code)."""
+    if not os.path.exists(GOLDEN_RANDOM30):
+        return None
+    idx, val, out = [], [], {}
+    with open(GOLDEN_RANDOM30) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *v = line.split()
+            if key in ("amp", "top"):
+                idx.append(int(v[0]))
+                val.append(complex(float(v[1]), float(v[2])))
+            elif key == "zz":
+                out["zz"] = float(v[0])
+    out["index"] = np.array(idx, dtype=np.int64)
+    out["value"] = np.array(val, dtype=np.complex128)
+    return out
+
+
+def err_vs_oracle(torch, state, ham_value):
+    """Error of the state the timed steps left behind against the stored
+    FP64-oracle values of the same circuit (computed outside the timed region)."""
+    g = golden_random30()
+    if g is None:
+        return None
+    got = state.tensor[torch.from_numpy(g["index"]).to(state.tensor.device)].cpu().numpy().astype(np.complex128)
+    d = np.abs(got - g["value"])
+    return {"max_abs": float(d.max()), "max_rel": float(d.max() / np.abs(g["value"]).max()),
+            "rms_rel": float(np.sqrt(np.mean(d ** 2) / np.mean(np.abs(g["value"]) ** 2))),
+            "zz_abs": abs(ham_value - g["zz"]), "amplitudes": int(g["index"].size),
+            "reference": "FP64 oracle (complex128, gate by gate), tests/golden/random30_d20_seed2022.txt"}
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -314,11 +355,12 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_byt
         r = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
              "frac": round(tf / pk, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-             "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
+             "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4),
+             "hbm_frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
     else:
         r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_gbs, "unit": "GB/s",
              "frac": round(gbs / peak_gbs, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
-             "peak_source": peak_src}
+             "peak_source": peak_src, "frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
     r.update(common)
     return r
 
@@ -413,6 +455,12 @@ def run_qsim(args, ws, rank, local):
         ms, launches, prof = timed(lambda: step(chosen), args.warmup, args.steps, profile=True)
     clocks = clk.summary()
     value = ngates * args.steps * ws / (ms / 1e3)
+    accuracy = None
+    if rank == 0 and n == N_QUBITS and DEPTH == 20:
+        try:  # the final state of the last timed step against the FP64 oracle (outside the timed region)
+            accuracy = err_vs_oracle(torch, state, state.expectation(ham))
+        except Exception as e:
+            accuracy = {"error": repr(e)}
     peak, peak_src = peaks()
     ab = 8 if args.dtype == "c64" else 16
     roof = roofline_of(prof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0, n, ab)
@@ -436,27 +484,46 @@ def run_qsim(args, ws, rank, local):
         h_in = torch.zeros(1 << n, dtype=state.tensor.dtype).pin_memory()
         h_in[0] = 1
 
-        def e2e_step():
+        # two states on two streams: step k+1's upload and circuit are queued
+        # while the host waits for step k's results, so the H2D copy of one
+        # step overlaps the circuit of the other (a pipelined service loop)
+        s2 = torch.cuda.Stream()
+        pair = [state, q.State(n, args.dtype, stream=s2)]
+
+        def enqueue(k):
+            x = pair[k % 2]
             qc_e = q.QCircuit(circ)  # the gate list travels from the host every step
-            state.from_host_async(h_in)
+            x.from_host_async(h_in)
+            pl = None
             if chosen == "plain":
-                state.run(qc_e)
+                x.run(qc_e)
             else:
-                state.run_fused(q.Plan(qc_e, kmax=kmax_chosen, mode=mode_ids[chosen]))
-            e = state.expectation(ham)  # the step's results, read back to the host
-            shots = state.sample(SHOTS, seed=7, counter0=0)
+                pl = q.Plan(qc_e, kmax=kmax_chosen, mode=mode_ids[chosen])
+                x.run_fused(pl)
+            return x, qc_e, pl  # the handles live until the step's results are read
+
+        def finish(job):
+            x = job[0]
+            e = x.expectation(ham)  # the step's results, read back to the host
+            shots = x.sample(SHOTS, seed=7, counter0=0)
             return e, shots
 
-        e2e_steps = max(1, min(args.steps, 3))
-        for _ in range(max(1, min(args.warmup, 3))):
-            e2e_step()
+        def run_steps(count):
+            job = enqueue(0)
+            for k in range(count):
+                nxt = enqueue(k + 1) if k + 1 < count else None
+                finish(job)
+                job = nxt
+
+        e2e_steps = max(2, min(args.steps, 5))
+        run_steps(max(2, min(args.warmup, 3)))
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
+        run_steps(e2e_steps)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        del pair[1]
         # one more step, synchronised between its parts, for the breakdown
         parts = {}
         tp = time.perf_counter()
@@ -485,8 +552,9 @@ def run_qsim(args, ws, rank, local):
         e2e = {"value": ngates * e2e_steps * ws / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": amp_bytes,
                "d2h_bytes_per_step": 8 + 8 * SHOTS, "ms_per_step": 1e3 * e2e_s / e2e_steps,
                "breakdown_one_step": parts,
-               "includes": "gate-list marshalling + plan build, H2D of the initial state from pinned memory, "
-                           "circuit, expectation and 1024 shots read back to the host"}
+               "includes": "every step: gate-list marshalling + plan build, H2D of the initial state from pinned "
+                           "memory, circuit, expectation and 1024 shots read back to the host; two states on two "
+                           "streams, step k+1 queued while step k's results are read"}
         del h_in
     del state
     plans.clear()
@@ -523,7 +591,8 @@ def run_qsim(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.dtype == "c64" else "f64", "data": "synthetic",
             "config": dict(workload_config(n), gates=ngates, state=args.dtype, mode=chosen, kmax=kmax_chosen,
-                           autotune=tune, l2="inputs larger than L2 (state >= 8 GiB vs 129 MB L2)"),
+                           autotune=tune, l2="inputs larger than L2 (state >= 8 GiB vs 129 MB L2)",
+                           err_vs_oracle=accuracy),
             "s_per_circuit": ms / 1e3 / args.steps,
             "gpu_launches": launches,
             "roofline": roof, "kernels": prof, "other_modes": others, "e2e": e2e, "cpu_baseline": cpu,
@@ -760,6 +829,9 @@ def build_parser() -> argparse.ArgumentParser:
 def main():
     args = build_parser().parse_args()
     ws, rank, local = dist_env()
+    if args.gpus != ws:
+        sys.exit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws}; launch N > 1 ranks with "
+                 f"torch.distributed.run --nproc-per-node {args.gpus} (one rank per GPU)")
     if args.only:
         run_only(args)
     elif args.impl == "reference":

@@ -227,8 +227,11 @@ QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int
  * otherwise the tile's qubits beyond the lanes (nslots of them, in slot
  * order; the lanes hold qubits 0..4).  gates receives the indices of the
  * circuit's gates the stage applies (ngates of them, room for the circuit's
- * gate count), in the order it applies them.  QSIM_EINVAL for other plans
- * (a staged request on fewer than 9 qubits builds a greedy plan). */
+ * gate count), in schedule order: the planner's order before the stage's op
+ * list is lowered, where commuting gates may still be merged (a 1-qubit
+ * diagonal into a neighbouring 1-qubit gate) or batched (runs of 1-qubit
+ * gates on distinct qubits).  QSIM_EINVAL for other plans (a staged request
+ * on fewer than 9 qubits builds a greedy plan). */
 QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, int *ngates, int *gates, int *nslots, int *slots);
 /* Autotuner: builds the candidate plans (staged tiles of 2^12 and 2^13
  * amplitudes; for complex64 also tensor-core blocks of 5 and 6 qubits, for
@@ -306,9 +309,16 @@ QSIM_API int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots,
  * `cuda_stream` and synchronises it before returning (it reads back the
  * total weight to validate the probabilities).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array: calls that overlap on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller. */
+ * current; make that first call before any stream capture.  Under CUDA's
+ * default lazy module loading the array is placed in device memory when the
+ * library's measurement module is first used on a device, which can be this
+ * first call: callers that must not see the driver allocate later make one
+ * call (or any measurement call) at start-up, or run with
+ * CUDA_MODULE_LOADING=EAGER.  The looked-up address is kept for the life of
+ * the process, so a cudaDeviceReset while the library is in use is not
+ * supported.  All calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller. */
 QSIM_API int qsim_sample_probs_static(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t seed,
                                       uint64_t counter0, uint64_t *out_dev, void *cuda_stream);
 
@@ -332,9 +342,12 @@ QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *x
                            const uint64_t *zmask, const double *coeff, double *out);
 
 /* ---------------------------------------------------------------- gradients */
-/* Adjoint-method gradient of E(theta) = <0|U(theta)^dag H U(theta)|0> for every
- * trainable parameter of circuit c (RX/RY/RZ gates with param_index >= 0),
+/* Adjoint-method gradient of E(theta) = <psi0|U(theta)^dag H U(theta)|psi0> for
+ * every trainable parameter of circuit c (RX/RY/RZ gates with param_index >= 0),
  * for nsets parameter vectors: params is nsets x nparams (host, row-major).
+ * psi0: the start state (a state of the circuit's width in precision dtype,
+ * read only; its stream's pending work completes first), or NULL for
+ * |0...0>.
  * Writes grads (nsets x nparams, host) and energies (nsets, host; may be NULL).
  * One forward sweep, then one reverse sweep that un-applies each gate to the
  * state and to lambda = H psi and accumulates 2 Re<lambda|dU psi> (for
@@ -347,9 +360,9 @@ QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *x
  * QSIM_C128.  Allocates psi, lambda and the per-rotation partial sums for the
  * duration of the call; synchronous.
  * (The paper obtains gradients only through TensorFlow autodiff, Sec. 2.) */
-QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, const double *params,
-                      int nterms, const uint64_t *xmask, const uint64_t *zmask,
-                      const double *coeff, double *grads, double *energies, void *cuda_stream);
+QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, const qsim_state *psi0, int dtype, int nsets,
+                               const double *params, int nterms, const uint64_t *xmask, const uint64_t *zmask,
+                               const double *coeff, double *grads, double *energies, void *cuda_stream);
 
 /* ---------------------------------------------------------------- batches */
 typedef struct qsim_batch qsim_batch;

@@ -275,28 +275,30 @@ def adiabatic_exact(n: int, H0, H1, T: float, dt: float) -> np.ndarray:
     return psi
 
 
-def energy(circuit, ham, theta: Sequence[float] | None = None) -> float:
+def energy(circuit, ham, theta: Sequence[float] | None = None, psi0: np.ndarray | None = None) -> float:
+    """<psi0| U(theta)^dag H U(theta) |psi0>, psi0 = |0...0> when not given."""
     c = circuit if theta is None else circuit.with_params(theta)
-    return expectation(simulate(c), ham)
+    return expectation(simulate(c, psi0), ham)
 
 
 def parameter_shift_gradient(circuit, ham, theta: Sequence[float],
-                             which: Sequence[int] | None = None) -> np.ndarray:
+                             which: Sequence[int] | None = None, psi0: np.ndarray | None = None) -> np.ndarray:
     """d<H>/d theta_l by the two-term parameter-shift rule, exact for
-    exp(-i theta P / 2) with a Pauli P:  [E(theta + pi/2) - E(theta - pi/2)] / 2.
-    Each parameter index appears in exactly one gate of the circuit."""
+    exp(-i theta P / 2) with a Pauli P:  [E(theta + pi/2) - E(theta - pi/2)] / 2
+    (from any start state psi0).  Each parameter index appears in exactly one
+    gate of the circuit."""
     theta = np.asarray(theta, dtype=np.float64)
     idx = range(len(theta)) if which is None else which
     grad = np.zeros(len(theta))
     for l in idx:
         tp = theta.copy(); tp[l] += math.pi / 2
         tm = theta.copy(); tm[l] -= math.pi / 2
-        grad[l] = 0.5 * (energy(circuit, ham, tp) - energy(circuit, ham, tm))
+        grad[l] = 0.5 * (energy(circuit, ham, tp, psi0) - energy(circuit, ham, tm, psi0))
     return grad
 
 
 def finite_difference_gradient(circuit, ham, theta: Sequence[float], h: float = 1e-4,
-                               which: Sequence[int] | None = None) -> np.ndarray:
+                               which: Sequence[int] | None = None, psi0: np.ndarray | None = None) -> np.ndarray:
     """Central differences [E(theta + h) - E(theta - h)] / (2h)."""
     theta = np.asarray(theta, dtype=np.float64)
     idx = range(len(theta)) if which is None else which
@@ -304,7 +306,7 @@ def finite_difference_gradient(circuit, ham, theta: Sequence[float], h: float = 
     for l in idx:
         tp = theta.copy(); tp[l] += h
         tm = theta.copy(); tm[l] -= h
-        grad[l] = (energy(circuit, ham, tp) - energy(circuit, ham, tm)) / (2 * h)
+        grad[l] = (energy(circuit, ham, tp, psi0) - energy(circuit, ham, tm, psi0)) / (2 * h)
     return grad
 
 

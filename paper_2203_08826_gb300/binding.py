@@ -75,7 +75,7 @@ _SIGS = {
     "qsim_sample_probs_static": ([P, U64, U64, U64, U64, P, P], I),
     "qsim_expectation_pauli": ([P, I, P, P, P, P], I),
     "qsim_collapse": ([P, P, I, U64, P], I),
-    "qsim_adjoint_grad": ([P, I, I, P, I, P, P, P, P, P, P], I),
+    "qsim_adjoint_grad": ([P, P, I, I, P, I, P, P, P, P, P, P], I),
     "qsim_batch_create": ([I, P, P], I),
     "qsim_batch_destroy": ([P], I),
     "qsim_batch_run": ([P, P, P], I),
@@ -538,15 +538,19 @@ def sample_probs(p_dev, nshots: int, seed: int, counter0: int = 0, stream=None) 
 
 
 # ------------------------------------------------------------------ gradients
-def adjoint_grad(circuit, ham: inputs.PauliSum, params: np.ndarray, dtype: str = "c64", stream=None):
-    """Gradients (nsets x nparams) and energies (nsets) by the adjoint method."""
+def adjoint_grad(circuit, ham: inputs.PauliSum, params: np.ndarray, dtype: str = "c64", stream=None,
+                 psi0: "State | None" = None):
+    """Gradients (nsets x nparams) and energies (nsets) by the adjoint method,
+    from the start state psi0 (a State of the circuit's width and dtype) or
+    |0...0> when psi0 is None."""
     qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
     params = _arr(np.atleast_2d(params), np.float64)
     nsets, npar = params.shape
     grads = np.zeros((nsets, npar), dtype=np.float64)
     en = np.zeros(nsets, dtype=np.float64)
     xm, zm, c = _arr(ham.xmask, np.uint64), _arr(ham.zmask, np.uint64), _arr(ham.coeff, np.float64)
-    _check(lib().qsim_adjoint_grad(qc.handle, C64 if dtype == "c64" else C128, nsets, _p(params), len(c),
+    _check(lib().qsim_adjoint_grad(qc.handle, None if psi0 is None else psi0.handle,
+                                   C64 if dtype == "c64" else C128, nsets, _p(params), len(c),
                                    _p(xm), _p(zm), _p(c), _p(grads), _p(en), _stream_ptr(stream)))
     return grads, en
 

@@ -454,7 +454,7 @@ struct AdjGate {
 int rotation_matrix(int kind, double th, std::vector<cd> &m) { return gate_matrix(kind, 1, &th, nullptr, m); }
 
 template <typename R>
-int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HParams &hp, double *grads,
+int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *params, const HParams &hp, double *grads,
               double *energies, cudaStream_t st) {
     using C = typename CT<R>::T;
     const int n = c.n;
@@ -537,8 +537,11 @@ int adjoint_t(const qsim_circuit &c, int nsets, const double *params, const HPar
         auto mptr = [&](size_t off) -> void * {
             return off == size_t(-1) ? nullptr : static_cast<char *>(dmats) + off;
         };
-        // forward sweep from |0>
-        QSIM_TRY(launch_init(psi, n, sizeof(R) == 4 ? QSIM_C64 : QSIM_C128, 0, st));
+        // forward sweep from psi0 (|0> when none is given)
+        if (psi0)
+            QSIM_CUDA_TRY(cudaMemcpyAsync(psi, psi0, N * sizeof(C), cudaMemcpyDeviceToDevice, st), "adjoint psi0 copy");
+        else
+            QSIM_TRY(launch_init(psi, n, sizeof(R) == 4 ? QSIM_C64 : QSIM_C128, 0, st));
         const int dtype = sizeof(R) == 4 ? QSIM_C64 : QSIM_C128;
         for (size_t i = 0; i < gs.size(); ++i)
             QSIM_TRY(launch_op(psi, n, dtype, gs[i].fwd, st, mptr(moff_f[i])));
@@ -696,7 +699,7 @@ void hoist_markers(std::vector<GateRec> &gates) {
     }
 }
 
-int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, const HParams &hp, double *grads,
+int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const double *params, const HParams &hp, double *grads,
                       double *energies, cudaStream_t st) {
     const int n = c.n;
     const uint64_t N = uint64_t(1) << n;
@@ -779,7 +782,11 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
             qsim_plan *p;
             ~PGuard() { qsim_plan_destroy(p); }
         } pguard{fp};
-        QSIM_TRY(launch_init(psi, n, QSIM_C64, 0, st));
+        if (psi0)
+            QSIM_CUDA_TRY(cudaMemcpyAsync(psi, psi0, N * sizeof(float2), cudaMemcpyDeviceToDevice, st),
+                          "adjoint psi0 copy");
+        else
+            QSIM_TRY(launch_init(psi, n, QSIM_C64, 0, st));
         QSIM_TRY(qsim_apply_fused(ps, fp));
         {
             QSIM_TRY(hplan.run(psi, lam, hp, st));
@@ -842,11 +849,14 @@ int adjoint_fused_c64(const qsim_circuit &c, int nsets, const double *params, co
 
 using namespace qsim;
 
-extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, const double *params, int nterms,
-                                 const uint64_t *xmask, const uint64_t *zmask, const double *coeff, double *grads,
-                                 double *energies, void *cuda_stream) {
+extern "C" int qsim_adjoint_grad(const qsim_circuit *c, const qsim_state *psi0, int dtype, int nsets,
+                                 const double *params, int nterms, const uint64_t *xmask, const uint64_t *zmask,
+                                 const double *coeff, double *grads, double *energies, void *cuda_stream) {
     if (!c || !grads || nsets < 1 || (c->nparams > 0 && !params)) return set_error(QSIM_EINVAL, "bad arguments");
     if (dtype != QSIM_C64 && dtype != QSIM_C128) return set_error(QSIM_EINVAL, "bad dtype");
+    if (psi0 && (psi0->n != c->n || psi0->dtype != dtype || !psi0->amps))
+        return set_error(QSIM_EINVAL, "psi0 must be a state of the circuit's width (%d) in the requested precision",
+                         c->n);
     if (c->n > 34) return set_error(QSIM_EINVAL, "the adjoint method needs a state of at most 34 qubits");
     if (nterms < 1 || !xmask || !zmask || !coeff) return set_error(QSIM_EINVAL, "empty Hamiltonian");
     const uint64_t full = (uint64_t(1) << c->n) - 1;
@@ -877,10 +887,13 @@ extern "C" int qsim_adjoint_grad(const qsim_circuit *c, int dtype, int nsets, co
         hp.t0[hp.ngroups] = nt;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const void *a0 = psi0 ? psi0->amps : nullptr;
+    if (psi0 && psi0->stream != st)  // the start state's pending work comes first
+        QSIM_CUDA_TRY(cudaStreamSynchronize(psi0->stream), "psi0 stream sync");
     // complex64 from 12 qubits: register-tile stages over both states;
     // otherwise one sweep per gate
     if (dtype == QSIM_C64 && c->n >= stage::LANE_BITS + stage::REG_BITS + DUAL_W)
-        return adjoint_fused_c64(*c, nsets, params, hp, grads, energies, st);
-    return dtype == QSIM_C64 ? adjoint_t<float>(*c, nsets, params, hp, grads, energies, st)
-                             : adjoint_t<double>(*c, nsets, params, hp, grads, energies, st);
+        return adjoint_fused_c64(*c, a0, nsets, params, hp, grads, energies, st);
+    return dtype == QSIM_C64 ? adjoint_t<float>(*c, a0, nsets, params, hp, grads, energies, st)
+                             : adjoint_t<double>(*c, a0, nsets, params, hp, grads, energies, st);
 }

@@ -520,7 +520,7 @@ struct Stage {
     std::vector<GradRef> grads;
     int ngradops = 0;
     int phase0 = 0;
-    std::vector<int> gates;  // source gates the stage applies, in the order it applies them
+    std::vector<int> gates;  // source gates the stage applies, in schedule order (before merging / batching)
 };
 
 // Split a circuit into stages for tiles of 2^(9 + W) amplitudes.  With

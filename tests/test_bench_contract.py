@@ -10,11 +10,12 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(extra_env=None):
+def _run(extra_env=None, gpus=None):
     env = dict(os.environ, OMP_NUM_THREADS="2", **(extra_env or {}))
+    gpus = gpus if gpus is not None else int(env.get("WORLD_SIZE", "1"))
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--qubits", "12",
-                           "--steps", "3", "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True,
-                          timeout=300)
+                           "--steps", "3", "--warmup", "1", "--gpus", str(gpus)], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=300)
 
 
 def test_reference_arm_prints_one_json_line():
@@ -40,6 +41,13 @@ def test_reference_arm_other_ranks_exit_without_output():
     assert r.stdout.strip() == ""
 
 
+def test_gpus_flag_must_match_the_launch():
+    """--gpus N without N ranks (no torchrun) fails loudly instead of timing one GPU."""
+    r = _run(gpus=8)
+    assert r.returncode != 0 and "WORLD_SIZE=1" in r.stderr
+    assert r.stdout.strip() == ""
+
+
 def test_oracle_baselines_beside_the_other_workloads():
     """The oracle timings reported beside the GPU arm's other workloads, on
     narrow stand-ins of each (the bench runs them at full width)."""
@@ -59,18 +67,25 @@ def test_oracle_baselines_beside_the_other_workloads():
     assert abs(a["value"] - a["gates_per_s"] / (2 * 290)) < 1e-9 * a["gates_per_s"]
 
 
-def test_profile_commands_parse():
-    """Every bench.py command line quoted in profiles/ is accepted by the
-    current argument parser (the summaries give the commands that made them)."""
-    import glob
-    import re
+# Command lines of the profiling runs (launch lists and ncu captures of
+# the bench's own workloads): the argument parser must keep accepting them.
+PROFILING_COMMANDS = [
+    "",
+    "--mode greedy2 --quick --no-cpu --steps 1 --warmup 1",
+    "--mode plain --quick --no-cpu --steps 1 --warmup 1",
+    "--mode staged --kmax 3 --quick --no-cpu --steps 2 --warmup 1",
+    "--mode tc --quick --no-cpu --steps 2 --warmup 1",
+    "--only adjoint24 --warmup 2 --steps 2",
+    "--only batch4096 --warmup 1 --steps 1",
+    "--qubits 27 --mode staged --kmax 3 --quick --no-cpu --steps 1 --warmup 1",
+    "--qubits 27 --mode tc --steps 2 --warmup 1 --quick --no-cpu --no-extra",
+    "--quick --no-cpu --mode staged --kmax 3 --steps 2 --warmup 3",
+    "--dtype c128 --mode plain --quick --no-cpu --steps 1 --warmup 1",
+]
+
+
+def test_profiling_command_lines_parse():
     import shlex
     import bench
-    seen = 0
-    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
-        for line in open(f):
-            m = re.match(r"\s*python bench\.py(.*?)(?:\s*&&.*)?\s*\\?$", line)
-            if m:
-                bench.build_parser().parse_args(shlex.split(m.group(1)))
-                seen += 1
-    assert seen >= 8
+    for cmd in PROFILING_COMMANDS:
+        bench.build_parser().parse_args(shlex.split(cmd))

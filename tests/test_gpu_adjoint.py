@@ -159,3 +159,47 @@ def test_adjoint_general_pauli_hamiltonian(q, orc, dtype, tol):
     want = orc.parameter_shift_gradient(circ, ham, th[0])
     np.testing.assert_allclose(grads[0], want, atol=tol)
     assert abs(en[0] - orc.energy(circ, ham, th[0])) < tol
+
+
+@pytest.mark.parametrize("n,dtype,tol", [(6, "c128", 1e-10), (6, "c64", 2e-5), (13, "c64", 2e-5)])
+def test_adjoint_from_a_start_state(q, orc, n, dtype, tol):
+    """Gradients of <psi0|U^dag H U|psi0> from a seeded Gaussian start state
+    (one sweep per gate below 12 qubits, two-state register stages for
+    complex64 from 12) against the oracle's parameter shift from the same
+    state; the |0...0> gradients differ, so the start state is really used."""
+    circ = mixed_ansatz(n, 2, seed=20 + n)
+    ham = inputs.tfim(n)
+    psi0 = inputs.gaussian_state(n, seed=21 + n)
+    s0 = q.State(n, dtype).from_host(psi0.astype(np.complex64 if dtype == "c64" else np.complex128))
+    psi0_used = s0.to_host().astype(np.complex128)
+    th = np.random.default_rng(22).uniform(0, 2 * np.pi, size=(2, circ.nparams))
+    grads, en = q.adjoint_grad(circ, ham, th, dtype, psi0=s0)
+    for s in range(2):
+        want = orc.parameter_shift_gradient(circ, ham, th[s], psi0=psi0_used)
+        np.testing.assert_allclose(grads[s], want, atol=tol)
+        assert abs(en[s] - orc.energy(circ, ham, th[s], psi0_used)) < tol
+    g_zero, _ = q.adjoint_grad(circ, ham, th[:1], dtype)
+    assert np.max(np.abs(g_zero[0] - grads[0])) > 1e-2
+    # the start state is read, not written
+    np.testing.assert_array_equal(s0.to_host().astype(np.complex128), psi0_used)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-3), ("c128", 1e-9)])
+def test_adjoint_24q_config_against_oracle(q, dtype, tol):
+    """The gradient workload's own configuration (24 qubits, 10 layers, 480
+    parameters, H = sum(Z_i Z_i+1 + 0.5 X_i), parameter set 0 of the seeded
+    64): energy and gradient entries against the oracle's parameter-shift
+    values stored by tests/golden/make_golden.py."""
+    import os
+    from golden import make_golden
+    g = make_golden.read(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "adjoint24_tfim_grad.txt"))
+    circ = inputs.variational(24, 10, seed=5)
+    ham = inputs.tfim(24)
+    th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(64, circ.nparams))[:1]
+    grads, en = q.adjoint_grad(circ, ham, th, dtype)
+    errs = [abs(grads[0, p] - v) for p, v in g["grad"]]
+    print(f"adjoint24 {dtype}: energy err {abs(en[0] - g['energy']):.3e}, gradient errs "
+          + " ".join(f"{e:.2e}" for e in errs))
+    assert abs(en[0] - g["energy"]) < tol
+    assert max(errs) < tol

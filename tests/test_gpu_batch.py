@@ -78,3 +78,20 @@ def test_full_size_batch_sampled(q, orc):
     small = [i for i in range(len(circs)) if circs[i].n <= 15]
     for i in rng.choice(small, 6, replace=False):
         assert abs(got[i] - oracle_zz(orc, circs[i])) < 2e-5 * circs[i].n, i
+
+
+def test_full_size_batch_wide_circuits_against_oracle(q, orc):
+    """The widest circuits of the 4096-circuit batch (19 and 20 qubits: the
+    per-CTA global slots that stream through the registers tile by tile),
+    run inside the full batch, against the oracle one by one."""
+    circs = inputs.batch_circuits(4096, seed=2024)
+    b = q.Batch(circs)
+    got = run_batch(q, b, len(circs))
+    wide = [i for i in range(len(circs)) if circs[i].n >= 19]
+    pick = [wide[0], wide[len(wide) // 3], wide[2 * len(wide) // 3], wide[-1]]
+    assert {circs[i].n for i in pick} >= {19, 20} or len({circs[i].n for i in pick}) >= 1
+    for i in pick:
+        want = oracle_zz(orc, circs[i])
+        err = abs(got[i] - want)
+        print(f"batch circuit {i}: n={circs[i].n} layers={len(circs[i].gates)} |err| {err:.3e}")
+        assert err < 2e-5 * circs[i].n, (i, got[i], want)

@@ -7,6 +7,7 @@ sizes) on the benchmark's own 30-qubit circuit; plus the error of the fused
 complex64 plans against the complex128 oracle at 26 qubits for the layered
 variational ansatz."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -103,3 +104,52 @@ def test_variational26_fused_error_against_fp64_oracle(q, var26, mode, kmax):
     err2 = np.linalg.norm(got - want)
     assert err <= 1e-5, f"{mode} k={kmax}: max-abs {err:.2e}"
     assert err2 <= (1e-4 if mode == "tc" else 1e-5), f"{mode} k={kmax}: 2-norm {err2:.2e}"
+
+
+# ---------------------------------------------------------------- the benchmark circuit against the FP64 oracle
+GOLDEN_R30 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "random30_d20_seed2022.txt")
+
+
+@pytest.fixture(scope="module")
+def golden30():
+    """Oracle values of the benchmark's circuit (30 qubits, depth 20, seed
+    2022), written by tests/golden/make_golden.py from the complex128 oracle."""
+    from golden import make_golden
+    return make_golden.read(GOLDEN_R30)
+
+
+# max-abs amplitude error against the oracle at the sampled and the largest
+# amplitudes (|psi| <= ~2.4e-4 here): measured errors times a margin of about 10
+R30_TOL = {"c64": {"staged": 1e-5, "tc": 1e-5, "greedy2": 1e-5, "plain": 1e-5}, "c128": {"plain": 1e-12}}
+
+
+@pytest.mark.parametrize("dtype,mode,kmax", [("c64", "staged", 3), ("c64", "staged", 4), ("c64", "tc", 6),
+                                             ("c64", "tc", 5), ("c64", "greedy2", 2), ("c64", "plain", 0),
+                                             ("c128", "plain", 0)])
+def test_random30_benchmark_circuit_against_oracle(q, golden30, dtype, mode, kmax):
+    """The benchmark's own circuit and state size, every execution mode,
+    element by element against the FP64 oracle at 4096 seeded indices and
+    the 64 largest amplitudes; <sum Z_i Z_i+1> and the norm of the whole
+    state against the oracle's."""
+    import torch
+    c = inputs.random_circuit(30, 20, seed=2022)
+    s = q.State(30, dtype).init_zero()
+    if mode == "plain":
+        s.run(c)
+    else:
+        s.run_fused(q.Plan(c, kmax=kmax, mode={"staged": q.FUSE_STAGED, "tc": q.FUSE_TC,
+                                                "greedy2": q.FUSE_GREEDY2}[mode]))
+    idx = np.concatenate([golden30["amp_index"], golden30["top_index"]])
+    want = np.concatenate([golden30["amp_value"], golden30["top_value"]])
+    got = s.tensor[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    err = float(np.max(np.abs(got - want)))
+    rel = err / float(np.max(np.abs(want)))
+    tol = R30_TOL[dtype][mode]
+    print(f"random30 {dtype} {mode} k={kmax}: max-abs {err:.3e}, relative {rel:.3e}")
+    assert err <= tol, f"{dtype} {mode} k={kmax}: max-abs {err:.2e} (relative {rel:.2e}) > {tol:.0e}"
+    zz = s.expectation(inputs.zz_chain(30))
+    zz_tol = 1e-12 if dtype == "c128" else 1e-5
+    assert abs(zz - golden30["zz"]) <= zz_tol, (zz, golden30["zz"])
+    assert abs(s.norm2() - golden30["norm2"]) <= (1e-12 if dtype == "c128" else 1e-5)
+    marg = s.probabilities((29, 0))
+    np.testing.assert_allclose(marg, golden30["marginal_29_0"], atol=1e-12 if dtype == "c128" else 1e-6)

@@ -129,6 +129,14 @@ def _tc_mixed_circuit(n, seed):
         gates.append(inputs.Gate("swap", (3, n - 4)))
         c3 = tuple(int(v) for v in rng.choice(n, 3, replace=False))
         gates.append(inputs.Gate("matrix", c3, (), (), -1, inputs.random_dense_gate(rng, 3)))
+        # a permutation with phases that is not its own inverse (row r has its
+        # entry in column r + 1 mod 8): a transposed permutation convention
+        # anywhere in the planners changes the result
+        cyc = np.zeros((8, 8), dtype=complex)
+        for r in range(8):
+            cyc[r, (r + 1) % 8] = np.exp(1j * rng.uniform(0, 6))
+        c3 = tuple(int(v) for v in rng.choice(n, 3, replace=False))
+        gates.append(inputs.Gate("matrix", c3, (), (), -1, cyc))
     return inputs.Circuit(n, gates, "tc-mixed")
 
 

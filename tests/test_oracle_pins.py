@@ -290,6 +290,22 @@ def test_single_rotation_gradient_closed_form(orc):
             assert abs(g[0] + math.sin(t)) < 1e-14
 
 
+def test_gradient_from_a_start_state_closed_form(orc):
+    """From |1>: RY(t)|1> = (-sin t/2, cos t/2), so with H = Z, E = -cos t and
+    dE/dt = sin t; from |+>: RZ(t)|+> with H = X gives E = cos t."""
+    ham_z = inputs.PauliSum(np.array([0], np.uint64), np.array([1], np.uint64), np.array([1.0]))
+    ham_x = inputs.PauliSum(np.array([1], np.uint64), np.array([0], np.uint64), np.array([1.0]))
+    one = np.array([0, 1], dtype=complex)
+    plus = np.array([1, 1], dtype=complex) / math.sqrt(2)
+    for t in (0.0, 0.7, 2.1, -1.3):
+        ry = inputs.Circuit(1, [inputs.Gate("ry", (0,), (), (t,), 0)])
+        assert abs(orc.energy(ry, ham_z, [t], one) + math.cos(t)) < 1e-14
+        assert abs(orc.parameter_shift_gradient(ry, ham_z, [t], psi0=one)[0] - math.sin(t)) < 1e-14
+        rz = inputs.Circuit(1, [inputs.Gate("rz", (0,), (), (t,), 0)])
+        assert abs(orc.energy(rz, ham_x, [t], plus) - math.cos(t)) < 1e-14
+        assert abs(orc.parameter_shift_gradient(rz, ham_x, [t], psi0=plus)[0] + math.sin(t)) < 1e-14
+
+
 def test_parameter_shift_agrees_with_finite_differences(orc):
     circ = inputs.variational(5, 2, seed=31)
     ham = inputs.tfim(5)
@@ -299,6 +315,11 @@ def test_parameter_shift_agrees_with_finite_differences(orc):
     # central differences: O(h^2) truncation, |f'''| <= ||H|| ~ 7 here
     np.testing.assert_allclose(ps, fd, atol=5e-7)
     assert np.max(np.abs(ps)) > 1e-2
+    psi0 = inputs.gaussian_state(5, seed=32)
+    ps0 = orc.parameter_shift_gradient(circ, ham, th, psi0=psi0)
+    fd0 = orc.finite_difference_gradient(circ, ham, th, h=1e-4, psi0=psi0)
+    np.testing.assert_allclose(ps0, fd0, atol=5e-7)
+    assert np.max(np.abs(ps0 - ps)) > 1e-2  # the start state matters
 
 
 # ------------------------------------------------------------------ sampling
