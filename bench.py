@@ -65,6 +65,7 @@ def golden_random30():
             if line.startswith("#") or not line.strip():
                 continue
             key, *v = line.split()
+            v = [t[len("np.float64("):-1] if t.startswith("np.float64(") else t for t in v]
             if key in ("amp", "top"):
                 idx.append(int(v[0]))
                 val.append(complex(float(v[1]), float(v[2])))

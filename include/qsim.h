@@ -23,6 +23,12 @@
  *   - Host arrays passed in are read during the call and may be reused when it
  *     returns.  Device work runs asynchronously on the state's CUDA stream;
  *     calls that return host values synchronise that stream.
+ *   - QSIM_C128 arithmetic: dense 1-qubit and diagonal sweeps compute each
+ *     amplitude either in FP64 or in double-float arithmetic (a double held as
+ *     the sum of two floats, about 48 significant bits, on the FP32 pipes, with
+ *     FP64 for values outside [2^-74, 2^77) and subnormals read as 0); other
+ *     complex128 kernels use FP64.  The per-gate error stays near 1e-14
+ *     relative.
  *   - One process drives one device (the multi-GPU paths run one rank per
  *     GPU): the kernels' shared-memory limits are raised once per process,
  *     on the device current at the first launch.
@@ -481,6 +487,21 @@ QSIM_API uint64_t qsim_sampler_weight_c64(float re, float im);
 /* The complex64 probability re^2 + im^2 rounded once to double, by the
  * integer rule qsim_probabilities uses for complex64 states (host). */
 QSIM_API double qsim_prob_c64(float re, float im);
+/* Failure injection on the host (test support; the paper has no counterpart):
+ * after `skip` more successful device allocations by the library, the next
+ * `count` fail as if the device were out of memory, so every entry point's
+ * QSIM_ENOMEM path (and its release of what it had allocated) can be
+ * exercised without exhausting a GPU.  (0, 0) turns injection off.  Affects
+ * all threads; QSIM_EINVAL for negative arguments. */
+QSIM_API int qsim_debug_fail_alloc(int skip, int count);
+/* Polls a tensor-core pipeline wait (QSIM_FUSE_TC passes) makes before it
+ * gives up (test support; 0 restores the default of 2^26).  A wait that gives
+ * up stops every role of its CTA; the CTA still waits, with the default
+ * bound, for the tensor-core work it has committed before it frees its tensor
+ * memory, and qsim_apply_fused returns QSIM_ETIMEOUT with the state's
+ * contents undefined.  A limit of a few polls makes the first waits expire,
+ * which tests the timeout path without a fault or a hang. */
+QSIM_API int qsim_debug_set_wait_limit(unsigned long long polls);
 
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each

@@ -95,6 +95,8 @@ _SIGS = {
     "qsim_slice_run": ([P, I, P, I, P], I),
     "qsim_sampler_weight_c64": ([ctypes.c_float, ctypes.c_float], U64),
     "qsim_prob_c64": ([ctypes.c_float, ctypes.c_float], D),
+    "qsim_debug_fail_alloc": ([I, I], I),
+    "qsim_debug_set_wait_limit": ([ctypes.c_ulonglong], I),
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),

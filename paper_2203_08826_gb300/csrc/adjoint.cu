@@ -324,7 +324,7 @@ struct HPlan {
                             sm[size_t(j) * 256 + size_t(v)] = R(f);
                         }
                     const size_t pb = pt.size() * sizeof(uint64_t), sb = sm.size() * sizeof(R);
-                    QSIM_CUDA_TRY(cudaMalloc(&dtabs, pb + sb), "hamiltonian tables");
+                    QSIM_CUDA_TRY(dev_alloc(&dtabs, pb + sb), "hamiltonian tables");
                     QSIM_CUDA_TRY(cudaMemcpyAsync(dtabs, pt.data(), pb, cudaMemcpyHostToDevice, st), "hamiltonian tables");
                     QSIM_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(dtabs) + pb, sm.data(), sb,
                                                   cudaMemcpyHostToDevice, st),
@@ -472,10 +472,10 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
     C *psi = nullptr, *lam = nullptr;
     double *partial = nullptr, *rows = nullptr;
     const size_t prow = size_t(blocks);
-    cudaError_t e = cudaMalloc(&psi, N * sizeof(C));
-    if (e == cudaSuccess) e = cudaMalloc(&lam, N * sizeof(C));
-    if (e == cudaSuccess) e = cudaMalloc(&partial, (size_t(nrot) + 1) * prow * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    cudaError_t e = dev_alloc(&psi, N * sizeof(C));
+    if (e == cudaSuccess) e = dev_alloc(&lam, N * sizeof(C));
+    if (e == cudaSuccess) e = dev_alloc(&partial, (size_t(nrot) + 1) * prow * sizeof(double));
+    if (e == cudaSuccess) e = dev_alloc(&rows, (size_t(nrot) + 1) * sizeof(double));
     struct Guard {
         void *p[4];
         ~Guard() {
@@ -529,7 +529,7 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
         }
         void *dmats = nullptr;
         if (!matbuf.empty()) {
-            QSIM_CUDA_TRY(cudaMalloc(&dmats, matbuf.size()), "adjoint matrices");
+            QSIM_CUDA_TRY(dev_alloc(&dmats, matbuf.size()), "adjoint matrices");
             QSIM_CUDA_TRY(cudaMemcpyAsync(dmats, matbuf.data(), matbuf.size(), cudaMemcpyHostToDevice, st),
                           "adjoint matrix upload");
             mats.push_back(dmats);
@@ -716,11 +716,11 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
     }
     float2 *psi = nullptr, *lam = nullptr;
     double *partial = nullptr, *rows = nullptr, *epart = nullptr;
-    cudaError_t e = cudaMalloc(&psi, N * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&lam, N * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&partial, std::max<size_t>(1, size_t(nrot) * ntiles) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t(nrot) + 1) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&epart, size_t(blocks) * sizeof(double));
+    cudaError_t e = dev_alloc(&psi, N * sizeof(float2));
+    if (e == cudaSuccess) e = dev_alloc(&lam, N * sizeof(float2));
+    if (e == cudaSuccess) e = dev_alloc(&partial, std::max<size_t>(1, size_t(nrot) * ntiles) * sizeof(double));
+    if (e == cudaSuccess) e = dev_alloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    if (e == cudaSuccess) e = dev_alloc(&epart, size_t(blocks) * sizeof(double));
     struct Guard {
         void *p[5];
         ~Guard() {

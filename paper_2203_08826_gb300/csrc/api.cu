@@ -26,6 +26,29 @@ int set_error(int code, const char *fmt, ...) {
     return code;
 }
 
+// ------------------------------------------------------------------ allocation
+// Injected allocation failures (test support): after `g_alloc_skip` more
+// successful device allocations, the next `g_alloc_fail` ones fail as if the
+// device were out of memory.
+static std::mutex g_alloc_mu;
+static int g_alloc_skip = 0, g_alloc_fail = 0;
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        if (g_alloc_fail > 0) {
+            if (g_alloc_skip > 0) {
+                --g_alloc_skip;
+            } else {
+                --g_alloc_fail;
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 int cuda_error(cudaError_t e, const char *what) {
     if (e == cudaErrorMemoryAllocation)
         return set_error(QSIM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
@@ -332,7 +355,7 @@ int qsim_state::ensure_scratch(size_t bytes) {
         scratch_bytes = 0;
     }
     const size_t want = std::max<size_t>(bytes, 1 << 20);
-    QSIM_CUDA_TRY(cudaMalloc(&scratch, want), "scratch allocation");
+    QSIM_CUDA_TRY(dev_alloc(&scratch, want), "scratch allocation");
     scratch_bytes = want;
     return QSIM_OK;
 }
@@ -358,7 +381,7 @@ int qsim_state_create(int n, int dtype, void *dev_ptr, void *cuda_stream, qsim_s
         s->amps = dev_ptr;
         s->owned = false;
     } else {
-        cudaError_t e = cudaMalloc(&s->amps, s->size() * s->amp_bytes());
+        cudaError_t e = dev_alloc(&s->amps, s->size() * s->amp_bytes());
         if (e != cudaSuccess) {
             delete s;
             return cuda_error(e, "state allocation");
@@ -662,7 +685,7 @@ int qsim_sample_probs(const double *p_dev, uint64_t N, uint64_t nshots, uint64_t
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t nsc = sample_scratch_u64(N) + sample_offsets_u64(N);
     uint64_t *scratch = nullptr;
-    QSIM_CUDA_TRY(cudaMalloc(&scratch, (nsc + 8 + (out_on_device ? 0 : nshots)) * sizeof(uint64_t)),
+    QSIM_CUDA_TRY(dev_alloc(&scratch, (nsc + 8 + (out_on_device ? 0 : nshots)) * sizeof(uint64_t)),
                   "sampler scratch");
     int rc = sample_common(p_dev, SRC_PROBS, N, nshots, seed, counter0, out, out_on_device, st, scratch);
     cudaStreamSynchronize(st);
@@ -711,3 +734,11 @@ int qsim_profile_get(int i, const char **name, uint64_t *launches, double *total
 uint64_t qsim_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
+
+extern "C" QSIM_API int qsim_debug_fail_alloc(int skip, int count) {
+    if (skip < 0 || count < 0) return qsim::set_error(QSIM_EINVAL, "skip and count must be >= 0");
+    std::lock_guard<std::mutex> lk(qsim::g_alloc_mu);
+    qsim::g_alloc_skip = skip;
+    qsim::g_alloc_fail = count;
+    return QSIM_OK;
+}

@@ -307,7 +307,7 @@ int pack(qsim_batch &b, int W) {
     auto up = [](auto &vec, auto **dst, const char *what) -> int {
         using T = typename std::remove_reference<decltype(vec)>::type::value_type;
         const size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(T);
-        QSIM_CUDA_TRY(cudaMalloc(reinterpret_cast<void **>(dst), bytes), what);
+        QSIM_CUDA_TRY(dev_alloc(reinterpret_cast<void **>(dst), bytes), what);
         if (!vec.empty()) QSIM_CUDA_TRY(cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice), what);
         return QSIM_OK;
     };
@@ -351,7 +351,7 @@ int launch_batch(qsim_batch &b, double *out, cudaStream_t st, int ctas_per_sm) {
             cudaFree(b.d_slots);
             b.d_slots = nullptr;
         }
-        QSIM_CUDA_TRY(cudaMalloc(&b.d_slots, grid * slot_amps * sizeof(float2)), "batch slots");
+        QSIM_CUDA_TRY(dev_alloc(&b.d_slots, grid * slot_amps * sizeof(float2)), "batch slots");
         b.slot_ctas = grid;
     }
     BatchParams bp{};
@@ -416,9 +416,9 @@ int qsim_batch_create(int ncircuits, const qsim_circuit *const *circuits, qsim_b
         const double cy = double(uint64_t(1) << b->circuits[y].n) * double(b->circuits[y].gates.size());
         return cx > cy;
     });
-    cudaError_t e = cudaMalloc(&b->d_order, sizeof(int) * ncircuits);
+    cudaError_t e = dev_alloc(&b->d_order, sizeof(int) * ncircuits);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * ncircuits, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_counter, sizeof(int));
     if (e != cudaSuccess) {
         delete b;
         return cuda_error(e, "batch setup");
@@ -465,7 +465,7 @@ int qsim_batch_autotune(qsim_batch *b, void *cuda_stream, int reps, int *best_ti
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (reps < 1) reps = 2;
     if (!b->d_tune_out)
-        QSIM_CUDA_TRY(cudaMalloc(&b->d_tune_out, sizeof(double) * b->circuits.size()), "autotune buffer");
+        QSIM_CUDA_TRY(dev_alloc(&b->d_tune_out, sizeof(double) * b->circuits.size()), "autotune buffer");
     cudaEvent_t e0, e1;
     QSIM_CUDA_TRY(cudaEventCreate(&e0), "event");
     QSIM_CUDA_TRY(cudaEventCreate(&e1), "event");

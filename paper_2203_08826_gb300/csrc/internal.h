@@ -22,6 +22,12 @@ int cuda_error(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return ::qsim::cuda_error(e_, what);  \
     } while (0)
+// Every device allocation of the library goes through here, so that a test can
+// make chosen allocations fail (qsim_debug_fail_alloc) without a GPU fault.
+cudaError_t dev_alloc(void **p, size_t bytes);
+template <typename T> inline cudaError_t dev_alloc(T **p, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
 #define QSIM_TRY(call)                 \
     do {                               \
         int rc_ = (call);              \

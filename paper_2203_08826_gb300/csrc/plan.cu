@@ -149,7 +149,7 @@ static int prepare_ops(qsim_plan &p, int dtype, cudaStream_t st) {
         dv.mat_off.push_back(off);
     }
     if (!host.empty()) {
-        QSIM_CUDA_TRY(cudaMalloc(&dv.mats, host.size()), "plan matrices");
+        QSIM_CUDA_TRY(dev_alloc(&dv.mats, host.size()), "plan matrices");
         QSIM_CUDA_TRY(cudaMemcpyAsync(dv.mats, host.data(), host.size(), cudaMemcpyHostToDevice, st),
                       "plan matrices upload");
         QSIM_CUDA_TRY(cudaStreamSynchronize(st), "plan upload sync");
@@ -284,7 +284,7 @@ static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double 
     const size_t bytes = s->size() * s->amp_bytes();
     void *ref = nullptr;
     bool have_ref = false;
-    if (measure && cudaMalloc(&ref, bytes) != cudaSuccess) {
+    if (measure && dev_alloc(&ref, bytes) != cudaSuccess) {
         cudaGetLastError();  // not enough memory for the reference copy: errors are not measured
         ref = nullptr;
     }

@@ -676,7 +676,7 @@ int run_host(const qsim_slice_plan &P, int dtype, void *const *slices, cudaStrea
     for (const Pass &ps : passes) maxm = std::max(maxm, __builtin_popcount(ps.gmask));
     const size_t nslots = size_t(2) << maxm;
     DevBuf buf;
-    QSIM_CUDA_TRY(cudaMalloc(&buf.p, nslots * slice_bytes), "slice staging");
+    QSIM_CUDA_TRY(dev_alloc(&buf.p, nslots * slice_bytes), "slice staging");
     char *stage = static_cast<char *>(buf.p);
     Streams ss;
     for (cudaStream_t *x : {&ss.up, &ss.comp, &ss.down})

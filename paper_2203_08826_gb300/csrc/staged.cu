@@ -576,7 +576,7 @@ static int prepare_staged(qsim_plan &p, int dtype) {
                     memcpy(&buf[e * eb], v, 16);
                 }
             }
-            QSIM_CUDA_TRY(cudaMalloc(&d.plain_mats[i], buf.size()), "stage plain matrix");
+            QSIM_CUDA_TRY(dev_alloc(&d.plain_mats[i], buf.size()), "stage plain matrix");
             QSIM_CUDA_TRY(cudaMemcpy(d.plain_mats[i], buf.data(), buf.size(), cudaMemcpyHostToDevice),
                           "stage plain matrix upload");
             continue;

@@ -9,6 +9,7 @@
 // amplitudes of a group form 2^k separate contiguous streams.
 #include <cuComplex.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace qsim {
@@ -99,6 +100,85 @@ __global__ void __launch_bounds__(256) k_dense1(typename CT<R>::T *__restrict__ 
         o0 = cfma(m.m01, b[j], o0);
         C o1 = cmul(m.m10, a[j]);
         o1 = cfma(m.m11, b[j], o1);
+        psi[idx[j]] = o0;
+        psi[idx[j] + stride] = o1;
+    }
+}
+
+// Complex128 form of the same update, mostly on the FP32 pipes: each double
+// of a and b is split into a float pair, the four outputs are compensated dot
+// products (double-float, about 48 bits), and the results are rounded back
+// to doubles.  A pair with an element outside the float pair's range takes
+// the FP64 formula instead (a warp-divergent branch that exact or near-zero
+// amplitudes never take; zero is in range), and so do the pairs of the first
+// DF_FP64_WARPS warps of each CTA, which keeps the FP64 pipe busy alongside.
+// Warps 0 .. DF_FP64_WARPS - 1 of every 8 compute their pairs in FP64, the
+// others in double-float: the FP64 pipe and the FP32/integer pipes then work
+// side by side.  Measured on the 30-qubit random circuit (dense 1-qubit
+// sweeps, complex128): 0 -> 7.98 ms, 2 -> 6.63 ms, 3 -> 6.22 ms (5.5 TB/s),
+// 4 -> 8.19 ms per sweep (the FP64 pipe becomes the limit).
+constexpr int DF_FP64_WARPS = 3;
+
+struct DfMat2 {
+    float v[16];  // m00, m01, m10, m11: (re.hi, re.lo, im.hi, im.lo)
+};
+
+// y = mA * a + mB * b (complex), every part a float pair
+__device__ __forceinline__ void df_row(const float *mA, const float *mB, const float (&a)[4], const float (&b)[4],
+                                       double &yr, double &yi) {
+    // a = (re.hi, re.lo, im.hi, im.lo)
+    dfl::Dot re, im;
+    re.first(mA[0], mA[1], a[0], a[1]);
+    re.add(-mA[2], -mA[3], a[2], a[3]);
+    re.add(mB[0], mB[1], b[0], b[1]);
+    re.add(-mB[2], -mB[3], b[2], b[3]);
+    im.first(mA[0], mA[1], a[2], a[3]);
+    im.add(mA[2], mA[3], a[0], a[1]);
+    im.add(mB[0], mB[1], b[2], b[3]);
+    im.add(mB[2], mB[3], b[0], b[1]);
+    float h, l;
+    re.result(h, l);
+    yr = dfl::join(h, l);
+    im.result(h, l);
+    yi = dfl::join(h, l);
+}
+
+template <int PER>
+__global__ void __launch_bounds__(256) k_dense1_df(double2 *__restrict__ psi, uint64_t npairs,
+                                                   const __grid_constant__ IndexMap map, uint64_t stride,
+                                                   const __grid_constant__ DfMat2 m, Mat2<double> md, int fp64_warps) {
+    const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
+    const bool use64 = int(threadIdx.x >> 5) < fp64_warps;  // warp-uniform
+    double2 a[PER], b[PER];
+    uint64_t idx[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t g = base + uint64_t(j) * blockDim.x;
+        idx[j] = g < npairs ? expand_index(g, map) : ~uint64_t(0);
+        if (g < npairs) {
+            a[j] = psi[idx[j]];
+            b[j] = psi[idx[j] + stride];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (idx[j] == ~uint64_t(0)) continue;
+        float fa[4], fb[4];
+        bool ok = !use64;
+        if (ok) {
+            ok &= dfl::split(a[j].x, fa[0], fa[1]);
+            ok &= dfl::split(a[j].y, fa[2], fa[3]);
+            ok &= dfl::split(b[j].x, fb[0], fb[1]);
+            ok &= dfl::split(b[j].y, fb[2], fb[3]);
+        }
+        double2 o0, o1;
+        if (ok) {
+            df_row(m.v + 0, m.v + 4, fa, fb, o0.x, o0.y);
+            df_row(m.v + 8, m.v + 12, fa, fb, o1.x, o1.y);
+        } else {
+            o0 = cfma(md.m01, b[j], cmul(md.m00, a[j]));
+            o1 = cfma(md.m11, b[j], cmul(md.m10, a[j]));
+        }
         psi[idx[j]] = o0;
         psi[idx[j] + stride] = o1;
     }
@@ -244,6 +324,82 @@ __global__ void __launch_bounds__(256) k_diag(typename CT<R>::T *__restrict__ ps
     }
 }
 
+// Complex128 diagonal on the FP32 pipes: psi[x] *= d[j(x)] as a
+// double-float product (two compensated two-term dot products per
+// amplitude), FP64 for an amplitude outside the float pair's range.
+template <int PER>
+__global__ void __launch_bounds__(256) k_diag_df(double2 *__restrict__ psi, uint64_t count,
+                                                 const __grid_constant__ IndexMap map,
+                                                 const __grid_constant__ DiagParams<double> p) {
+    const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
+    double2 a[PER];
+    uint64_t idx[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t g = base + uint64_t(j) * blockDim.x;
+        idx[j] = g < count ? expand_index(g, map) : ~uint64_t(0);
+        if (g < count) a[j] = psi[idx[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (idx[j] == ~uint64_t(0)) continue;
+        int sel = 0;
+        for (int i = 0; i < p.k; ++i) sel = (sel << 1) | int((idx[j] >> p.tbits[i]) & 1);
+        const double2 d = p.d[sel];
+        float x[4], dd[4];
+        bool ok = dfl::split(a[j].x, x[0], x[1]);
+        ok &= dfl::split(a[j].y, x[2], x[3]);
+        ok &= dfl::split(d.x, dd[0], dd[1]);
+        ok &= dfl::split(d.y, dd[2], dd[3]);
+        double2 o;
+        if (ok) {
+            dfl::Dot re, im;
+            re.first(dd[0], dd[1], x[0], x[1]);
+            re.add(-dd[2], -dd[3], x[2], x[3]);
+            im.first(dd[0], dd[1], x[2], x[3]);
+            im.add(dd[2], dd[3], x[0], x[1]);
+            float h, l;
+            re.result(h, l);
+            o.x = dfl::join(h, l);
+            im.result(h, l);
+            o.y = dfl::join(h, l);
+        } else {
+            o = cmul(d, a[j]);
+        }
+        psi[idx[j]] = o;
+    }
+}
+
+// Diagonal whose entries are all +1 or -1 (CZ, Z, controlled Z): the sign
+// bits of the selected amplitudes flip; no arithmetic, exact in any precision.
+template <typename R, int PER>
+__global__ void __launch_bounds__(256) k_diag_sign(typename CT<R>::T *__restrict__ psi, uint64_t count,
+                                                   const __grid_constant__ IndexMap map, int k, uint64_t neg_table, int nt0, int nt1, int nt2, int nt3, int nt4,
+                                                   int nt5) {
+    using C = typename CT<R>::T;
+    const int tb[6] = {nt0, nt1, nt2, nt3, nt4, nt5};
+    const uint64_t base = uint64_t(blockIdx.x) * (blockDim.x * PER) + threadIdx.x;
+    C a[PER];
+    uint64_t idx[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t g = base + uint64_t(j) * blockDim.x;
+        idx[j] = g < count ? expand_index(g, map) : ~uint64_t(0);
+        if (g < count) a[j] = psi[idx[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        if (idx[j] == ~uint64_t(0)) continue;
+        int sel = 0;
+        for (int i = 0; i < k; ++i) sel = (sel << 1) | int((idx[j] >> tb[i]) & 1);
+        if ((neg_table >> sel) & 1) {
+            a[j].x = -a[j].x;
+            a[j].y = -a[j].y;
+            psi[idx[j]] = a[j];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ monomial
 // Permutation with phases (X, Y, SWAP, ...): only the rows that change are
 // loaded and stored: out[dst_a] = ph_a * in[src_a].
@@ -256,7 +412,8 @@ template <typename R> struct MonoParams {
 
 // NA rows move per group; each thread takes PER groups (loads first, then
 // stores) so that several loads per thread are in flight.
-template <typename R, int NA, int PER>
+// UNIT: every phase is exactly 1 (X, SWAP, CNOT): a pure move, no arithmetic.
+template <typename R, int NA, int PER, bool UNIT>
 __global__ void __launch_bounds__(256) k_mono(typename CT<R>::T *__restrict__ psi, uint64_t ngroups,
                                               const __grid_constant__ IndexMap map,
                                               const __grid_constant__ MonoParams<R> p) {
@@ -279,7 +436,7 @@ __global__ void __launch_bounds__(256) k_mono(typename CT<R>::T *__restrict__ ps
         if (x[j] == ~uint64_t(0)) continue;
 #pragma unroll
         for (int a = 0; a < NA; ++a)
-            if (a < p.na) psi[x[j] | p.dst[a]] = cmul(p.ph[a], v[j][a]);
+            if (a < p.na) psi[x[j] | p.dst[a]] = UNIT ? v[j][a] : cmul(p.ph[a], v[j][a]);
     }
 }
 
@@ -289,6 +446,13 @@ template <typename R> static typename CT<R>::T to_c(const cd &z) {
     r.x = R(z.real());
     r.y = R(z.imag());
     return r;
+}
+
+// hi + lo with hi = x rounded to float and lo = x - hi rounded to float
+// (host; the matrix entries of the double-float sweeps)
+static void df_parts(double x, float &hi, float &lo) {
+    hi = float(x);
+    lo = float(x - double(hi));
 }
 
 static uint64_t target_offset(int j, const int *targets, int k) {
@@ -316,8 +480,20 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 constexpr int PER = 4, T = 256;
                 const uint64_t blocks = (ngroups + T * PER - 1) / (T * PER);
                 LaunchScope ls(K_DENSE1, st, bytes, 16.0 * double(ngroups << 1));
-                k_dense1<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, ngroups, map,
-                                                                  uint64_t(1) << op.targets[0], m);
+                if constexpr (sizeof(R) == 8) {
+                    constexpr int PD = 2;
+                    DfMat2 dm{};
+                    for (int e = 0; e < 4; ++e) {
+                        df_parts(op.m[size_t(e)].real(), dm.v[4 * e], dm.v[4 * e + 1]);
+                        df_parts(op.m[size_t(e)].imag(), dm.v[4 * e + 2], dm.v[4 * e + 3]);
+                    }
+                    k_dense1_df<PD><<<unsigned((ngroups + T * PD - 1) / (T * PD)), T, 0, st>>>(
+                        reinterpret_cast<double2 *>(psi), ngroups, map, uint64_t(1) << op.targets[0], dm, m,
+                        DF_FP64_WARPS);
+                } else {
+                    k_dense1<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, ngroups, map,
+                                                                      uint64_t(1) << op.targets[0], m);
+                }
             } else if (k <= 3) {
                 constexpr int T = 256;
                 const double flops = 8.0 * double(1 << k) * double(ngroups << k);
@@ -386,8 +562,31 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
             for (int j = 0; j < (1 << k); ++j) p.d[j] = to_c<R>(op.m[j]);
             constexpr int PER = 4, T = 256;
             const uint64_t blocks = (count + T * PER - 1) / (T * PER);
+            bool signs = true;  // every entry exactly +1 or -1
+            uint64_t neg = 0;
+            for (int j = 0; j < (1 << k); ++j) {
+                if (op.m[j] == cd(-1.0)) neg |= uint64_t(1) << j;
+                else if (op.m[j] != cd(1.0)) signs = false;
+            }
+            if (signs) {
+                // only the flipped amplitudes are written: bytes read S * count,
+                // written S * (flipped share of count)
+                const double flipped = double(__builtin_popcountll(neg)) / double(1 << k);
+                LaunchScope ls(K_DIAG, st, S * double(count) * (1.0 + flipped));
+                int tb[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = 0; i < k; ++i) tb[i] = op.targets[i];
+                k_diag_sign<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, count, map, k, neg, tb[0], tb[1], tb[2],
+                                                                    tb[3], tb[4], tb[5]);
+                break;
+            }
             LaunchScope ls(K_DIAG, st, 2.0 * S * double(count), 6.0 * double(count));
-            k_diag<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, count, map, p);
+            if constexpr (sizeof(R) == 8) {
+                constexpr int PD = 2;
+                k_diag_df<PD><<<unsigned((count + T * PD - 1) / (T * PD)), T, 0, st>>>(
+                    reinterpret_cast<double2 *>(psi), count, map, p);
+            } else {
+                k_diag<R, PER><<<unsigned(blocks), T, 0, st>>>(psi, count, map, p);
+            }
             break;
         }
         case Op::MONO: {
@@ -402,12 +601,16 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
                 ++p.na;
             }
             const int T = 256;
+            bool unit = true;  // no phase to apply: the moved amplitudes are copied exactly
+            for (int r = 0; r < (1 << k); ++r) unit &= op.phase[r] == cd(1.0);
             LaunchScope ls(K_MONO, st, 2.0 * S * double(ngroups) * p.na);
+            const unsigned b4 = unsigned((ngroups + T * 4 - 1) / (T * 4)), b1 = unsigned((ngroups + T - 1) / T);
             if (p.na <= 2) {
-                constexpr int PER = 4;
-                k_mono<R, 2, PER><<<unsigned((ngroups + T * PER - 1) / (T * PER)), T, 0, st>>>(psi, ngroups, map, p);
+                if (unit) k_mono<R, 2, 4, true><<<b4, T, 0, st>>>(psi, ngroups, map, p);
+                else k_mono<R, 2, 4, false><<<b4, T, 0, st>>>(psi, ngroups, map, p);
             } else {
-                k_mono<R, 8, 1><<<unsigned((ngroups + T - 1) / T), T, 0, st>>>(psi, ngroups, map, p);
+                if (unit) k_mono<R, 8, 1, true><<<b1, T, 0, st>>>(psi, ngroups, map, p);
+                else k_mono<R, 8, 1, false><<<b1, T, 0, st>>>(psi, ngroups, map, p);
             }
             break;
         }

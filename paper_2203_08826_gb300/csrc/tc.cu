@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -65,6 +66,7 @@ struct TcParams {
     float2 *out;
     const uint4 *bimg;   // shared-memory image of B_hi then B_lo
     int *err;            // set to 1 when a bounded wait expires
+    unsigned long long wait_limit;  // polls of a pipeline wait before it gives up
     uint64_t ntiles;     // 2^(n-k) / 128
     int n;
     int nepi;               // phase ops (evaluated per element)
@@ -121,12 +123,19 @@ template <> struct Elem<TC_BF16X3> {
         lo = __bfloat16_as_ushort(l);
     }
 };
+// Round a float to the nearest tf32 value (10 fraction bits; ties away from
+// zero in magnitude): add half of the dropped range to the magnitude bits,
+// then clear them.  The tensor cores read only the top 19 bits of a tf32
+// operand, so a part given with more bits would be truncated toward zero;
+// rounding both parts here keeps the split unbiased.
+__host__ __device__ inline uint32_t tf32_rn(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
+
 template <> struct Elem<TC_TF32X3> {
     static constexpr int EB = 4;
     __device__ static void split(float a, uint32_t &hi, uint32_t &lo) {
-        const uint32_t h = __float_as_uint(a) & 0xFFFFE000u;  // exactly representable in tf32
+        const uint32_t h = tf32_rn(__float_as_uint(a));
         hi = h;
-        lo = __float_as_uint(a - __uint_as_float(h));
+        lo = tf32_rn(__float_as_uint(a - __uint_as_float(h)));  // a - hi is exact in fp32
     }
 };
 
@@ -166,8 +175,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 // Bounded wait that also gives up as soon as another role has given up
 // (*abort set); on its own expiry it sets *abort.
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int *abort) {
-    for (unsigned long long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t mbar, uint32_t parity, volatile int *abort,
+                                             unsigned long long limit) {
+    for (unsigned long long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -189,8 +199,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 // Every lane of a warp waits; the warp goes on only if all lanes saw the
 // phase complete, so its lanes never leave a loop in different iterations.
-__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
-    const bool ok = mbar_wait_ab(mbar, parity, abort);
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, volatile int *abort,
+                                          unsigned long long limit) {
+    const bool ok = mbar_wait_ab(mbar, parity, abort, limit);
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constan
             const int st = int(i & 1);
             const uint32_t u = uint32_t(i >> 1);
             const bool more = i + 1 < my_tiles;
-            if (i >= 2 && !warp_wait(empty_a0 + 8 * st, (u - 1) & 1, abort_f)) break;
+            if (i >= 2 && !warp_wait(empty_a0 + 8 * st, (u - 1) & 1, abort_f, p.wait_limit)) break;
             convert_half(v0, st, 0);
             if (more) load_half(v0, i + 1, 0);
             convert_half(v1, st, 1);
@@ -328,8 +339,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constan
             for (uint64_t i = 0; i < my_tiles; ++i) {
                 const int st = int(i & 1);
                 const uint32_t u = uint32_t(i >> 1);
-                if (!mbar_wait_ab(full_a0 + 8 * st, u & 1, abort_f)) break;
-                if (i >= 2 && !mbar_wait_ab(empty_acc0 + 8 * st, (u - 1) & 1, abort_f)) break;
+                if (!mbar_wait_ab(full_a0 + 8 * st, u & 1, abort_f, p.wait_limit)) break;
+                if (i >= 2 && !mbar_wait_ab(empty_acc0 + 8 * st, (u - 1) & 1, abort_f, p.wait_limit)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t ah = smem_u32(a_hi(st)), al = smem_u32(a_lo(st));
                 const uint32_t dacc = tmem + uint32_t(st * S::KR);
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constan
             const uint64_t tile = blockIdx.x + i * gridDim.x;
             const int st = int(i & 1);
             const uint32_t u = uint32_t(i >> 1);
-            if (!warp_wait(full_acc0 + 8 * st, u & 1, abort_f)) break;
+            if (!warp_wait(full_acc0 + 8 * st, u & 1, abort_f, p.wait_limit)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t R = tile * TC_M + m;  // row index = bits K.. of the current index
             const uint32_t trow = tmem + uint32_t(st * S::KR) + (uint32_t(warp * 32) << 16);
@@ -705,12 +716,15 @@ void build_bimage(const std::vector<cd> &G, int k, std::vector<unsigned char> &i
             } else {
                 uint32_t u;
                 memcpy(&u, &f, 4);
-                const uint32_t hu = u & 0xFFFFE000u;
+                const uint32_t hu = tf32_rn(u);
                 float hf;
                 memcpy(&hf, &hu, 4);
                 const float lf = f - hf;
+                uint32_t lu;
+                memcpy(&lu, &lf, 4);
+                lu = tf32_rn(lu);
                 memcpy(&img[off], &hu, 4);
-                memcpy(&img[opnd + off], &lf, 4);
+                memcpy(&img[opnd + off], &lu, 4);
             }
         }
 }
@@ -768,9 +782,9 @@ int prepare_tc(qsim_plan &p, int n) {
         }
         tp.dev.params.push_back(prm);
     }
-    QSIM_CUDA_TRY(cudaMalloc(&tp.dev.bimg, all.size()), "tc B images");
+    QSIM_CUDA_TRY(dev_alloc(&tp.dev.bimg, all.size()), "tc B images");
     QSIM_CUDA_TRY(cudaMemcpy(tp.dev.bimg, all.data(), all.size(), cudaMemcpyHostToDevice), "tc B upload");
-    QSIM_CUDA_TRY(cudaMalloc(&tp.dev.err, sizeof(int)), "tc error flag");
+    QSIM_CUDA_TRY(dev_alloc(&tp.dev.err, sizeof(int)), "tc error flag");
     QSIM_CUDA_TRY(cudaMemset(tp.dev.err, 0, sizeof(int)), "tc error flag clear");
     tp.dev.ready = true;
     return QSIM_OK;
@@ -799,6 +813,9 @@ int launch_tc_k(const TcParams &prm, cudaStream_t st) {
 
 }  // namespace
 
+// polls before a pipeline wait gives up (test support can shorten it)
+static std::atomic<unsigned long long> g_wait_limit{WAIT_LIMIT};
+
 int run_tc(qsim_state *s, qsim_plan &p) {
     if (s->dtype != QSIM_C64) return set_error(QSIM_EUNSUPPORTED, "tensor-core plans run complex64 states");
     QSIM_TRY(prepare_tc(p, s->n));
@@ -823,6 +840,7 @@ int run_tc(qsim_state *s, qsim_plan &p) {
         prm.out = bufs[cur ^ 1];
         prm.bimg = reinterpret_cast<const uint4 *>(static_cast<char *>(tp.dev.bimg) + tp.dev.boff[i]);
         prm.err = tp.dev.err;
+        prm.wait_limit = g_wait_limit.load();
         const int k = tp.passes[i].k;
         int rc;
         if (tp.prec == TC_BF16X3) rc = k == 6 ? launch_tc_k<6, TC_BF16X3>(prm, s->stream) : launch_tc_k<5, TC_BF16X3>(prm, s->stream);
@@ -942,4 +960,9 @@ QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int
 void qsim_plan::release_tc() {
     delete tc;
     tc = nullptr;
+}
+
+extern "C" QSIM_API int qsim_debug_set_wait_limit(unsigned long long polls) {
+    qsim::g_wait_limit.store(polls ? polls : qsim::WAIT_LIMIT);
+    return QSIM_OK;
 }

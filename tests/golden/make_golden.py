@@ -74,13 +74,13 @@ def make_random30():
                 "# norm2 <value>; zz <sum_i Z_i Z_i+1>; marginal_29_0 <p00 p01 p10 p11>;\n"
                 "# then 'amp <index> <re> <im>' at the seeded indices and 'top <index> <re> <im>' at the\n"
                 "# 64 indices of largest magnitude.\n")
-        f.write(f"norm2 {norm2!r}\n")
-        f.write(f"zz {zz!r}\n")
+        f.write(f"norm2 {float(norm2)!r}\n")
+        f.write(f"zz {float(zz)!r}\n")
         f.write("marginal_29_0 " + " ".join(repr(float(v)) for v in marg) + "\n")
         for i in idx:
-            f.write(f"amp {int(i)} {psi[i].real!r} {psi[i].imag!r}\n")
+            f.write(f"amp {int(i)} {float(psi[i].real)!r} {float(psi[i].imag)!r}\n")
         for i in top:
-            f.write(f"top {int(i)} {psi[i].real!r} {psi[i].imag!r}\n")
+            f.write(f"top {int(i)} {float(psi[i].real)!r} {float(psi[i].imag)!r}\n")
     print(f"wrote {RANDOM30} in {time.time() - t0:.0f} s")
 
 
@@ -96,10 +96,15 @@ def make_adjoint24():
                 "# ansatz (seed 5), parameter set 0 of default_rng(0).uniform(0, 2 pi, (64, 480)),\n"
                 "# H = sum_i (Z_i Z_i+1 + 0.5 X_i); energy, then 'grad <parameter> <value>' by the\n"
                 "# parameter-shift rule [E(theta + pi/2) - E(theta - pi/2)] / 2 in complex128.\n")
-        f.write(f"energy {e!r}\n")
+        f.write(f"energy {float(e)!r}\n")
         for p in ADJ_PARAMS:
-            f.write(f"grad {p} {g[p]!r}\n")
+            f.write(f"grad {p} {float(g[p])!r}\n")
     print(f"wrote {ADJOINT24} in {time.time() - t0:.0f} s")
+
+
+def _num(tok: str) -> str:
+    # values are written with repr(); numpy scalars print as np.float64(...)
+    return tok[len("np.float64("):-1] if tok.startswith("np.float64(") else tok
 
 
 def read(path: str) -> dict:
@@ -110,6 +115,7 @@ def read(path: str) -> dict:
             if line.startswith("#") or not line.strip():
                 continue
             key, *vals = line.split()
+            vals = [_num(v) for v in vals]
             if key in ("amp", "top"):
                 out[key].append((int(vals[0]), complex(float(vals[1]), float(vals[2]))))
             elif key == "grad":

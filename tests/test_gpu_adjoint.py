@@ -33,7 +33,9 @@ def mixed_ansatz(n, layers, seed):
     return inputs.Circuit(n, gates)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 2e-4)])
+# Tolerances: the measured errors against the oracle's parameter shift times
+# about 10 (complex64: <= 6.2e-7; complex128: <= 3e-14).
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 5e-6)])
 def test_adjoint_matches_parameter_shift(q, orc, dtype, tol):
     circ = mixed_ansatz(6, 3, seed=1)
     ham = inputs.tfim(6)
@@ -42,10 +44,11 @@ def test_adjoint_matches_parameter_shift(q, orc, dtype, tol):
     grads, en = q.adjoint_grad(circ, ham, thetas, dtype)
     for s in range(3):
         want = orc.parameter_shift_gradient(circ, ham, thetas[s])
+        print(f"adjoint mixed6 {dtype}: max gradient err {np.max(np.abs(grads[s] - want)):.3e}")
         np.testing.assert_allclose(grads[s], want, atol=tol)
         assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < tol
     fd = orc.finite_difference_gradient(circ, ham, thetas[0], h=1e-4)
-    np.testing.assert_allclose(grads[0], fd, atol=max(tol, 1e-6))
+    np.testing.assert_allclose(grads[0], fd, atol=max(tol, 1e-6))  # O(h^2) truncation of the differences
 
 
 def test_adjoint_variational_12q_all_parameters(q, orc):
@@ -55,8 +58,8 @@ def test_adjoint_variational_12q_all_parameters(q, orc):
     ham = inputs.tfim(12)
     th = circ.params()
     grads, en = q.adjoint_grad(circ, ham, th[None, :], "c128")
-    np.testing.assert_allclose(grads[0], orc.parameter_shift_gradient(circ, ham, th), atol=1e-10)
-    assert abs(en[0] - orc.energy(circ, ham, th)) < 1e-10
+    np.testing.assert_allclose(grads[0], orc.parameter_shift_gradient(circ, ham, th), atol=1e-12)
+    assert abs(en[0] - orc.energy(circ, ham, th)) < 1e-12
 
 
 def test_autograd_function(q, orc):
@@ -69,7 +72,7 @@ def test_autograd_function(q, orc):
     (2.0 * e[0] + 3.0 * e[1]).backward()
     g0 = orc.parameter_shift_gradient(circ, ham, circ.params())
     g1 = orc.parameter_shift_gradient(circ, ham, circ.params() + 0.1)
-    np.testing.assert_allclose(theta.grad.numpy(), np.stack([2 * g0, 3 * g1]), atol=1e-10)
+    np.testing.assert_allclose(theta.grad.numpy(), np.stack([2 * g0, 3 * g1]), atol=1e-12)
 
 
 def test_adjoint_24q_config_properties(q):
@@ -81,8 +84,8 @@ def test_adjoint_24q_config_properties(q):
     th = circ.params()
     g64, e64 = q.adjoint_grad(circ, ham, th[None, :], "c64")
     g128, e128 = q.adjoint_grad(circ, ham, th[None, :], "c128")
-    assert abs(e64[0] - e128[0]) < 1e-4
-    np.testing.assert_allclose(g64[0], g128[0], atol=2e-3)
+    assert abs(e64[0] - e128[0]) < 5e-6
+    np.testing.assert_allclose(g64[0], g128[0], atol=5e-6)
     h = 1e-4
     for p_ in (0, 237, 479):
         tp, tm = th.copy(), th.copy()
@@ -130,12 +133,14 @@ def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker):
     g128, e128 = q.adjoint_grad(circ, ham, thetas, "c128")   # the plain sweeps path
     for s in range(2):
         want = orc.parameter_shift_gradient(circ, ham, thetas[s])
-        np.testing.assert_allclose(grads[s], want, atol=2e-4)
-        np.testing.assert_allclose(g128[s], want, atol=1e-10)
-        assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < 2e-4
+        print(f"adjoint fused {maker}: max gradient err {np.max(np.abs(grads[s] - want)):.3e}, "
+              f"energy err {abs(en[s] - orc.energy(circ, ham, thetas[s])):.3e}")
+        np.testing.assert_allclose(grads[s], want, atol=4e-6)  # measured <= 4.1e-7
+        np.testing.assert_allclose(g128[s], want, atol=1e-12)
+        assert abs(en[s] - orc.energy(circ, ham, thetas[s])) < 4e-6
 
 
-@pytest.mark.parametrize("dtype,tol", [("c64", 2e-4), ("c128", 1e-10)])
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-6), ("c128", 1e-12)])  # measured 2.1e-7 / 1.8e-14
 def test_adjoint_general_pauli_hamiltonian(q, orc, dtype, tol):
     """A Hamiltonian of mixed Pauli strings on 14 qubits: X masks inside the
     low 12 qubits, across qubits 0..4 and the top chunk, and across both
@@ -157,11 +162,12 @@ def test_adjoint_general_pauli_hamiltonian(q, orc, dtype, tol):
     th = np.random.default_rng(13).uniform(0, 2 * np.pi, size=(1, circ.nparams))
     grads, en = q.adjoint_grad(circ, ham, th, dtype)
     want = orc.parameter_shift_gradient(circ, ham, th[0])
+    print(f"adjoint general-pauli {dtype}: max gradient err {np.max(np.abs(grads[0] - want)):.3e}")
     np.testing.assert_allclose(grads[0], want, atol=tol)
     assert abs(en[0] - orc.energy(circ, ham, th[0])) < tol
 
 
-@pytest.mark.parametrize("n,dtype,tol", [(6, "c128", 1e-10), (6, "c64", 2e-5), (13, "c64", 2e-5)])
+@pytest.mark.parametrize("n,dtype,tol", [(6, "c128", 1e-12), (6, "c64", 2e-6), (13, "c64", 2e-6)])
 def test_adjoint_from_a_start_state(q, orc, n, dtype, tol):
     """Gradients of <psi0|U^dag H U|psi0> from a seeded Gaussian start state
     (one sweep per gate below 12 qubits, two-state register stages for
@@ -176,6 +182,7 @@ def test_adjoint_from_a_start_state(q, orc, n, dtype, tol):
     grads, en = q.adjoint_grad(circ, ham, th, dtype, psi0=s0)
     for s in range(2):
         want = orc.parameter_shift_gradient(circ, ham, th[s], psi0=psi0_used)
+        print(f"adjoint psi0 n={n} {dtype}: max gradient err {np.max(np.abs(grads[s] - want)):.3e}")
         np.testing.assert_allclose(grads[s], want, atol=tol)
         assert abs(en[s] - orc.energy(circ, ham, th[s], psi0_used)) < tol
     g_zero, _ = q.adjoint_grad(circ, ham, th[:1], dtype)
@@ -184,7 +191,7 @@ def test_adjoint_from_a_start_state(q, orc, n, dtype, tol):
     np.testing.assert_array_equal(s0.to_host().astype(np.complex128), psi0_used)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c64", 2e-3), ("c128", 1e-9)])
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-6), ("c128", 1e-11)])  # measured 2.5e-7 / 6.4e-13
 def test_adjoint_24q_config_against_oracle(q, dtype, tol):
     """The gradient workload's own configuration (24 qubits, 10 layers, 480
     parameters, H = sum(Z_i Z_i+1 + 0.5 X_i), parameter set 0 of the seeded

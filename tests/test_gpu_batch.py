@@ -94,4 +94,4 @@ def test_full_size_batch_wide_circuits_against_oracle(q, orc):
         want = oracle_zz(orc, circs[i])
         err = abs(got[i] - want)
         print(f"batch circuit {i}: n={circs[i].n} layers={len(circs[i].gates)} |err| {err:.3e}")
-        assert err < 2e-5 * circs[i].n, (i, got[i], want)
+        assert err < 3e-6, (i, got[i], want)  # measured <= 3.0e-7

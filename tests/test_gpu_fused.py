@@ -126,9 +126,11 @@ def test_tensor_core_blocks_match_oracle(q, orc, kmax, maker):
     got = run_plan(q, circ, "c64", psi0, q.FUSE_TC, kmax)
     err = np.max(np.abs(got - want))
     rel = err / np.max(np.abs(want))
+    print(f"tc {maker} kmax={kmax}: max-abs {err:.3e} relative {rel:.3e}")
     assert err <= 1e-5, f"tc {maker} kmax={kmax}: max-abs {err:.3e} (relative {rel:.3e})"
-    # the split keeps ~16 (BF16x3) or ~21 (3xTF32) bits per operand
-    assert rel <= (2e-4 if kmax == 6 else 2e-5), f"relative error {rel:.3e}"
+    # the split keeps ~16 (BF16x3) or ~21 (3xTF32) bits per operand; measured
+    # relative errors <= 1.5e-5 (BF16x3) and 5.4e-6 (3xTF32), bounds about 3x that
+    assert rel <= (5e-5 if kmax == 6 else 1.5e-5), f"relative error {rel:.3e}"
 
 
 def test_tensor_core_rejects_complex128(q):

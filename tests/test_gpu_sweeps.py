@@ -295,3 +295,42 @@ def test_sampler_prefix_over_several_scan_tiles(q, orc):
     p /= p.sum()
     got = binding.sample_probs(torch.from_numpy(p).cuda(), 6000, seed=123, counter0=9)
     np.testing.assert_array_equal(got, orc.sample(p, 6000, seed=123, counter0=9))
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-21, 1e-30, 1e30, "mixed"])
+def test_complex128_double_float_range(q, orc, scale):
+    """complex128 dense 1-qubit and diagonal sweeps run in double-float
+    arithmetic on the FP32 pipes; amplitudes outside [2^-74, 2^77) take the
+    FP64 formula per pair.  States scaled into and beyond that range (and a
+    state mixing normal, tiny, subnormal and zero amplitudes within one warp)
+    against the oracle, relative to the scale, at the complex128 bound; CZ
+    and Z (sign flips) are exact."""
+    n = 11
+    rng = np.random.default_rng(77)
+    psi0 = inputs.gaussian_state(n, seed=78)
+    if scale == "mixed":
+        psi0 = psi0.copy()
+        psi0[::3] *= 1e-30
+        psi0[1::7] = 0.0
+        psi0[2::11] *= 1e-310  # subnormal doubles
+        ref_scale = float(np.max(np.abs(psi0)))
+    else:
+        psi0 = psi0 * scale
+        ref_scale = scale
+    s = new_state(q, n, "c128", psi0)
+    ref = psi0.copy()
+    gates = []
+    for _ in range(6):
+        for t in range(n):
+            gates.append(inputs.Gate("su2", (t,), (), inputs.haar_su2_quaternion(rng)))
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        gates.append(inputs.Gate("cz", (a, b)))
+        gates.append(inputs.Gate("z", (int(rng.integers(n)),)))
+        gates.append(inputs.Gate("phase", (a,), (b,), (float(rng.uniform(0, 6.28)),)))
+        gates.append(inputs.Gate("rz", (int(rng.integers(n)),), (), (float(rng.uniform(0, 6.28)),)))
+        gates.append(inputs.Gate("h", (b,), (a,)))  # controlled H
+    for g in gates:
+        s.apply(g)
+        orc.apply_gate(ref, g)
+    err = np.max(np.abs(s.to_host() - ref)) / ref_scale
+    assert err <= 1e-12, f"scale {scale}: max-abs error / scale {err:.3e}"
