@@ -228,6 +228,20 @@ QSIM_API int qsim_plan_tc_pass(const qsim_plan *p, int i, int *plain, int *k, in
  * its 2^k diagonal entries (complex128, interleaved).  Host-only. */
 QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int *targets, int *nc, int *controls,
                                    double *diag);
+/* Arithmetic of each pass of a QSIM_FUSE_TC plan (mixed-precision refinement
+ * of the fused blocks): BF16x3 or 3xTF32 split products on the tensor cores,
+ * or the same contraction in FP32 on the CUDA cores (slower, no split error).
+ * A plan starts with every pass at its window width's split (BF16x3 for
+ * kmax >= 6, 3xTF32 for kmax 5); 3xTF32 needs a 5-qubit window.  set takes
+ * one value per pass (npasses = the plan's sweeps; plain passes ignore
+ * theirs) and QSIM_EINVAL for a bad value; host-only, the next run rebuilds
+ * the device images.  Citation: Sec. 3.2 (fusion into blocks of a few qubits);
+ * the precision choice itself has no counterpart in the paper. */
+#define QSIM_PREC_BF16X3 0
+#define QSIM_PREC_TF32X3 1
+#define QSIM_PREC_FP32 2
+QSIM_API int qsim_plan_tc_precision(const qsim_plan *p, int i, int *prec);
+QSIM_API int qsim_plan_tc_set_precision(qsim_plan *p, int npasses, const int *prec);
 /* Stage i of a QSIM_FUSE_STAGED plan (0 <= i < nsweeps; host-only, for
  * checking the planner): *plain = 1 for a gate applied by a plain sweep;
  * otherwise the tile's qubits beyond the lanes (nslots of them, in slot
@@ -249,24 +263,34 @@ QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, int *ngates,
 QSIM_API int qsim_plan_autotune(const qsim_circuit *c, qsim_state *s, int reps, qsim_plan **out, int *mode_out,
                                 int *kmax_out, double *ms_out);
 /* Autotuner with a measured error/speed table (mixed-precision refinement of
- * the fused blocks: FP32 register stages vs BF16x3 vs 3xTF32 tensor-core
- * blocks).  Every candidate runs from |0...0> once; its error is the
- * difference of that result from the first candidate's (the FP32 staged
- * plan, kmax 3): err = ||psi - psi_ref||_2 (relative to ||psi|| = 1) and
- * max_abs = max_x |psi(x) - psi_ref(x)|.  The fastest candidate with
- * err <= max_err is kept (max_err <= 0: no bound, and errors are measured only
- * when table_cap > 0).  Errors need one extra state-sized device buffer; when
- * it cannot be allocated they are reported as -1, and with max_err > 0 no
- * candidate qualifies (QSIM_EUNSUPPORTED).  The reference is the first
- * candidate that runs.  table
+ * the fused blocks).  Candidates for complex64: FP32 register stages (kmax 3
+ * and 4), tensor-core plans with every pass in BF16x3 (6-qubit windows),
+ * 3xTF32 (5-qubit windows) or FP32 on the CUDA cores (6-qubit windows), and a
+ * mixed plan chosen per block: when the BF16x3 plan misses max_err and the
+ * FP32 one meets it, the per-pass errors measured for the two (plan error /
+ * passes) give the fewest passes that must run in FP32 for the predicted
+ * error (summed over passes) to stay within max_err; that plan runs as one
+ * more candidate.  complex128: stages against one sweep per gate.  Every
+ * candidate runs from |0...0> once; its error is err = ||psi - psi_ref||_2
+ * (relative to ||psi|| = 1) and max_abs = max_x |psi(x) - psi_ref(x)|, where
+ * psi_ref is the circuit run gate by gate in complex128 (FP64 truth; ref = 1
+ * in the table) for a complex64 state of at most 30 qubits whose complex128
+ * copy fits in free device memory, else the first candidate's result
+ * (ref = 0; its own error then reads 0).  The fastest candidate with
+ * err <= max_err is kept (max_err <= 0: no bound, and errors are measured
+ * only when table_cap > 0).  When no reference can be allocated errors read
+ * -1, and with max_err > 0 no candidate qualifies (QSIM_EUNSUPPORTED).  table
  * (may be NULL when table_cap = 0) receives one entry per candidate, in
  * order; ms < 0 marks a candidate that could not run. */
 typedef struct qsim_tune_entry {
     int mode;       /* QSIM_FUSE_* */
     int kmax;
     double ms;      /* time per circuit, CUDA events */
-    double err;     /* 2-norm of the difference from the reference plan's result */
+    double err;     /* 2-norm of the difference from the reference result */
     double max_abs; /* largest amplitude difference */
+    int ref;        /* 1: reference = gate-by-gate complex128 run; 0: the first candidate */
+    int npasses;    /* tensor-core plans: passes */
+    int nfp32;      /* tensor-core plans: passes run in FP32 on the CUDA cores */
 } qsim_tune_entry;
 QSIM_API int qsim_plan_autotune_ex(const qsim_circuit *c, qsim_state *scratch, int reps, double max_err,
                                    qsim_plan **out, qsim_tune_entry *table, int table_cap, int *table_len);

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
 
 C64, C128 = 0, 1
 FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
+PREC_BF16X3, PREC_TF32X3, PREC_FP32 = 0, 1, 2
 INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE, INIT_NULL = 0, 1, 2, 3, 4
 SLICE_SEGMENT, SLICE_SWAP = 0, 1
 SLICES_DEVICE, SLICES_HOST = 0, 1
@@ -65,6 +66,8 @@ _SIGS = {
     "qsim_plan_tc_pass": ([P, I, P, P, P, P, P, P, P], I),
     "qsim_plan_tc_epilogue": ([P, I, I, P, P, P, P, P], I),
     "qsim_plan_stage": ([P, I, P, P, P, P, P], I),
+    "qsim_plan_tc_precision": ([P, I, P], I),
+    "qsim_plan_tc_set_precision": ([P, I, P], I),
     "qsim_apply_fused": ([P, P], I),
     "qsim_plan_autotune": ([P, P, I, P, P, P, P], I),
     "qsim_plan_autotune_ex": ([P, P, I, D, P, P, I, P], I),
@@ -207,7 +210,8 @@ def circuit_gates(handle) -> list:
 
 class _TuneEntry(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("kmax", ctypes.c_int), ("ms", ctypes.c_double), ("err", ctypes.c_double),
-                ("max_abs", ctypes.c_double)]
+                ("max_abs", ctypes.c_double), ("ref", ctypes.c_int), ("npasses", ctypes.c_int),
+                ("nfp32", ctypes.c_int)]
 
 
 class Plan:
@@ -230,16 +234,20 @@ class Plan:
     def autotune(cls, circuit, scratch_state: "State", reps: int = 1, max_err: float | None = None) -> "Plan":
         """Fastest plan for `circuit`, timed on `scratch_state` (overwritten).
 
-        With `max_err`, every candidate's error against the FP32 staged plan
-        is measured (qsim_plan_autotune_ex) and only plans within it qualify;
-        the measured table is kept in `.table`."""
+        With `max_err`, every candidate's error is measured against the
+        gate-by-gate complex128 run (or, when that does not fit, the FP32
+        staged plan) by qsim_plan_autotune_ex, only plans within it qualify,
+        and a tensor-core plan with FP32 passes mixed in may be added; the
+        measured table is kept in `.table` (`ref`: 1 for the complex128
+        reference; `npasses`, `nfp32`: tensor-core passes and how many run in
+        FP32)."""
         qc = circuit if isinstance(circuit, QCircuit) else QCircuit(circuit)
         if max_err is not None:
-            tab = (_TuneEntry * 8)()
+            tab = (_TuneEntry * 16)()
             nt = ctypes.c_int()
             h = ctypes.c_void_p()
             _check(lib().qsim_plan_autotune_ex(qc.handle, scratch_state.handle, reps, float(max_err),
-                                               ctypes.byref(h), tab, 8, ctypes.byref(nt)))
+                                               ctypes.byref(h), tab, 16, ctypes.byref(nt)))
             self = cls.__new__(cls)
             info = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
             self.n, self.handle = qc.n, h
@@ -247,10 +255,12 @@ class Plan:
             self.mode = info[2].value
             names = {FUSE_GREEDY2: "greedy2", FUSE_STAGED: "staged", FUSE_TC: "tc"}
             self.table = [{"mode": names.get(e.mode, e.mode), "kmax": e.kmax, "ms": e.ms, "err": e.err,
-                           "max_abs": e.max_abs} for e in tab[: nt.value]]
+                           "max_abs": e.max_abs, "ref": "fp64" if e.ref else "first candidate",
+                           "npasses": e.npasses, "nfp32": e.nfp32} for e in tab[: nt.value]]
             ok = [e for e in self.table if e["ms"] >= 0 and 0 <= e["err"] <= max_err]
             best = min(ok, key=lambda e: e["ms"]) if ok else None
             self.kmax = best["kmax"] if best else 0
+            self.nfp32 = best["nfp32"] if best else 0
             self.tuned_ms = best["ms"] if best else -1.0
             return self
         h = ctypes.c_void_p()
@@ -261,6 +271,19 @@ class Plan:
         self.n, self.handle, self.mode = qc.n, h, mode.value
         self.kmax, self.tuned_ms = kmax.value, ms.value
         return self
+
+    def tc_precisions(self) -> list:
+        """Arithmetic of each pass of a tensor-core plan (PREC_* values)."""
+        out = []
+        for i in range(self.info()["sweeps"]):
+            v = ctypes.c_int()
+            _check(lib().qsim_plan_tc_precision(self.handle, i, ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
+    def set_tc_precisions(self, prec):
+        arr = _arr(prec, np.int32)
+        _check(lib().qsim_plan_tc_set_precision(self.handle, len(arr), _p(arr)))
 
     def info(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -125,6 +125,9 @@ size_t marginal_scratch_doubles(int n, int m);
 int launch_norm2(const void *psi, int n, int dtype, double *partials, double *result,
                  cudaStream_t st);
 size_t reduce_partials_needed(int n);
+// a complex64, b complex128 (a result against its FP64 reference); otherwise as below
+int launch_diff_norm2_c64_c128(const void *a, const void *b, int n, double *partials, double *result,
+                               cudaStream_t st);
 // result[0] = sum |a - b|^2, result[1] = max |a - b|^2 (partials: 2 x reduce_partials_needed)
 int launch_diff_norm2(const void *a, const void *b, int n, int dtype, double *partials, double *result,
                       cudaStream_t st);

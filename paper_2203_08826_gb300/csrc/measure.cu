@@ -382,9 +382,10 @@ __global__ void __launch_bounds__(256) k_norm2(const C *__restrict__ psi, uint64
     if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
-// Squared 2-norm and largest modulus of a - b (double), per block.
-template <typename C>
-__global__ void __launch_bounds__(256) k_diff2(const C *__restrict__ a, const C *__restrict__ b, uint64_t N,
+// Squared 2-norm and largest modulus of a - b (double), per block; a and b
+// may differ in precision (a complex64 result against a complex128 reference).
+template <typename CA, typename CB>
+__global__ void __launch_bounds__(256) k_diff2(const CA *__restrict__ a, const CB *__restrict__ b, uint64_t N,
                                                double *__restrict__ partials, double *__restrict__ maxes) {
     double acc = 0, mx = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
@@ -430,6 +431,23 @@ int launch_diff_norm2(const void *a, const void *b, int n, int dtype, double *pa
         else
             k_diff2<<<blocks, T, 0, st>>>(static_cast<const double2 *>(a), static_cast<const double2 *>(b), N,
                                           partials, partials + blocks);
+        QSIM_CUDA_TRY(cudaGetLastError(), "difference launch");
+    }
+    LaunchScope ls(K_REDUCE, st, blocks * 16.0);
+    k_sum_partials<<<1, 256, 0, st>>>(partials, blocks, result, 0);
+    k_max_partials<<<1, 256, 0, st>>>(partials + blocks, blocks, result + 1);
+    QSIM_CUDA_TRY(cudaGetLastError(), "difference sum launch");
+    return QSIM_OK;
+}
+
+int launch_diff_norm2_c64_c128(const void *a, const void *b, int n, double *partials, double *result,
+                               cudaStream_t st) {
+    const uint64_t N = uint64_t(1) << n;
+    const int blocks = reduce_blocks(), T = 256;
+    {
+        LaunchScope ls(K_REDUCE, st, 24.0 * double(N));
+        k_diff2<<<blocks, T, 0, st>>>(static_cast<const float2 *>(a), static_cast<const double2 *>(b), N, partials,
+                                      partials + blocks);
         QSIM_CUDA_TRY(cudaGetLastError(), "difference launch");
     }
     LaunchScope ls(K_REDUCE, st, blocks * 16.0);

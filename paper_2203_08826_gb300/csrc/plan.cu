@@ -255,13 +255,22 @@ int qsim_plan_block(const qsim_plan *p, int i, int *k, int *targets, double *mat
     return QSIM_OK;
 }
 
-// Candidates: complex64 — staged tiles (FP32 on the CUDA cores) and
-// tensor-core blocks (BF16x3, 3xTF32); complex128 (FP64-bound) — staged
-// tiles against one sweep per gate (greedy fusion limited to 1 qubit).  Each
-// runs once from |0...0> (warm-up, and the state whose error is measured
-// when max_err > 0), then `reps` timed times.  The error of a plan is the
-// difference of its |0...0> result from the first candidate's (staged,
-// kmax 3: the plan with the fewest rounding steps per gate).
+// Candidates: complex64 -- staged tiles (FP32 on the CUDA cores, tiles of
+// 2^12 and 2^13 amplitudes) and tensor-core plans with every pass in BF16x3
+// (6-qubit windows), 3xTF32 (5-qubit windows) or FP32 on the CUDA cores
+// (6-qubit windows); complex128 -- staged tiles against one sweep per gate
+// (greedy fusion limited to 1 qubit).  Each runs once from |0...0> (warm-up,
+// and the state whose error is measured when max_err > 0 or a table is
+// asked for), then `reps` timed times.
+// Error reference: for a complex64 state of at most 30 qubits whose
+// complex128 copy fits in free device memory, the circuit run gate by gate
+// in complex128 (FP64 truth); otherwise the first candidate's result.
+// Mixed precision per block: when the BF16x3 plan misses the bound and the
+// FP32 one meets it, their measured errors give a per-pass error for each
+// precision (error of the whole plan / its passes); the fewest passes that
+// must run in FP32 for the predicted error (sum over passes) to stay within
+// the bound run in FP32, the others in BF16x3, and that plan is measured as
+// one more candidate.
 static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double max_err, qsim_plan **out,
                          qsim_tune_entry *table, int table_cap, int *table_len) {
     if (!c || !s || !out) return set_error(QSIM_EINVAL, "NULL argument");
@@ -272,19 +281,40 @@ static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double 
     if (reps < 1) reps = 1;
     struct Cand {
         int mode, kmax;
+        int fp32;  // tensor-core plans: -1 every pass at the window's split, -2 every pass in FP32, k >= 0: k passes in FP32
     };
-    std::vector<Cand> cands = {{QSIM_FUSE_STAGED, 3}, {QSIM_FUSE_STAGED, 4}};
+    std::vector<Cand> cands = {{QSIM_FUSE_STAGED, 3, -1}, {QSIM_FUSE_STAGED, 4, -1}};
     if (s->dtype == QSIM_C64) {
-        cands.push_back({QSIM_FUSE_TC, 6});
-        cands.push_back({QSIM_FUSE_TC, 5});
+        cands.push_back({QSIM_FUSE_TC, 6, -1});
+        cands.push_back({QSIM_FUSE_TC, 5, -1});
+        if (max_err > 0 || table_cap > 0) cands.push_back({QSIM_FUSE_TC, 6, -2});  // only an accuracy option
     } else {
-        cands.push_back({QSIM_FUSE_GREEDY2, 1});
+        cands.push_back({QSIM_FUSE_GREEDY2, 1, -1});
     }
     const bool measure = max_err > 0 || table_cap > 0;
     const size_t bytes = s->size() * s->amp_bytes();
+    // FP64 reference: the gate-by-gate complex128 run
+    qsim_state *ref64 = nullptr;
+    struct R64Guard {
+        qsim_state *&p;
+        ~R64Guard() {
+            if (p) qsim_state_destroy(p);
+        }
+    } r64g{ref64};
+    if (measure && s->dtype == QSIM_C64 && s->n <= 30) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > 2 * s->size() * 16 + (size_t(1) << 30) &&
+            qsim_state_create(s->n, QSIM_C128, nullptr, s->stream, &ref64) == QSIM_OK) {
+            if (qsim_state_init(ref64, QSIM_INIT_ZERO, 0, nullptr) != QSIM_OK || qsim_run(ref64, c) != QSIM_OK) {
+                qsim_state_destroy(ref64);
+                ref64 = nullptr;
+            }
+        }
+        cudaGetLastError();
+    }
     void *ref = nullptr;
     bool have_ref = false;
-    if (measure && dev_alloc(&ref, bytes) != cudaSuccess) {
+    if (measure && !ref64 && dev_alloc(&ref, bytes) != cudaSuccess) {
         cudaGetLastError();  // not enough memory for the reference copy: errors are not measured
         ref = nullptr;
     }
@@ -301,20 +331,40 @@ static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double 
     qsim_plan *best = nullptr;
     float best_ms = 1e30f;
     int nt = 0;
-    for (const Cand &cd_ : cands) {
-        qsim_tune_entry ent{cd_.mode, cd_.kmax, -1.0, -1.0, -1.0};
+    double err_bf = -1, err_fp = -1;  // whole-plan errors of the BF16x3 and FP32 6-qubit plans
+    int passes_bf = 0;
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        const Cand cd_ = cands[ci];
+        qsim_tune_entry ent{cd_.mode, cd_.kmax, -1.0, -1.0, -1.0, ref64 ? 1 : 0, 0, 0};
         qsim_plan *p = nullptr;
         bool ok = qsim_plan_build(c, cd_.kmax, cd_.mode, &p) == QSIM_OK;  // e.g. too narrow for a tile
+        if (ok && cd_.mode == QSIM_FUSE_TC && p->tc) {
+            const int m = tc_nsweeps(*p);
+            std::vector<int> prec(size_t(m), -1);
+            for (int i = 0; i < m; ++i) prec[size_t(i)] = tc_pass_precision(*p, i);
+            int nfp = 0;
+            for (int i = 0; i < m; ++i)
+                if (cd_.fp32 == -2 || (cd_.fp32 >= 0 && nfp < cd_.fp32)) {
+                    prec[size_t(i)] = QSIM_PREC_FP32;
+                    ++nfp;
+                }
+            ok = tc_set_precisions(*p, prec) == QSIM_OK;
+            ent.npasses = m;
+            ent.nfp32 = nfp;
+        }
         ok = ok && qsim_state_init(s, QSIM_INIT_ZERO, 0, nullptr) == QSIM_OK && qsim_apply_fused(s, p) == QSIM_OK;
-        if (ok && ref) {
-            if (!have_ref) {
+        if (ok && (ref64 || ref)) {
+            if (!ref64 && !have_ref) {
                 ok = cudaMemcpyAsync(ref, s->amps, bytes, cudaMemcpyDeviceToDevice, s->stream) == cudaSuccess;
                 have_ref = ok;
                 ent.err = ent.max_abs = 0.0;
             } else if (s->ensure_scratch((2 * np + 2) * sizeof(double)) == QSIM_OK) {
                 double *part = static_cast<double *>(s->scratch);
                 double host[2] = {0, 0};
-                ok = launch_diff_norm2(s->amps, ref, s->n, s->dtype, part, part + 2 * np, s->stream) == QSIM_OK &&
+                const int rc = ref64 ? launch_diff_norm2_c64_c128(s->amps, ref64->amps, s->n, part, part + 2 * np,
+                                                                  s->stream)
+                                     : launch_diff_norm2(s->amps, ref, s->n, s->dtype, part, part + 2 * np, s->stream);
+                ok = rc == QSIM_OK &&
                      cudaMemcpyAsync(host, part + 2 * np, sizeof host, cudaMemcpyDeviceToHost, s->stream) ==
                          cudaSuccess &&
                      cudaStreamSynchronize(s->stream) == cudaSuccess;
@@ -337,6 +387,19 @@ static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double 
         }
         if (nt < table_cap) table[nt] = ent;
         ++nt;
+        if (ok && cd_.mode == QSIM_FUSE_TC && cd_.kmax == 6 && cd_.fp32 == -1) {
+            err_bf = ent.err;
+            passes_bf = ent.npasses;
+        }
+        if (ok && cd_.mode == QSIM_FUSE_TC && cd_.fp32 == -2) {
+            err_fp = ent.err;
+            // per-block precision: how many passes must run in FP32
+            if (max_err > 0 && err_bf > max_err && err_fp >= 0 && err_fp < max_err && passes_bf > 0) {
+                const double x = double(passes_bf) * (err_bf - max_err) / (err_bf - err_fp);
+                const int nfp = std::min(passes_bf, int(std::ceil(x)));
+                if (nfp > 0 && nfp < passes_bf) cands.push_back({QSIM_FUSE_TC, 6, nfp});
+            }
+        }
         // within the bound: the error was measured and is small enough, or no bound
         const bool accurate = max_err <= 0 || (ent.err >= 0 && ent.err <= max_err);
         if (ok && accurate && ms < best_ms) {

@@ -77,5 +77,7 @@ void tc_describe(const qsim_plan &p, std::string &out);
 int build_tc(const qsim_circuit &c, qsim_plan &p);
 int run_tc(qsim_state *s, qsim_plan &p);
 int tc_nsweeps(const qsim_plan &p);
+int tc_set_precisions(qsim_plan &p, const std::vector<int> &prec);
+int tc_pass_precision(const qsim_plan &p, int i);
 int run_block_plan(qsim_state *s, qsim_plan &p);
 }  // namespace qsim

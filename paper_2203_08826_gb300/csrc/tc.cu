@@ -51,7 +51,9 @@ constexpr int MAX_EPI = 48;        // epilogue diagonal ops per pass
 constexpr int MAX_EPI_POOL = 256;  // their complex entries
 constexpr unsigned long long WAIT_LIMIT = 1ull << 26;  // bounded mbarrier waits
 
-enum TcPrec { TC_BF16X3 = 0, TC_TF32X3 = 1 };
+// per-pass arithmetic: BF16x3 or 3xTF32 on the tensor cores, or the same
+// contraction in FP32 on the CUDA cores (k_rot_simt)
+enum TcPrec { TC_BF16X3 = 0, TC_TF32X3 = 1, TC_FP32 = 2 };
 
 struct EpiOp {
     uint64_t cmask;  // control bits (current index) that must all be 1
@@ -461,6 +463,85 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_block(const __grid_constan
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TCOLS));
 }
 
+// The FP32 CUDA-core form of a pass: the same contraction, epilogue and
+// rotated store as k_tc_block, with the block matrix (complex64, row-major)
+// broadcast from shared memory.  A CTA of 128 threads loads 128 consecutive
+// rows (one contiguous run of 128 * 2^K amplitudes) into a padded shared
+// tile, each thread takes one row into registers and forms its 2^K outputs;
+// for each output column the 128 threads store 128 consecutive amplitudes.
+template <int K>
+__global__ void __launch_bounds__(128) k_rot_simt(const __grid_constant__ TcParams p, const float2 *__restrict__ G) {
+    constexpr int D = 1 << K;
+    constexpr int ROWS = 128;
+    extern __shared__ __align__(16) unsigned char simt_smem[];
+    float2 *gm = reinterpret_cast<float2 *>(simt_smem);
+    float2 *tile = gm + D * D;  // ROWS x (D + 1)
+    uint64_t *s_negr = reinterpret_cast<uint64_t *>(tile + ROWS * (D + 1));
+    uint64_t *s_negc = s_negr + MAX_EPI;
+    EpiOp *s_epi = reinterpret_cast<EpiOp *>(s_negc + MAX_EPI);
+    float2 *s_pool = reinterpret_cast<float2 *>(s_epi + MAX_EPI);
+    for (int i = threadIdx.x; i < D * D; i += ROWS) gm[i] = G[i];
+    for (int i = threadIdx.x; i < p.nneg; i += ROWS) {
+        s_negr[i] = p.negr[i];
+        s_negc[i] = p.negc[i];
+    }
+    for (int i = threadIdx.x; i < p.nepi; i += ROWS) s_epi[i] = p.epi[i];
+    for (int i = threadIdx.x; i < MAX_EPI_POOL; i += ROWS) s_pool[i] = p.pool[i];
+    const int n = p.n;
+    const uint64_t nrows = uint64_t(1) << (n - K);
+    const int m = threadIdx.x;
+    for (uint64_t r0 = uint64_t(blockIdx.x) * ROWS; r0 < nrows; r0 += uint64_t(gridDim.x) * ROWS) {
+        __syncthreads();  // the matrix and tables are in place; the previous tile is consumed
+        const float2 *src = p.in + (r0 << K);
+        for (int i = threadIdx.x; i < ROWS * D; i += ROWS) tile[(i >> K) * (D + 1) + (i & (D - 1))] = __ldcs(src + i);
+        __syncthreads();
+        float2 v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = tile[m * (D + 1) + c];
+        const uint64_t R = r0 + uint64_t(m);
+        uint64_t flip = 0;
+        for (int e = 0; e < p.nneg; ++e)
+            if ((R & s_negr[e]) == s_negr[e]) flip ^= s_negc[e];
+#pragma unroll 1
+        for (int c = 0; c < D; ++c) {
+            const float2 *row = gm + c * D;
+            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+            for (int j = 0; j < D; j += 2) {
+                const float2 g0 = row[j], g1 = row[j + 1];
+                ax = fmaf(g0.x, v[j].x, ax);
+                ax = fmaf(-g0.y, v[j].y, ax);
+                ay = fmaf(g0.x, v[j].y, ay);
+                ay = fmaf(g0.y, v[j].x, ay);
+                bx = fmaf(g1.x, v[j + 1].x, bx);
+                bx = fmaf(-g1.y, v[j + 1].y, bx);
+                by = fmaf(g1.x, v[j + 1].y, by);
+                by = fmaf(g1.y, v[j + 1].x, by);
+            }
+            float2 o = make_float2(ax + bx, ay + by);
+            if ((flip >> c) & 1) {
+                o.x = -o.x;
+                o.y = -o.y;
+            }
+            const uint64_t x = (R << K) | uint64_t(c);
+            for (int e = 0; e < p.nepi; ++e) {
+                const EpiOp &op = s_epi[e];
+                if ((x & op.cmask) != op.cmask) continue;
+                int sel = 0;
+                for (int t = 0; t < op.k; ++t) sel = (sel << 1) | int((x >> op.sel[t]) & 1);
+                const float2 f = s_pool[op.moff + sel];
+                o = make_float2(f.x * o.x - f.y * o.y, f.x * o.y + f.y * o.x);
+            }
+            __stcs(&p.out[(uint64_t(c) << (n - K)) | R], o);
+        }
+    }
+}
+
+template <int K> constexpr int simt_smem_bytes() {
+    return int(((1 << K) * (1 << K) + 128 * ((1 << K) + 1)) * sizeof(float2) + 2 * MAX_EPI * sizeof(uint64_t) +
+               MAX_EPI * sizeof(EpiOp) + MAX_EPI_POOL * sizeof(float2));
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ plan
@@ -477,6 +558,7 @@ struct TcPass {
     };
     std::vector<Diag> epi;
     int ngates = 0;
+    int prec = TC_BF16X3;        // arithmetic of this pass (TcPrec)
 };
 
 struct TcPlan {
@@ -679,8 +761,30 @@ int build_tc(const qsim_circuit &c, qsim_plan &p) {
             break;
         }
     }
+    for (TcPass &ps : tp->passes) ps.prec = tp->prec;
     return QSIM_OK;
 }
+
+// Arithmetic of each pass (TcPrec values, one per pass; plain passes ignore
+// theirs).  3xTF32 needs a 5-wide window (6-wide operands do not fit shared
+// memory).  The device images are rebuilt at the next run.
+int tc_set_precisions(qsim_plan &p, const std::vector<int> &prec) {
+    if (!p.tc) return set_error(QSIM_EINVAL, "not a tensor-core plan");
+    TcPlan &tp = *p.tc;
+    if (prec.size() != tp.passes.size()) return set_error(QSIM_EINVAL, "one precision per pass");
+    for (size_t i = 0; i < prec.size(); ++i) {
+        if (prec[i] < TC_BF16X3 || prec[i] > TC_FP32) return set_error(QSIM_EINVAL, "pass %zu: bad precision", i);
+        if (prec[i] == TC_TF32X3 && !tp.passes[i].plain && tp.passes[i].k != 5)
+            return set_error(QSIM_EINVAL, "pass %zu: 3xTF32 passes are 5 qubits wide", i);
+    }
+    for (size_t i = 0; i < prec.size(); ++i) tp.passes[i].prec = prec[i];
+    if (tp.dev.bimg) cudaFree(tp.dev.bimg);
+    tp.dev.bimg = nullptr;
+    tp.dev.ready = false;
+    return QSIM_OK;
+}
+
+int tc_pass_precision(const qsim_plan &p, int i) { return p.tc->passes[size_t(i)].prec; }
 
 namespace {
 
@@ -745,8 +849,18 @@ int prepare_tc(qsim_plan &p, int n) {
             tp.dev.params.push_back(prm);
             continue;
         }
-        if (tp.prec == TC_BF16X3) build_bimage<2>(ps.block, ps.k, img, tp.prec);
-        else build_bimage<4>(ps.block, ps.k, img, tp.prec);
+        if (ps.prec == TC_FP32) {  // the block itself, complex64 row-major
+            const size_t d2 = size_t(1) << (2 * ps.k);
+            img.resize(d2 * sizeof(float2));
+            for (size_t e = 0; e < d2; ++e) {
+                const float2 v = make_float2(float(ps.block[e].real()), float(ps.block[e].imag()));
+                memcpy(&img[e * sizeof(float2)], &v, sizeof v);
+            }
+        } else if (ps.prec == TC_BF16X3) {
+            build_bimage<2>(ps.block, ps.k, img, ps.prec);
+        } else {
+            build_bimage<4>(ps.block, ps.k, img, ps.prec);
+        }
         tp.dev.boff.push_back(all.size());
         all.insert(all.end(), img.begin(), img.end());
         while (all.size() % 256) all.push_back(0);
@@ -811,6 +925,23 @@ int launch_tc_k(const TcParams &prm, cudaStream_t st) {
     return QSIM_OK;
 }
 
+template <int K>
+int launch_rot_simt(const TcParams &prm, cudaStream_t st) {
+    constexpr int smem = simt_smem_bytes<K>();
+    static bool attr = false;
+    if (!attr) {
+        QSIM_CUDA_TRY(cudaFuncSetAttribute(k_rot_simt<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "fp32 pass smem attribute");
+        attr = true;
+    }
+    const uint64_t rows = uint64_t(1) << (prm.n - K);
+    const unsigned grid = unsigned(std::min<uint64_t>(uint64_t(sm_count_tc()) * 2, (rows + 127) / 128));
+    LaunchScope ls(K_TC_BLOCK, st, 2.0 * double(rows << K) * 8.0, 8.0 * double(1 << K) * double(rows << K));
+    k_rot_simt<K><<<grid, 128, smem, st>>>(prm, reinterpret_cast<const float2 *>(prm.bimg));
+    QSIM_CUDA_TRY(cudaGetLastError(), "fp32 pass launch");
+    return QSIM_OK;
+}
+
 }  // namespace
 
 // polls before a pipeline wait gives up (test support can shorten it)
@@ -843,7 +974,9 @@ int run_tc(qsim_state *s, qsim_plan &p) {
         prm.wait_limit = g_wait_limit.load();
         const int k = tp.passes[i].k;
         int rc;
-        if (tp.prec == TC_BF16X3) rc = k == 6 ? launch_tc_k<6, TC_BF16X3>(prm, s->stream) : launch_tc_k<5, TC_BF16X3>(prm, s->stream);
+        const int prec = tp.passes[i].prec;
+        if (prec == TC_FP32) rc = k == 6 ? launch_rot_simt<6>(prm, s->stream) : launch_rot_simt<5>(prm, s->stream);
+        else if (prec == TC_BF16X3) rc = k == 6 ? launch_tc_k<6, TC_BF16X3>(prm, s->stream) : launch_tc_k<5, TC_BF16X3>(prm, s->stream);
         else if (k == 5) rc = launch_tc_k<5, TC_TF32X3>(prm, s->stream);
         else rc = set_error(QSIM_EUNSUPPORTED, "3xTF32 passes are 5 qubits wide");
         QSIM_TRY(rc);
@@ -868,7 +1001,7 @@ int tc_nsweeps(const qsim_plan &p) { return p.tc ? int(p.tc->passes.size()) : 0;
 void tc_describe(const qsim_plan &p, std::string &out) {
     if (!p.tc) return;
     char buf[256];
-    snprintf(buf, sizeof buf, "tensor-core plan: %zu passes, %s\n", p.tc->passes.size(),
+    snprintf(buf, sizeof buf, "tensor-core plan: %zu passes, default %s\n", p.tc->passes.size(),
              p.tc->prec == TC_BF16X3 ? "BF16x3 (kind::f16)" : "3xTF32 (kind::tf32)");
     out += buf;
     for (size_t i = 0; i < p.tc->passes.size(); ++i) {
@@ -879,8 +1012,9 @@ void tc_describe(const qsim_plan &p, std::string &out) {
             out += buf;
             continue;
         }
-        snprintf(buf, sizeof buf, "  %3zu k=%d qubits %d..%d (mod n) gates=%d epilogue=%zu\n", i, ps.k, ps.off,
-                 ps.off + ps.k - 1, ps.ngates, ps.epi.size());
+        static const char *pn[3] = {"bf16x3", "3xtf32", "fp32"};
+        snprintf(buf, sizeof buf, "  %3zu k=%d qubits %d..%d (mod n) gates=%d epilogue=%zu %s\n", i, ps.k, ps.off,
+                 ps.off + ps.k - 1, ps.ngates, ps.epi.size(), pn[ps.prec]);
         out += buf;
     }
 }
@@ -953,6 +1087,21 @@ QSIM_API int qsim_plan_tc_epilogue(const qsim_plan *p, int i, int e, int *k, int
             diag[2 * j + 1] = dg.d[j].imag();
         }
     return QSIM_OK;
+}
+
+QSIM_API int qsim_plan_tc_precision(const qsim_plan *p, int i, int *prec) {
+    using namespace qsim;
+    if (!p || !p->tc || !prec) return set_error(QSIM_EINVAL, "not a tensor-core plan");
+    if (i < 0 || i >= int(p->tc->passes.size())) return set_error(QSIM_EINVAL, "pass %d outside the plan", i);
+    *prec = tc_pass_precision(*p, i);
+    return QSIM_OK;
+}
+
+QSIM_API int qsim_plan_tc_set_precision(qsim_plan *p, int npasses, const int *prec) {
+    using namespace qsim;
+    if (!p || !p->tc || !prec) return set_error(QSIM_EINVAL, "not a tensor-core plan");
+    if (npasses != int(p->tc->passes.size())) return set_error(QSIM_EINVAL, "one precision per pass");
+    return tc_set_precisions(*p, std::vector<int>(prec, prec + npasses));
 }
 
 }  // extern "C"

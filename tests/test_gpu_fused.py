@@ -154,24 +154,70 @@ def test_plan_autotuner_picks_a_correct_plan(q, orc, dtype):
 
 
 def test_autotuner_error_table_and_bound(q, orc):
-    """qsim_plan_autotune_ex: every candidate's error against the FP32 staged
-    plan; a tight bound keeps only the reference plan, a loose one the
-    fastest; the kept plan matches the oracle."""
+    """qsim_plan_autotune_ex: every candidate's error against the gate-by-gate
+    complex128 run (FP64 truth), checked against the oracle's own result; a
+    bound between the BF16x3 and FP32 tensor-core plans' errors adds a mixed
+    plan with part of its passes in FP32; the kept plan is within the bound
+    and matches the oracle."""
     circ = inputs.random_circuit(18, 6, seed=13)
     want = orc.simulate(circ)
     s = q.State(18, "c64")
-    tight = q.Plan.autotune(circ, s, reps=1, max_err=1e-12)
-    tab = tight.table
-    assert [e["mode"] for e in tab] == ["staged", "staged", "tc", "tc"]
-    assert tab[0]["err"] == 0.0 and all(e["ms"] > 0 for e in tab)
-    for e in tab[2:]:
-        assert 0 < e["err"] < 1e-3 and 0 < e["max_abs"] <= e["err"]
-    assert tight.mode == q.FUSE_STAGED
-    assert any(e["mode"] == "staged" and e["kmax"] == tight.kmax and e["err"] <= 1e-12 for e in tab)
     loose = q.Plan.autotune(circ, s, reps=1, max_err=1.0)
-    fastest = min(loose.table, key=lambda e: e["ms"])
+    tab = loose.table
+    assert [(e["mode"], e["kmax"], e["nfp32"] == e["npasses"] > 0) for e in tab] == [
+        ("staged", 3, False), ("staged", 4, False), ("tc", 6, False), ("tc", 5, False), ("tc", 6, True)]
+    assert all(e["ref"] == "fp64" and e["ms"] > 0 and 0 < e["err"] < 1e-3 for e in tab)
+    fastest = min(tab, key=lambda e: e["ms"])
     assert loose.kmax == fastest["kmax"]
-    for p in (tight, loose):
+    # the table's errors are those of the plans against the oracle
+    for e in tab:
+        p = q.Plan(circ, kmax=e["kmax"], mode={"staged": q.FUSE_STAGED, "tc": q.FUSE_TC}[e["mode"]])
+        if e["mode"] == "tc" and e["nfp32"]:
+            p.set_tc_precisions([q.PREC_FP32] * p.info()["sweeps"])
         s2 = q.State(18, "c64").init_zero()
         s2.run_fused(p)
-        assert np.max(np.abs(s2.to_host() - want)) <= 1e-5
+        err2 = np.linalg.norm(s2.to_host().astype(np.complex128) - want)
+        assert abs(err2 - e["err"]) <= 1e-3 * e["err"] + 1e-9, (e, err2)
+    e_bf, e_fp = tab[2]["err"], tab[4]["err"]
+    print(f"autotune 18q: staged {tab[0]['err']:.2e}, bf16x3 {e_bf:.2e}, 3xtf32 {tab[3]['err']:.2e}, fp32 {e_fp:.2e}")
+    assert e_fp < 0.5 * e_bf
+    bound = (e_bf * e_fp) ** 0.5
+    mixed = q.Plan.autotune(circ, s, reps=1, max_err=bound)
+    mx = [e for e in mixed.table if e["mode"] == "tc" and 0 < e["nfp32"] < e["npasses"]]
+    assert len(mx) == 1 and mx[0]["kmax"] == 6
+    chosen = [e for e in mixed.table if e["ms"] >= 0 and e["err"] <= bound]
+    assert chosen and mixed.tuned_ms == min(e["ms"] for e in chosen)
+    s2 = q.State(18, "c64").init_zero()
+    s2.run_fused(mixed)
+    assert np.linalg.norm(s2.to_host().astype(np.complex128) - want) <= bound * 1.001
+
+
+def test_tensor_core_plan_per_pass_precision(q, orc):
+    """Each pass of a tensor-core plan in its own arithmetic: all FP32 (CUDA
+    cores) is as accurate as the FP32 stages; a mix of BF16x3, 3xTF32 and FP32
+    passes matches the oracle; 3xTF32 on a 6-qubit window is refused."""
+    n = 16
+    circ = inputs.random_circuit(n, 6, seed=41)
+    psi0 = inputs.gaussian_state(n, seed=42)
+    want = orc.simulate(circ, psi0)
+    p = q.Plan(circ, kmax=6, mode=q.FUSE_TC)
+    m = p.info()["sweeps"]
+    assert p.tc_precisions() == [q.PREC_BF16X3] * m
+    ks = [0 if ps["plain"] else len(ps["targets"]) for ps in p.tc_passes()]  # window width per pass
+    p.set_tc_precisions([q.PREC_FP32] * m)
+    s = q.State(n, "c64").from_host(psi0.astype(np.complex64))
+    s.run_fused(p)
+    err = np.max(np.abs(s.to_host() - want)) / np.max(np.abs(want))
+    print(f"tc fp32 passes 16q: relative max-abs {err:.2e}")
+    assert err <= 2e-6
+    mix = [(q.PREC_TF32X3 if k == 5 else q.PREC_BF16X3) if i % 2 else q.PREC_FP32 for i, k in enumerate(ks)]
+    p.set_tc_precisions(mix)
+    assert p.tc_precisions() == mix
+    s = q.State(n, "c64").from_host(psi0.astype(np.complex64))
+    s.run_fused(p)
+    err = np.max(np.abs(s.to_host() - want)) / np.max(np.abs(want))
+    assert err <= 5e-5
+    if 6 in ks:
+        bad = [q.PREC_TF32X3 if k == 6 else q.PREC_BF16X3 for k in ks]
+        with pytest.raises(q.QsimError):
+            p.set_tc_precisions(bad)

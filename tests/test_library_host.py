@@ -271,3 +271,33 @@ def test_complex64_sampler_weights_match_their_definition():
             assert lib.qsim_prob_c64(re, im) == math.inf
         elif not (math.isnan(x) or math.isnan(y)):
             assert lib.qsim_prob_c64(re, im) == float(Fraction(x) ** 2 + Fraction(y) ** 2), (re, im)
+
+
+def test_tensor_core_pass_precisions_host(q):
+    """Per-pass arithmetic of a tensor-core plan (host only): every pass
+    starts at its window's split, any mix of BF16x3, 3xTF32 (5-qubit windows
+    only) and FP32 can be set and read back, bad values are refused."""
+    c = inputs.random_circuit(16, 4, seed=2)
+    p6 = q.Plan(c, kmax=6, mode=q.FUSE_TC)
+    p5 = q.Plan(c, kmax=5, mode=q.FUSE_TC)
+    m6, m5 = p6.info()["sweeps"], p5.info()["sweeps"]
+    assert p6.tc_precisions() == [q.PREC_BF16X3] * m6
+    assert p5.tc_precisions() == [q.PREC_TF32X3] * m5
+    ks = [0 if ps["plain"] else len(ps["targets"]) for ps in p6.tc_passes()]
+    mix = [q.PREC_FP32 if i % 3 == 0 else (q.PREC_TF32X3 if k == 5 else q.PREC_BF16X3) for i, k in enumerate(ks)]
+    p6.set_tc_precisions(mix)
+    assert p6.tc_precisions() == mix
+    assert "fp32" in p6.describe()
+    with pytest.raises(q.QsimError):
+        p6.set_tc_precisions(mix[:-1])
+    with pytest.raises(q.QsimError):
+        p6.set_tc_precisions([7] * m6)
+    if 6 in ks:
+        with pytest.raises(q.QsimError):
+            p6.set_tc_precisions([q.PREC_TF32X3] * m6)
+    assert p6.tc_precisions() == mix  # a refused setting changes nothing
+    p5.set_tc_precisions([q.PREC_FP32] * m5)
+    assert p5.tc_precisions() == [q.PREC_FP32] * m5
+    st = q.Plan(c, kmax=3, mode=q.FUSE_STAGED)
+    with pytest.raises(q.QsimError):
+        st.set_tc_precisions([0])
