@@ -43,8 +43,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC_30Q_C64 = {
     "sweep_dense1": 16.71e9,  # 27-qubit capture (2.089 GB) x 8
     "stage": 16.70e9,         # 27-qubit capture (2.087 GB) x 8
-    "tc_block": 16.73e9,      # 27-qubit capture (2.091 GB) x 8
+    "tc_block": 16.72e9,      # 27-qubit capture (1.07 + 1.02 GB) x 8
     "sweep_densek": 16.72e9,  # 2-qubit blocks, 27-qubit capture (2.090 GB) x 8
+}
+# complex128 kernels that are not the complex64 kernel at twice the bytes
+NCU_TRAFFIC_30Q_C128 = {
+    "sweep_dense1": 33.88e9,  # double-float / FP64 sweep, 27-qubit capture (4.234 GB) x 8
 }
 
 
@@ -334,6 +338,8 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 
 def traffic_of(name, n_qubits, amp_bytes):
+    if amp_bytes == 16 and name in NCU_TRAFFIC_30Q_C128:
+        return NCU_TRAFFIC_30Q_C128[name] * 2.0 ** (n_qubits - 30)
     t = NCU_TRAFFIC_30Q_C64.get(name)
     return None if t is None else t * 2.0 ** (n_qubits - 30) * amp_bytes / 8
 
@@ -356,6 +362,8 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_byt
         r = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
              "frac": round(tf / pk, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+             "flops_basis": "the circuit's gates, one sweep each (16 per amplitude per dense 1-qubit gate); "
+                            "fused 4x4 blocks execute fewer",
              "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4),
              "hbm_frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
     else:

@@ -526,6 +526,14 @@ QSIM_API int qsim_debug_fail_alloc(int skip, int count);
  * contents undefined.  A limit of a few polls makes the first waits expire,
  * which tests the timeout path without a fault or a hang. */
 QSIM_API int qsim_debug_set_wait_limit(unsigned long long polls);
+/* Index bound checks (test support; the paper has no counterpart).  A build
+ * compiled with QSIM_DEBUG checks, before every global access of the plain
+ * sweeps and of the staged register tiles, that the index lies inside the
+ * state; an index outside is counted and its access skipped, and
+ * qsim_synchronize then returns QSIM_EINVAL.  Returns the count since the
+ * library was loaded (cleared when clear != 0), or -1 in a release build,
+ * which has no checks. */
+QSIM_API long long qsim_debug_checks(int clear);
 
 /* ---------------------------------------------------------------- profiling */
 /* Launch accounting for every kernel the library starts.  When enabled, each

@@ -18,7 +18,9 @@ import numpy as np
 from . import inputs
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libqsim.so")
+# QSIM_LIBRARY=debug loads the build with index bound checks (build(debug=True))
+LIB_PATH = (os.path.join(_HERE, "_build_debug", "libqsim_debug.so") if os.environ.get("QSIM_LIBRARY") == "debug"
+            else os.path.join(_HERE, "_build", "libqsim.so"))
 
 C64, C128 = 0, 1
 FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
@@ -100,6 +102,7 @@ _SIGS = {
     "qsim_prob_c64": ([ctypes.c_float, ctypes.c_float], D),
     "qsim_debug_fail_alloc": ([I, I], I),
     "qsim_debug_set_wait_limit": ([ctypes.c_ulonglong], I),
+    "qsim_debug_checks": ([I], ctypes.c_longlong),
     "qsim_profile_enable": ([I], I),
     "qsim_profile_reset": ([], I),
     "qsim_profile_count": ([P], I),

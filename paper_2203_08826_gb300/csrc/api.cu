@@ -454,7 +454,20 @@ int qsim_state_copy_to_host(qsim_state *s, void *dst) {
 int qsim_synchronize(qsim_state *s) {
     if (!s) return set_error(QSIM_EINVAL, "state is NULL");
     QSIM_CUDA_TRY(cudaStreamSynchronize(s->stream), "synchronize");
+#ifdef QSIM_DEBUG
+    if (sweep_debug_oob(false) + staged_debug_oob(false))
+        return set_error(QSIM_EINVAL, "debug build: a kernel index fell outside its state (access skipped)");
+#endif
     return QSIM_OK;
+}
+
+long long qsim_debug_checks(int clear) {
+#ifdef QSIM_DEBUG
+    return (long long)(sweep_debug_oob(clear != 0) + staged_debug_oob(clear != 0));
+#else
+    (void)clear;
+    return -1;
+#endif
 }
 
 // ------------------------------------------------------------------ gates

@@ -22,6 +22,13 @@ int cuda_error(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return ::qsim::cuda_error(e_, what);  \
     } while (0)
+// QSIM_DEBUG builds check, before every global access of the plain sweeps and
+// the staged tiles, that the index lies inside the state; an index outside is
+// counted (per translation unit) and the access skipped.  These return the
+// count since load (and clear it when asked); release builds have no checks.
+unsigned long long sweep_debug_oob(bool clear);
+unsigned long long staged_debug_oob(bool clear);
+
 // Every device allocation of the library goes through here, so that a test can
 // make chosen allocations fail (qsim_debug_fail_alloc) without a GPU fault.
 cudaError_t dev_alloc(void **p, size_t bytes);
@@ -87,6 +94,7 @@ struct IndexMap {
     int nins;
     int ins[MAX_INS];
     uint64_t set;
+    uint64_t limit;  // 2^n of the state it indexes (0: unknown); checked in QSIM_DEBUG builds
 };
 IndexMap make_index_map(const int *zero_bits, int nz, const int *one_bits, int no);
 // Offsets of the 2^k amplitudes of a group (matrix index j, targets[0] = MSB).

@@ -523,11 +523,12 @@ struct Stage {
     std::vector<int> gates;  // source gates the stage applies, in schedule order (before merging / batching)
 };
 
-// Split a circuit into stages for tiles of 2^(9 + W) amplitudes.  With
-// `limits` the op, phase and pool counts of a stage stay within one kernel
-// parameter block.
-// useful flops per amplitude of a planned stage (host)
-double stage_flops_per_amp(const Stage &st);
+// algorithmic flops per amplitude of a planned stage: those of the circuit's
+// gates it applies, one sweep each (host)
+double stage_flops_per_amp(const qsim_circuit &c, const Stage &st);
+// Split a circuit into stages for tiles of 2^(9 + W) amplitudes (after pair
+// fusion, when the circuit has no gradient markers).  With `limits` the op,
+// phase and pool counts of a stage stay within one kernel parameter block.
 int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out);
 
 // Kernel parameter block of one tile stage.

@@ -25,6 +25,7 @@
 // bank), so every thread reads them at register speed.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -46,6 +47,10 @@ template <typename C> struct ParamSrc {
     __device__ uint64_t aux(int i) const { return p.aux[i]; }
 };
 
+#ifdef QSIM_DEBUG
+static __device__ unsigned long long g_staged_oob;
+#endif
+
 template <typename R, int W>
 __global__ void __launch_bounds__(32 << W, (sizeof(R) == 4 ? (W <= 3 ? 3 : 2) : 1))
     k_stage(typename CT<R>::T *__restrict__ psi, const __grid_constant__ StageParams<typename CT<R>::T> p) {
@@ -58,10 +63,32 @@ __global__ void __launch_bounds__(32 << W, (sizeof(R) == 4 ? (W <= 3 ? 3 : 2) : 
     int ph = p.phase0;
     uint64_t base = thread_base<W>(p.phases[ph], tile_base, lane, warp);
     C v[1 << REG_BITS];
+#ifdef QSIM_DEBUG
+    // every index this thread loads and stores (the same set: the final
+    // phase permutes registers within the tile) must lie inside the state;
+    // a thread with one outside computes on zeros and stores nothing, but
+    // still takes part in the CTA's exchanges
+    bool inside = true;
+    {
+        uint64_t hi = base;
+        for (int b = 0; b < REG_BITS; ++b) hi |= uint64_t(1) << p.phases[ph].rq[b];
+        if (p.outer.limit && hi >= p.outer.limit) {
+            atomicAdd(&g_staged_oob, 1ull);
+            inside = false;
+        }
+    }
+    if (inside) tile_global<C, W, false>(psi, v, p.phases[ph], base);
+    else
+        for (int j = 0; j < (1 << REG_BITS); ++j) v[j] = C{0, 0};
+#else
     tile_global<C, W, false>(psi, v, p.phases[ph], base);
+#endif
     const ParamSrc<C> src{p};
     stage_exec<C, W>(src, p.nops, v, ph, base, tile_base, tile, lane, warp);
-    tile_global<C, W, true>(psi, v, p.phases[ph], base);
+#ifdef QSIM_DEBUG
+    if (inside)
+#endif
+        tile_global<C, W, true>(psi, v, p.phases[ph], base);
 }
 
 // ------------------------------------------------------------------ host plan
@@ -378,22 +405,134 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
 
 }  // namespace
 
-// Useful flops per amplitude of a stage (a complex multiply-add is 8 flops;
-// a controlled op counts for the fraction of amplitudes it touches).
-double stage_flops_per_amp(const Stage &st) {
+// Algorithmic flops per amplitude of a stage: those of the circuit's gates it
+// applies, each counted as one sweep would apply it (a dense k-qubit gate with
+// c controls: 2^k complex multiply-adds of 8 flops on 1/2^c of the
+// amplitudes; a diagonal or permutation gate: one complex multiply of 6 flops
+// per amplitude it touches, none when every factor is +-1 or 1).  Fused
+// 4x4 blocks and merged diagonals do fewer flops than this; the count is
+// the workload's, not the plan's.
+double stage_flops_per_amp(const qsim_circuit &c, const Stage &st) {
     double f = 0;
-    if (st.plain) return st.op.type == Op::DENSE ? 8.0 * double(1 << st.op.k) / double(1ull << st.op.c) : 0.0;
-    for (const StageOp &o : st.ops) {
-        const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
-        if (o.type == SOP_U1) f += 16.0 * frac;
-        else if (o.type == SOP_U1R || o.type == SOP_U1L) f += 16.0 * __builtin_popcount(unsigned(o.a));
-        else if (o.type == SOP_U2) f += 32.0 * frac;
-        else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
+    for (int gi : st.gates) {
+        const GateRec &g = c.gates[size_t(gi)];
+        if (g.grad_slot >= 0) continue;
+        Op op;
+        if (classify(g.m, g.targets, g.k, g.controls, g.nc, op) != QSIM_OK) continue;
+        const double frac = 1.0 / double(1ull << op.c);
+        if (op.type == Op::DENSE) {
+            f += 8.0 * double(1 << op.k) * frac;
+        } else if (op.type == Op::DIAG || op.type == Op::MONO) {
+            const std::vector<cd> &e = op.type == Op::DIAG ? op.m : op.phase;
+            bool sign_only = true;
+            for (const cd &x : e) sign_only &= x.imag() == 0.0 && (x.real() == 1.0 || x.real() == -1.0);
+            if (!sign_only) f += 6.0 * frac;
+        }
     }
     return f;
 }
 
-int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out) {
+// Pair fusion before staging: a 2-qubit gate on qubits a, b (both outside
+// the lanes) absorbs the uncontrolled 1-qubit gates just before it on a and
+// on b and just after it on a and on b (each the neighbour of the 2-qubit gate
+// on its qubit, so moving it next to the gate crosses only gates it commutes
+// with), when at least three of the four exist: U = (Ha x Hb) M (Ga x Gb) is
+// one dense 4x4 at the 2-qubit gate's place.  Applied to a register pair that
+// costs 16 multiply-adds per amplitude instead of 8 per absorbed gate.  Gates
+// are taken greedily in circuit order, each 1-qubit gate absorbed at most
+// once.  src[i] lists the source gates of fused gate i in the order they act.
+static void pair_fuse(const qsim_circuit &c, std::vector<GateRec> &gates, std::vector<std::vector<int>> &src) {
+    const size_t G = c.gates.size();
+    auto touches = [&](size_t i, int q) {
+        const GateRec &g = c.gates[i];
+        for (int t = 0; t < g.k; ++t)
+            if (g.targets[t] == q) return true;
+        for (int t = 0; t < g.nc; ++t)
+            if (g.controls[t] == q) return true;
+        return false;
+    };
+    auto plain1 = [&](size_t i) {
+        const GateRec &g = c.gates[i];
+        return g.k == 1 && g.nc == 0 && g.grad_slot < 0;
+    };
+    std::vector<char> absorbed(G, 0);
+    std::vector<std::vector<int>> parts(G);  // fused 2-qubit gate -> [Ga, Gb, itself, Ha, Hb] present
+    std::vector<std::vector<cd>> fusedm(G);
+    for (size_t i = 0; i < G; ++i) {
+        const GateRec &g = c.gates[i];
+        if (g.k != 2 || g.nc != 0 || g.grad_slot >= 0 || g.targets[0] < LANE_BITS || g.targets[1] < LANE_BITS)
+            continue;
+        int prev[2] = {-1, -1}, next[2] = {-1, -1};
+        for (int t = 0; t < 2; ++t) {
+            const int q = g.targets[t];
+            for (size_t j = i; j-- > 0;)
+                if (touches(j, q)) {
+                    if (plain1(j) && !absorbed[j] && parts[j].empty()) prev[t] = int(j);
+                    break;
+                }
+            for (size_t j = i + 1; j < G; ++j)
+                if (touches(j, q)) {
+                    if (plain1(j)) next[t] = int(j);
+                    break;
+                }
+        }
+        const int have = (prev[0] >= 0) + (prev[1] >= 0) + (next[0] >= 0) + (next[1] >= 0);
+        if (have < 3) continue;
+        auto one = [&](int j) { return j >= 0 ? c.gates[size_t(j)].m : std::vector<cd>{1.0, 0.0, 0.0, 1.0}; };
+        auto kron = [](const std::vector<cd> &A, const std::vector<cd> &B) {  // A on the MSB
+            std::vector<cd> K(16);
+            for (int r = 0; r < 4; ++r)
+                for (int q = 0; q < 4; ++q) K[size_t(r * 4 + q)] = A[size_t((r >> 1) * 2 + (q >> 1))] * B[size_t((r & 1) * 2 + (q & 1))];
+            return K;
+        };
+        std::vector<cd> U = matmul(g.m, kron(one(prev[0]), one(prev[1])), 4);
+        U = matmul(kron(one(next[0]), one(next[1])), U, 4);
+        fusedm[i] = U;
+        for (int j : {prev[0], prev[1]})
+            if (j >= 0) parts[i].push_back(j);
+        parts[i].push_back(int(i));
+        for (int j : {next[0], next[1]})
+            if (j >= 0) parts[i].push_back(j);
+        for (int j : {prev[0], prev[1], next[0], next[1]})
+            if (j >= 0) absorbed[size_t(j)] = 1;
+    }
+    gates.clear();
+    src.clear();
+    for (size_t i = 0; i < G; ++i) {
+        if (absorbed[i]) continue;
+        GateRec r = c.gates[i];
+        if (!parts[i].empty()) {
+            r.kind = QSIM_GATE_MATRIX;
+            r.pindex = -1;
+            r.m = fusedm[i];
+            src.push_back(parts[i]);
+        } else {
+            src.push_back({int(i)});
+        }
+        gates.push_back(std::move(r));
+    }
+}
+
+int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stage> &out) {
+    // pair fusion first, except for the reverse sweep of the adjoint method,
+    // whose gradient markers must stay between the gates they sit between
+    qsim_circuit fused;
+    std::vector<std::vector<int>> src;
+    const bool use_fused = [&] {
+        for (const GateRec &g : c0.gates)
+            if (g.grad_slot >= 0) return false;
+        return true;
+    }();
+    if (use_fused) {
+        fused.n = c0.n;
+        fused.nparams = c0.nparams;
+        pair_fuse(c0, fused.gates, src);
+    }
+    const qsim_circuit &c = use_fused ? fused : c0;
+    auto source = [&](int gi, std::vector<int> &dst) {
+        if (use_fused) dst.insert(dst.end(), src[size_t(gi)].begin(), src[size_t(gi)].end());
+        else dst.push_back(gi);
+    };
     const int n = c.n;
     const int cap = REG_BITS + W;
     std::vector<GateClass> cls(c.gates.size());
@@ -461,7 +600,7 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
                     Stage st;
                     st.plain = true;
                     st.op = g.op;
-                    st.gates = {gi};
+                    source(gi, st.gates);
                     out.push_back(std::move(st));
                     plain_emitted = true;
                     continue;
@@ -492,7 +631,7 @@ int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage
             if (std::find(tile.begin(), tile.end(), q) == tile.end()) tile.push_back(q);
         Stage st;
         st.slots = tile;
-        st.gates = sched;
+        for (int gi : sched) source(gi, st.gates);
         std::vector<const GateClass *> gl;
         for (int gi : sched) gl.push_back(&cls[gi]);
         const int rc = emit_stage_ops(st, gl, W, limits);
@@ -528,7 +667,7 @@ struct StagedPlan {
         std::vector<unsigned char> params;  // packed StageParams per tile stage
         std::vector<size_t> param_off;
     } dev[2];
-    std::vector<double> flops_per_amp;  // useful flops per amplitude of each stage
+    std::vector<double> flops_per_amp;  // algorithmic flops per amplitude of each stage
     ~StagedPlan() {
         for (Dev &d : dev)
             for (void *m : d.plain_mats)
@@ -548,7 +687,7 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
     // kmax selects the tile: 2^(9 + W) amplitudes with W = min(kmax, 4) warp qubits
     sp->W = std::min(std::min(p.kmax, MAX_WARP_BITS), n - LANE_BITS - REG_BITS);
     QSIM_TRY(plan_stage_list(c, sp->W, true, sp->stages));
-    for (const Stage &st : sp->stages) sp->flops_per_amp.push_back(stage_flops_per_amp(st));
+    for (const Stage &st : sp->stages) sp->flops_per_amp.push_back(stage_flops_per_amp(c, st));
     return QSIM_OK;
 }
 
@@ -583,10 +722,15 @@ static int prepare_staged(qsim_plan &p, int dtype) {
         }
         d.param_off[i] = d.params.size();
         d.params.resize(d.params.size() + psz);
-        if (dtype == QSIM_C64)
-            make_params<float2>(st, *reinterpret_cast<StageParams<float2> *>(&d.params[d.param_off[i]]));
-        else
-            make_params<double2>(st, *reinterpret_cast<StageParams<double2> *>(&d.params[d.param_off[i]]));
+        if (dtype == QSIM_C64) {
+            auto &prm = *reinterpret_cast<StageParams<float2> *>(&d.params[d.param_off[i]]);
+            make_params<float2>(st, prm);
+            prm.outer.limit = uint64_t(1) << p.n;
+        } else {
+            auto &prm = *reinterpret_cast<StageParams<double2> *>(&d.params[d.param_off[i]]);
+            make_params<double2>(st, prm);
+            prm.outer.limit = uint64_t(1) << p.n;
+        }
     }
     d.ready = true;
     return QSIM_OK;
@@ -673,6 +817,21 @@ void staged_describe(const qsim_plan &p, std::string &out) {
 }
 
 int staged_nsweeps(const qsim_plan &p) { return p.staged ? int(p.staged->stages.size()) : int(p.blocks.size()); }
+
+unsigned long long staged_debug_oob(bool clear) {
+#ifdef QSIM_DEBUG
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, stage::g_staged_oob, sizeof v);
+    if (clear) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(stage::g_staged_oob, &z, sizeof z);
+    }
+    return v;
+#else
+    (void)clear;
+    return 0;
+#endif
+}
 
 }  // namespace qsim
 

@@ -32,6 +32,23 @@ template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
     return acc;
 }
 
+#ifdef QSIM_DEBUG
+static __device__ unsigned long long g_sweep_oob;
+#endif
+
+// True when index x (the largest a group will touch) lies inside the state; in
+// a QSIM_DEBUG build an index outside is counted and its group skipped, in a
+// release build nothing is checked.
+__device__ __forceinline__ bool in_state(uint64_t x, const IndexMap &m) {
+#ifdef QSIM_DEBUG
+    if (m.limit && x >= m.limit) {
+        atomicAdd(&g_sweep_oob, 1ull);
+        return false;
+    }
+#endif
+    return true;
+}
+
 __device__ __forceinline__ uint64_t expand_index(uint64_t g, const IndexMap &m) {
 #pragma unroll 1
     for (int i = 0; i < m.nins; ++i) {
@@ -88,7 +105,8 @@ __global__ void __launch_bounds__(256) k_dense1(typename CT<R>::T *__restrict__ 
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < npairs ? expand_index(g, map) : ~uint64_t(0);
-        if (g < npairs) {
+        if (g < npairs && !in_state(idx[j] + stride, map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) {
             a[j] = psi[idx[j]];
             b[j] = psi[idx[j] + stride];
         }
@@ -155,7 +173,8 @@ __global__ void __launch_bounds__(256) k_dense1_df(double2 *__restrict__ psi, ui
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < npairs ? expand_index(g, map) : ~uint64_t(0);
-        if (g < npairs) {
+        if (g < npairs && !in_state(idx[j] + stride, map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) {
             a[j] = psi[idx[j]];
             b[j] = psi[idx[j] + stride];
         }
@@ -205,7 +224,8 @@ __global__ void __launch_bounds__(256) k_dense_small(typename CT<R>::T *__restri
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < ngroups ? expand_index(g, map) : ~uint64_t(0);
-        if (g < ngroups) {
+        if (g < ngroups && !in_state(idx[j] | G.off[D - 1], map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) {
 #pragma unroll
             for (int r = 0; r < D; ++r) v[j][r] = psi[idx[j] | G.off[r]];
         }
@@ -242,6 +262,7 @@ __global__ void __launch_bounds__(128) k_dense_big(typename CT<R>::T *__restrict
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
         const uint64_t x = expand_index(g, map);
+        if (!in_state(x | offs.o[D - 1], map)) continue;
         C v[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) v[c] = psi[x | offs.o[c]];
@@ -276,13 +297,14 @@ __global__ void __launch_bounds__(256) k_densek(typename CT<R>::T *__restrict__ 
     for (int i = threadIdx.x; i < GPB * D; i += blockDim.x) {
         const int gl = i % GPB, j = i / GPB;
         const uint64_t g = g0 + gl;
-        if (g < ngroups) v[gl][j] = psi[expand_index(g, map) | offs.o[j]];
+        if (g < ngroups && in_state(expand_index(g, map) | offs.o[D - 1], map))
+            v[gl][j] = psi[expand_index(g, map) | offs.o[j]];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < GPB * D; i += blockDim.x) {
         const int gl = i % GPB, r = i / GPB;
         const uint64_t g = g0 + gl;
-        if (g >= ngroups) continue;
+        if (g >= ngroups || !in_state(expand_index(g, map) | offs.o[D - 1], map)) continue;
         C acc;
         acc.x = 0;
         acc.y = 0;
@@ -313,7 +335,8 @@ __global__ void __launch_bounds__(256) k_diag(typename CT<R>::T *__restrict__ ps
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < count ? expand_index(g, map) : ~uint64_t(0);
-        if (g < count) a[j] = psi[idx[j]];
+        if (g < count && !in_state(idx[j], map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) a[j] = psi[idx[j]];
     }
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -338,7 +361,8 @@ __global__ void __launch_bounds__(256) k_diag_df(double2 *__restrict__ psi, uint
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < count ? expand_index(g, map) : ~uint64_t(0);
-        if (g < count) a[j] = psi[idx[j]];
+        if (g < count && !in_state(idx[j], map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) a[j] = psi[idx[j]];
     }
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -385,7 +409,8 @@ __global__ void __launch_bounds__(256) k_diag_sign(typename CT<R>::T *__restrict
     for (int j = 0; j < PER; ++j) {
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         idx[j] = g < count ? expand_index(g, map) : ~uint64_t(0);
-        if (g < count) a[j] = psi[idx[j]];
+        if (g < count && !in_state(idx[j], map)) idx[j] = ~uint64_t(0);
+        if (idx[j] != ~uint64_t(0)) a[j] = psi[idx[j]];
     }
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
@@ -426,6 +451,13 @@ __global__ void __launch_bounds__(256) k_mono(typename CT<R>::T *__restrict__ ps
         const uint64_t g = base + uint64_t(j) * blockDim.x;
         x[j] = g < ngroups ? expand_index(g, map) : ~uint64_t(0);
         if (g < ngroups) {
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                if (a < p.na) ok = ok && in_state(x[j] | p.src[a] | p.dst[a], map);
+            if (!ok) x[j] = ~uint64_t(0);
+        }
+        if (x[j] != ~uint64_t(0)) {
 #pragma unroll
             for (int a = 0; a < NA; ++a)
                 if (a < p.na) v[j][a] = psi[x[j] | p.src[a]];
@@ -472,7 +504,8 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
         case Op::IDENTITY:
             return QSIM_OK;
         case Op::DENSE: {
-            const IndexMap map = make_index_map(op.targets, k, op.controls, c);
+            IndexMap map = make_index_map(op.targets, k, op.controls, c);
+            map.limit = uint64_t(1) << n;
             const uint64_t ngroups = uint64_t(1) << (n - k - c);
             const double bytes = 2.0 * S * double(ngroups << k);
             if (k == 1) {
@@ -554,7 +587,8 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
             break;
         }
         case Op::DIAG: {
-            const IndexMap map = make_index_map(nullptr, 0, op.controls, c);
+            IndexMap map = make_index_map(nullptr, 0, op.controls, c);
+            map.limit = uint64_t(1) << n;
             const uint64_t count = uint64_t(1) << (n - c);
             DiagParams<R> p{};
             p.k = k;
@@ -590,7 +624,8 @@ static int launch_op_t(void *psi_v, int n, const Op &op, cudaStream_t st, void *
             break;
         }
         case Op::MONO: {
-            const IndexMap map = make_index_map(op.targets, k, op.controls, c);
+            IndexMap map = make_index_map(op.targets, k, op.controls, c);
+            map.limit = uint64_t(1) << n;
             const uint64_t ngroups = uint64_t(1) << (n - k - c);
             MonoParams<R> p{};
             for (int r = 0; r < (1 << k); ++r) {
@@ -627,4 +662,21 @@ int launch_op(void *psi, int n, int dtype, const Op &op, cudaStream_t st, void *
                              : launch_op_t<double>(psi, n, op, st, mat_dev);
 }
 
+}  // namespace qsim
+
+namespace qsim {
+unsigned long long sweep_debug_oob(bool clear) {
+#ifdef QSIM_DEBUG
+    unsigned long long v = 0;
+    cudaMemcpyFromSymbol(&v, g_sweep_oob, sizeof v);
+    if (clear) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_sweep_oob, &z, sizeof z);
+    }
+    return v;
+#else
+    (void)clear;
+    return 0;
+#endif
+}
 }  // namespace qsim

@@ -301,3 +301,9 @@ def test_tensor_core_pass_precisions_host(q):
     st = q.Plan(c, kmax=3, mode=q.FUSE_STAGED)
     with pytest.raises(q.QsimError):
         st.set_tc_precisions([0])
+
+
+def test_release_build_has_no_index_checks(q):
+    """qsim_debug_checks is exported by both builds; the release library
+    reports -1 (no checks compiled in)."""
+    assert q.lib().qsim_debug_checks(0) == -1
