@@ -21,6 +21,9 @@ constexpr int MAX_POOL = 768;
 constexpr int MAX_AUX = 192;  // (thread mask, register pattern) pairs of batched sign flips
 constexpr int MAX_GRAD = 96;  // gradient terms (and SOP_GRAD ops) of one reverse-sweep stage
 
+// SOP_U2 on a lane position (a or b < POS_REG): the pool holds the matrix
+// rearranged per lane-bit value (lane_u2_layout), 16 entries as for two
+// register targets.
 // SOP_U1R / SOP_U1L: uncontrolled 1-qubit gates on distinct register / lane
 // bits (mask in a, matrices consecutive in the pool, lowest bit first);
 // SOP_NEG: sign flips (k pairs in aux from moff): amplitude j of a thread
@@ -139,6 +142,25 @@ __device__ __forceinline__ double2 shfl_c(double2 a, int mask) {
     return a;
 }
 
+// A dense 4x4 on one lane bit (partner lane = lane ^ lmask) and register bit
+// JB: for each register pair the thread's two amplitudes (x0, x1: register
+// bit 0, 1) and its partner's (y0, y1) give the thread's two outputs,
+// out_r = m[4r] x0 + m[4r+1] x1 + m[4r+2] y0 + m[4r+3] y1, with m the eight
+// coefficients the host laid out for this thread's lane-bit value.  Every
+// lane takes part in the shuffles; ok / rneed only gate the update.
+template <typename C, int JB>
+__device__ __forceinline__ void u2_lane_reg(C (&v)[1 << REG_BITS], const C (&m)[8], int lmask, bool ok, int rneed) {
+#pragma unroll
+    for (int i = 0; i < (1 << REG_BITS); ++i) {
+        if (i & (1 << JB)) continue;
+        const C x0 = v[i], x1 = v[i | (1 << JB)];
+        const C y0 = shfl_c(x0, lmask), y1 = shfl_c(x1, lmask);
+        if (!ok || (i & rneed) != rneed) continue;
+        v[i] = cmad(m[3], y1, cmad(m[2], y0, cmad(m[1], x1, cmul(m[0], x0))));
+        v[i | (1 << JB)] = cmad(m[7], y1, cmad(m[6], y0, cmad(m[5], x1, cmul(m[4], x0))));
+    }
+}
+
 // Global index of register 0 of this thread in phase P.
 template <int W>
 __device__ __forceinline__ uint64_t thread_base(const Phase &P, uint64_t tile_base, int lane, int warp) {
@@ -246,7 +268,8 @@ if (mask & (1 << J)) {                                                          
     // controls on lane / warp / tile qubits: one test per thread (a lane
     // gate still takes part in the shuffles when its controls are not met)
     const bool tok = (base & op.tmask) == op.tmask;
-    if (!tok && !(type == SOP_U1 && op.a < POS_REG)) return;
+    const bool on_lanes = op.a < POS_REG || (type == SOP_U2 && op.b < POS_REG);
+    if (!tok && !((type == SOP_U1 || type == SOP_U2) && on_lanes)) return;
     const int rneed = op.rneed;
     if (type == SOP_U1) {
         const C m00 = src.pool(op.moff), m01 = src.pool(op.moff + 1);
@@ -280,6 +303,39 @@ if (mask & (1 << J)) {                                                          
                         if (tok && (j & rneed) == rneed) x[j] = cmad(co, other, cmul(cs, x[j]));
                     }
                 }
+            }
+        }
+    } else if (type == SOP_U2 && on_lanes && (op.a >= POS_REG || op.b >= POS_REG)) {
+        // one lane and one register target: the host stores the 8 coefficients
+        // of lane-bit value 0, then those of value 1
+        const int la = op.a < POS_REG ? op.a : op.b;
+        const int rb = (op.a < POS_REG ? op.b : op.a) - POS_REG;
+        const int off = op.moff + 8 * ((lane >> la) & 1);
+        C m[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m[e] = src.pool(off + e);
+#pragma unroll
+        QSIM_EACH(s, x) {
+            switch (rb) {
+                case 0: u2_lane_reg<C, 0>(x, m, 1 << la, tok, rneed); break;
+                case 1: u2_lane_reg<C, 1>(x, m, 1 << la, tok, rneed); break;
+                case 2: u2_lane_reg<C, 2>(x, m, 1 << la, tok, rneed); break;
+                default: u2_lane_reg<C, 3>(x, m, 1 << la, tok, rneed); break;
+            }
+        }
+    } else if (type == SOP_U2 && on_lanes) {
+        // two lane targets: each amplitude takes its own value and those of
+        // the lanes across bit a, bit b and both, with the 4 coefficients
+        // the host stored for this lane's (bit a, bit b) values
+        const int ma = 1 << op.a, mb = 1 << op.b;
+        const int off = op.moff + 4 * ((((lane >> op.a) & 1) << 1) | ((lane >> op.b) & 1));
+        const C m0 = src.pool(off), m1 = src.pool(off + 1), m2 = src.pool(off + 2), m3 = src.pool(off + 3);
+#pragma unroll
+        QSIM_EACH(s, x) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const C p1 = shfl_c(x[j], ma), p2 = shfl_c(x[j], mb), p3 = shfl_c(x[j], ma | mb);
+                if (tok && (j & rneed) == rneed) x[j] = cmad(m3, p3, cmad(m2, p2, cmad(m1, p1, cmul(m0, x[j]))));
             }
         }
     } else if (type == SOP_U2) {

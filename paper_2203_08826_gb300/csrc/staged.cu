@@ -191,6 +191,35 @@ void batch_ops(Stage &st) {
     st.pool.swap(pool);
 }
 
+// Coefficients of a dense 4x4 U (row-major, index (bit A << 1) | bit B, A =
+// the first target) with a target on a lane, in the order the kernel reads
+// them (each thread holds its own amplitudes and gets its partner lanes' by
+// shuffle):
+//   one lane target: for lane-bit value beta = 0, 1 and the thread's output
+//     register value r = 0, 1: the coefficients of (own, register 0), (own,
+//     register 1), (partner, register 0), (partner, register 1);
+//   two lane targets: for the lane's values (bit A, bit B) = 00, 01, 10, 11:
+//     the coefficients of its own amplitude and of the lanes across bit A,
+//     across bit B and across both.
+static std::vector<cd> lane_u2_layout(const std::vector<cd> &U, bool lane_a, bool lane_b) {
+    std::vector<cd> out;
+    out.reserve(16);
+    if (lane_a && lane_b) {
+        for (int r = 0; r < 4; ++r)
+            for (int flip : {0, 2, 1, 3}) out.push_back(U[size_t(r * 4 + (r ^ flip))]);
+        return out;
+    }
+    // idx(beta, rho): matrix index of lane-bit value beta and register-bit value rho
+    auto idx = [&](int beta, int rho) { return lane_a ? (beta << 1) | rho : (rho << 1) | beta; };
+    for (int beta = 0; beta < 2; ++beta)
+        for (int rho = 0; rho < 2; ++rho) {
+            const int row = idx(beta, rho);
+            for (int c : {idx(beta, 0), idx(beta, 1), idx(1 - beta, 0), idx(1 - beta, 1)})
+                out.push_back(U[size_t(row * 4 + c)]);
+        }
+    return out;
+}
+
 // Build the op list of one tile stage from its gates (circuit order).
 // Returns QSIM_EUNSUPPORTED (without error text) when the stage outgrows the
 // parameter-block limits; the caller then splits it.
@@ -391,6 +420,11 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
             so.type = SOP_U2;
             so.a = int8_t(pos_of(g.op.targets[0]));
             so.b = int8_t(pos_of(g.op.targets[1]));
+            if (so.a < POS_REG || so.b < POS_REG) {
+                so.moff = add_pool(lane_u2_layout(g.op.m, so.a < POS_REG, so.b < POS_REG));
+                st.ops.push_back(so);
+                continue;
+            }
         }
         so.moff = add_pool(g.op.m);
         st.ops.push_back(so);
@@ -432,15 +466,19 @@ double stage_flops_per_amp(const qsim_circuit &c, const Stage &st) {
     return f;
 }
 
-// Pair fusion before staging: a 2-qubit gate on qubits a, b (both outside
-// the lanes) absorbs the uncontrolled 1-qubit gates just before it on a and
-// on b and just after it on a and on b (each the neighbour of the 2-qubit gate
-// on its qubit, so moving it next to the gate crosses only gates it commutes
-// with), when at least three of the four exist: U = (Ha x Hb) M (Ga x Gb) is
-// one dense 4x4 at the 2-qubit gate's place.  Applied to a register pair that
-// costs 16 multiply-adds per amplitude instead of 8 per absorbed gate.  Gates
-// are taken greedily in circuit order, each 1-qubit gate absorbed at most
-// once.  src[i] lists the source gates of fused gate i in the order they act.
+// Pair fusion before staging: an uncontrolled 2-qubit gate M on qubits a, b
+// absorbs the run of uncontrolled 1-qubit gates just before it on a (every
+// gate on a between the previous multi-qubit gate on a and M), the same run
+// on b, and the runs just after it on a and on b.  Each run touches only its
+// own qubit, so moving it next to M crosses only gates it commutes with, and
+// its product is one 2x2: U = (Ha x Hb) M (Ga x Gb) is one dense 4x4 at M's
+// place.  A 4x4 costs 16 multiply-adds per amplitude, a 1-qubit op 8, and a
+// 1-qubit diagonal merges into a neighbouring 1-qubit op for nothing; so M is
+// fused only when at least three of its four runs hold a non-diagonal gate.
+// Gates are taken greedily in circuit order, each 1-qubit gate absorbed at
+// most once.  src[i] lists the source gates of fused gate i in an order that
+// applies them correctly (the runs before M in circuit order, M, the runs
+// after M in circuit order).
 static void pair_fuse(const qsim_circuit &c, std::vector<GateRec> &gates, std::vector<std::vector<int>> &src) {
     const size_t G = c.gates.size();
     auto touches = [&](size_t i, int q) {
@@ -455,46 +493,59 @@ static void pair_fuse(const qsim_circuit &c, std::vector<GateRec> &gates, std::v
         const GateRec &g = c.gates[i];
         return g.k == 1 && g.nc == 0 && g.grad_slot < 0;
     };
+    auto diagonal = [&](size_t i) { return c.gates[i].m[1] == cd(0.0) && c.gates[i].m[2] == cd(0.0); };
+    const std::vector<cd> I2 = {1.0, 0.0, 0.0, 1.0};
     std::vector<char> absorbed(G, 0);
-    std::vector<std::vector<int>> parts(G);  // fused 2-qubit gate -> [Ga, Gb, itself, Ha, Hb] present
+    std::vector<std::vector<int>> parts(G);  // fused 2-qubit gate -> its source gates
     std::vector<std::vector<cd>> fusedm(G);
     for (size_t i = 0; i < G; ++i) {
         const GateRec &g = c.gates[i];
-        if (g.k != 2 || g.nc != 0 || g.grad_slot >= 0 || g.targets[0] < LANE_BITS || g.targets[1] < LANE_BITS)
-            continue;
-        int prev[2] = {-1, -1}, next[2] = {-1, -1};
+        if (g.k != 2 || g.nc != 0 || g.grad_slot >= 0) continue;
+        std::vector<int> prev[2], next[2];  // circuit order
+        int have = 0;
         for (int t = 0; t < 2; ++t) {
             const int q = g.targets[t];
-            for (size_t j = i; j-- > 0;)
-                if (touches(j, q)) {
-                    if (plain1(j) && !absorbed[j] && parts[j].empty()) prev[t] = int(j);
-                    break;
-                }
-            for (size_t j = i + 1; j < G; ++j)
-                if (touches(j, q)) {
-                    if (plain1(j)) next[t] = int(j);
-                    break;
-                }
+            for (size_t j = i; j-- > 0;) {
+                if (!touches(j, q)) continue;
+                if (!plain1(j) || absorbed[j]) break;
+                prev[t].insert(prev[t].begin(), int(j));
+            }
+            for (size_t j = i + 1; j < G; ++j) {
+                if (!touches(j, q)) continue;
+                if (!plain1(j)) break;
+                next[t].push_back(int(j));
+            }
+            for (const std::vector<int> *run : {&prev[t], &next[t]}) {
+                bool dense = false;
+                for (int j : *run) dense |= !diagonal(size_t(j));
+                have += dense;
+            }
         }
-        const int have = (prev[0] >= 0) + (prev[1] >= 0) + (next[0] >= 0) + (next[1] >= 0);
         if (have < 3) continue;
-        auto one = [&](int j) { return j >= 0 ? c.gates[size_t(j)].m : std::vector<cd>{1.0, 0.0, 0.0, 1.0}; };
+        auto product = [&](const std::vector<int> &run) {  // later gates on the left
+            std::vector<cd> P = I2;
+            for (int j : run) P = matmul(c.gates[size_t(j)].m, P, 2);
+            return P;
+        };
         auto kron = [](const std::vector<cd> &A, const std::vector<cd> &B) {  // A on the MSB
             std::vector<cd> K(16);
             for (int r = 0; r < 4; ++r)
                 for (int q = 0; q < 4; ++q) K[size_t(r * 4 + q)] = A[size_t((r >> 1) * 2 + (q >> 1))] * B[size_t((r & 1) * 2 + (q & 1))];
             return K;
         };
-        std::vector<cd> U = matmul(g.m, kron(one(prev[0]), one(prev[1])), 4);
-        U = matmul(kron(one(next[0]), one(next[1])), U, 4);
+        std::vector<cd> U = matmul(g.m, kron(product(prev[0]), product(prev[1])), 4);
+        U = matmul(kron(product(next[0]), product(next[1])), U, 4);
         fusedm[i] = U;
-        for (int j : {prev[0], prev[1]})
-            if (j >= 0) parts[i].push_back(j);
+        std::vector<int> before(prev[0]), after(next[0]);
+        before.insert(before.end(), prev[1].begin(), prev[1].end());
+        after.insert(after.end(), next[1].begin(), next[1].end());
+        std::sort(before.begin(), before.end());
+        std::sort(after.begin(), after.end());
+        parts[i] = before;
         parts[i].push_back(int(i));
-        for (int j : {next[0], next[1]})
-            if (j >= 0) parts[i].push_back(j);
-        for (int j : {prev[0], prev[1], next[0], next[1]})
-            if (j >= 0) absorbed[size_t(j)] = 1;
+        parts[i].insert(parts[i].end(), after.begin(), after.end());
+        for (const std::vector<int> &run : {prev[0], prev[1], next[0], next[1]})
+            for (int j : run) absorbed[size_t(j)] = 1;
     }
     gates.clear();
     src.clear();
@@ -567,10 +618,8 @@ int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stag
                 for (size_t r = 0; r < d; ++r) op.m[r * d + op.perm[r]] = op.phase[r];
                 op.type = Op::DENSE;
             }
-            bool lane_target = false;
-            for (int t = 0; t < op.k; ++t) lane_target |= op.targets[t] < LANE_BITS;
             if (op.k == 1) cls[i].kind = GateClass::DENSE1;
-            else if (op.k == 2 && !lane_target) cls[i].kind = GateClass::DENSE2;
+            else if (op.k == 2) cls[i].kind = GateClass::DENSE2;
             else cls[i].kind = GateClass::OTHER;
         }
     }

@@ -73,6 +73,49 @@ def test_staged_matches_oracle(q, orc, dtype, kmax, maker):
     assert err <= TOL[dtype], f"staged {maker} {dtype} kmax={kmax}: {err:.3e}"
 
 
+def lane_pair_circuit(n, seed, depth=4):
+    """Dense 2-qubit gates with targets on lane qubits (0..4): lane + lane,
+    lane + tile qubit in both orders, uncontrolled and with controls on lane,
+    tile and high qubits; 1-qubit gates around CZs on lane qubits, which the
+    planner fuses into 4x4 blocks."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    dense = lambda: inputs.random_dense_gate(rng, 2)
+    for _ in range(depth):
+        for q_ in range(n):
+            gates.append(inputs.Gate("su2", (q_,), (), inputs.haar_su2_quaternion(rng)))
+        la, lb = (int(v) for v in rng.choice(5, 2, replace=False))
+        hi = int(rng.integers(5, n))
+        gates.append(inputs.Gate("cz", (la, hi)))
+        gates.append(inputs.Gate("cz", (int(rng.integers(5, n)), lb)))
+        for q_ in (la, lb, hi):
+            gates.append(inputs.Gate("su2", (q_,), (), inputs.haar_su2_quaternion(rng)))
+        gates.append(inputs.Gate("matrix", (la, lb), (), (), -1, dense()))
+        gates.append(inputs.Gate("matrix", (la, hi), (), (), -1, dense()))
+        gates.append(inputs.Gate("matrix", (hi, lb), (), (), -1, dense()))
+        others = [int(v) for v in rng.permutation(n) if v not in (la, lb, hi)]
+        gates.append(inputs.Gate("matrix", (la, lb), (others[0],), (), -1, dense()))
+        gates.append(inputs.Gate("matrix", (hi, la), (others[1], others[2]), (), -1, dense()))
+        gates.append(inputs.Gate("swap", (lb, la)))
+        gates.append(inputs.Gate("swap", (la, int(rng.integers(5, n)))))
+    return inputs.Circuit(n, gates, "lane pairs")
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("kmax", [1, 3, 4])
+@pytest.mark.parametrize("n", [10, 14, 17])
+def test_staged_two_qubit_gates_on_lanes(q, orc, dtype, kmax, n):
+    """4x4 ops with one or two targets among the lane qubits (partner
+    amplitudes by shuffle, coefficients laid out per lane-bit value), with
+    controls on lanes, registers and tile qubits, against the oracle."""
+    circ = lane_pair_circuit(n, seed=n + kmax)
+    psi0 = inputs.gaussian_state(n, seed=3)
+    want = orc.simulate(circ, psi0)
+    got = run_plan(q, circ, dtype, psi0, q.FUSE_STAGED, kmax)
+    err = np.max(np.abs(got - want))
+    assert err <= TOL[dtype], f"lane pairs n={n} {dtype} kmax={kmax}: {err:.3e}"
+
+
 @pytest.mark.parametrize("n", [5, 9, 10, 12])
 def test_staged_small_widths(q, orc, n):
     """n < 9 falls back to the greedy plan; n = 9..12 uses tiles with fewer warps."""

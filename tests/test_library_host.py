@@ -204,6 +204,18 @@ def test_staged_plan_schedule_replays_the_circuit(q, orc, maker, kmax):
                 assert set(circ.gates[gi].targets) <= tile, (gi, circ.gates[gi])
 
 
+def test_pair_fusion_absorbs_the_random_circuits_one_qubit_gates(q):
+    """Pair fusion on the 30-qubit depth-20 random circuit: 150 of its 300 CZ
+    (lane qubits included) become dense 4x4 ops that take in all 600
+    1-qubit gates, so no stage applies a 1-qubit op; the rest stay sign
+    flips."""
+    import re
+    d = q.Plan(inputs.random_circuit(30, 20, seed=2022), kmax=3, mode=q.FUSE_STAGED).describe()
+    count = lambda key: sum(int(x) for x in re.findall(key + r"=(\d+)", d))
+    assert count("u2") == 150
+    assert count("u1") == 0 and count("reg") == 0 and count("lane") == 0
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
