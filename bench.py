@@ -329,7 +329,27 @@ def run_reference(args, ws, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
-PLAN_KMAX = {"greedy2": 2, "staged": 4, "tc": 6}
+PLAN_KMAX = {"greedy2": 2, "staged": 4, "tc": 6, "staged-spec": 3}
+
+
+def add_circuit_flops(roof, plan):
+    """For a staged plan: the same launches counted with the flops of the
+    circuit's gates applied one sweep each (what the fused plan replaces)."""
+    if not roof or roof.get("bound") != "alu" or plan is None:
+        return
+    try:
+        fl = plan.flops()
+    except Exception:
+        return
+    if fl["executed"] > 0:
+        r = fl["circuit"] / fl["executed"]
+        roof["circuit_flops_per_executed"] = round(r, 4)
+        roof["circuit_equiv_tflops"] = round(roof["achieved"] * r, 2)
+
+
+def mode_name(q, mode: int) -> str:
+    return {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc",
+            q.FUSE_STAGED | q.SPECIALIZE: "staged-spec"}[mode]
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -362,8 +382,8 @@ def roofline_of(prof, peak_gbs, peak_src, sm_max_mhz, n_qubits=N_QUBITS, amp_byt
         r = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk, 1), "unit": "TFLOP/s",
              "frac": round(tf / pk, 4), "traffic": traffic_of(name, n_qubits, amp_bytes),
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-             "flops_basis": "the circuit's gates, one sweep each (16 per amplitude per dense 1-qubit gate); "
-                            "fused 4x4 blocks execute fewer",
+             "flops_basis": "flops the stage ops execute (8 per complex multiply-add: 32 per amplitude for a "
+                            "fused 4x4, 16 for a 1-qubit gate)",
              "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4),
              "hbm_frac_of_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
     else:
@@ -401,7 +421,8 @@ def run_qsim(args, ws, rank, local):
     ham = inputs.zz_chain(n)
     st = torch.cuda.current_stream()
     state = q.State(n, args.dtype)
-    mode_ids = {"greedy2": q.FUSE_GREEDY2, "staged": q.FUSE_STAGED, "tc": q.FUSE_TC}
+    mode_ids = {"greedy2": q.FUSE_GREEDY2, "staged": q.FUSE_STAGED, "tc": q.FUSE_TC,
+                "staged-spec": q.FUSE_STAGED | q.SPECIALIZE}
     plans = {}
     for name, mode in mode_ids.items():
         if name == "tc" and args.dtype != "c64":
@@ -418,7 +439,7 @@ def run_qsim(args, ws, rank, local):
         # the library's autotuner times its candidate plans on this state (not in the timed region)
         t0 = time.perf_counter()
         tuned = q.Plan.autotune(qc, state, reps=1, max_err=args.max_err)
-        chosen = {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc"}[tuned.mode]
+        chosen = mode_name(q, tuned.mode)
         kmax_chosen = tuned.kmax
         plans[chosen] = tuned
         tune = {"mode": chosen, "kmax": tuned.kmax, "ms_per_circuit": tuned.tuned_ms,
@@ -473,6 +494,7 @@ def run_qsim(args, ws, rank, local):
     peak, peak_src = peaks()
     ab = 8 if args.dtype == "c64" else 16
     roof = roofline_of(prof, peak, peak_src, clocks.get("sm_max_mhz") or 2070.0, n, ab)
+    add_circuit_flops(roof, plans.get(chosen))
 
     # ---- the same circuit through the other execution modes
     others = {}
@@ -606,7 +628,7 @@ def run_qsim(args, ws, rank, local):
             "dtype": "f32" if args.dtype == "c64" else "f64", "data": "synthetic",
             "config": dict(workload_config(n), gates=ngates, state=args.dtype, mode=chosen, kmax=kmax_chosen,
                            autotune=tune, l2="inputs larger than L2 (state >= 8 GiB vs 129 MB L2)",
-                           err_vs_oracle=accuracy),
+                           err_vs_oracle=accuracy, specialized_kernels=q.spec_stats()),
             "s_per_circuit": ms / 1e3 / args.steps,
             "gpu_launches": launches,
             "roofline": roof, "kernels": prof, "other_modes": others, "e2e": e2e, "cpu_baseline": cpu,
@@ -726,8 +748,7 @@ def other_workloads(q, torch, peak, peak_src):
     amp_ok = [e for e in tuned.table if e["ms"] > 0 and 0 <= e["max_abs"] <= 1e-5]
     amp_best = min(amp_ok, key=lambda e: e["ms"]) if amp_ok else None
     res["autotune"] = {"max_err": 1e-5, "chosen": {"mode": tuned.table and
-                                                    {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged",
-                                                     q.FUSE_TC: "tc"}[tuned.mode], "kmax": tuned.kmax,
+                                                    mode_name(q, tuned.mode), "kmax": tuned.kmax,
                                                     "nfp32": tuned.nfp32},
                        "fastest_within_amplitude_bound_1e-5": amp_best,
                        "table": tuned.table}
@@ -791,7 +812,7 @@ def other_workloads(q, torch, peak, peak_src):
     out["adiabatic_tfim30_c64"] = {
         "fused": {"s_per_evolution": ms_f / 1e3, "s_per_trotter_step": ms_f / 1e3 / nsteps,
                   "gates_per_s": len(c) / (ms_f / 1e3),
-                  "mode": {q.FUSE_GREEDY2: "greedy2", q.FUSE_STAGED: "staged", q.FUSE_TC: "tc"}[tuned.mode],
+                  "mode": mode_name(q, tuned.mode),
                   "kmax": tuned.kmax, "autotune_table": tuned.table,
                   "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
         "plain": {"s_per_evolution": ms_p / 1e3, "gates_per_s": len(c) / (ms_p / 1e3)},
@@ -831,7 +852,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="qsim", choices=["qsim", "reference"])
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "greedy2", "staged", "tc"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "greedy2", "staged", "staged-spec", "tc"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)

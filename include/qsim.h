@@ -195,11 +195,36 @@ typedef struct qsim_plan qsim_plan;
  * for QSIM_FUSE_STAGED the tile's warp qubits (at most 4); for QSIM_FUSE_TC
  * the window width as above.  The plan copies what it needs from the circuit;
  * it does not depend on the circuit afterwards.
- * Citation: Sec. 3.2 (gate fusion; fusing up to about five qubits may help). */
+ * QSIM_PLAN_SPECIALIZE may be ORed into QSIM_FUSE_STAGED: the same stages,
+ * but each tile stage runs as a kernel written out for its own op list (every
+ * position, mask and coefficient offset a constant) and compiled with NVRTC
+ * for sm_103a when the plan first runs on a dtype; the coefficients are
+ * kernel parameters, so circuits of the same structure with other angles
+ * reuse the compiled code (an in-process cache keyed by the source).  The
+ * first run pays the compile (about a second per few stages, in parallel
+ * threads); QSIM_ECUDA with the compiler's log if it fails.  qsim_plan_info
+ * reports the flag in *mode.
+ * Citation: Sec. 3.2 (gate fusion; fusing up to about five qubits may help);
+ * the paper compiles its own kernels at run time as well (Sec. 2). */
 #define QSIM_FUSE_GREEDY2 0
 #define QSIM_FUSE_STAGED 1
 #define QSIM_FUSE_TC 2
+#define QSIM_PLAN_SPECIALIZE 0x100
 QSIM_API int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out);
+/* Arithmetic of a staged plan per amplitude of the state: the flops its
+ * stages execute (a complex multiply-add is 8 flops; a fused 4x4 on a pair
+ * costs 32, a 1-qubit gate 16) and those of the circuit's gates applied one
+ * sweep each (what the plan replaces).  Host-only; QSIM_EINVAL for other
+ * plans.  The library profiler counts the executed flops. */
+QSIM_API int qsim_plan_flops(const qsim_plan *p, double *executed, double *circuit);
+/* Specialised stage kernels compiled since the library was loaded: seconds
+ * spent in the compiler, programs compiled, programs found in the cache. */
+QSIM_API int qsim_spec_stats(double *compile_s, uint64_t *compiles, uint64_t *cache_hits);
+/* CUDA source of the specialised kernels of a staged plan's tile stages
+ * (one kernel per stage, `qsim_spec_stage_<i>`) for dtype, NUL-terminated
+ * and truncated to len bytes; *needed receives the full length + 1.
+ * Host-only (works on any staged plan, specialised or not). */
+QSIM_API int qsim_plan_source(const qsim_plan *p, int dtype, char *buf, size_t len, size_t *needed);
 QSIM_API int qsim_plan_destroy(qsim_plan *p);
 /* Number of sweeps (HBM passes) and of source gates the plan covers. */
 QSIM_API int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode);

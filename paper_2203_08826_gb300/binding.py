@@ -24,6 +24,7 @@ LIB_PATH = (os.path.join(_HERE, "_build_debug", "libqsim_debug.so") if os.enviro
 
 C64, C128 = 0, 1
 FUSE_GREEDY2, FUSE_STAGED, FUSE_TC = 0, 1, 2
+SPECIALIZE = 0x100  # ORed into FUSE_STAGED: stage kernels compiled for the plan
 PREC_BF16X3, PREC_TF32X3, PREC_FP32 = 0, 1, 2
 INIT_ZERO, INIT_BASIS, INIT_HOST, INIT_DEVICE, INIT_NULL = 0, 1, 2, 3, 4
 SLICE_SEGMENT, SLICE_SWAP = 0, 1
@@ -65,6 +66,9 @@ _SIGS = {
     "qsim_plan_info": ([P, P, P, P], I),
     "qsim_plan_block": ([P, I, P, P, P], I),
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
+    "qsim_plan_source": ([P, I, P, ctypes.c_size_t, P], I),
+    "qsim_spec_stats": ([P, P, P], I),
+    "qsim_plan_flops": ([P, P, P], I),
     "qsim_plan_tc_pass": ([P, I, P, P, P, P, P, P, P], I),
     "qsim_plan_tc_epilogue": ([P, I, I, P, P, P, P, P], I),
     "qsim_plan_stage": ([P, I, P, P, P, P, P], I),
@@ -256,7 +260,8 @@ class Plan:
             self.n, self.handle = qc.n, h
             _check(lib().qsim_plan_info(h, *[ctypes.byref(x) for x in info]))
             self.mode = info[2].value
-            names = {FUSE_GREEDY2: "greedy2", FUSE_STAGED: "staged", FUSE_TC: "tc"}
+            names = {FUSE_GREEDY2: "greedy2", FUSE_STAGED: "staged", FUSE_TC: "tc",
+                     FUSE_STAGED | SPECIALIZE: "staged-spec"}
             self.table = [{"mode": names.get(e.mode, e.mode), "kmax": e.kmax, "ms": e.ms, "err": e.err,
                            "max_abs": e.max_abs, "ref": "fp64" if e.ref else "first candidate",
                            "npasses": e.npasses, "nfp32": e.nfp32} for e in tab[: nt.value]]
@@ -292,6 +297,22 @@ class Plan:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().qsim_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"sweeps": a.value, "gates": b.value, "mode": c.value}
+
+    def flops(self) -> dict:
+        """Flops per amplitude: executed by the staged plan's ops, and of the
+        circuit's gates one sweep each."""
+        e, c = ctypes.c_double(), ctypes.c_double()
+        _check(lib().qsim_plan_flops(self.handle, ctypes.byref(e), ctypes.byref(c)))
+        return {"executed": e.value, "circuit": c.value}
+
+    def source(self, dtype: str = "c64") -> str:
+        """CUDA source of the plan's specialised stage kernels (staged plans)."""
+        need = ctypes.c_size_t()
+        dt = C64 if dtype == "c64" else C128
+        _check(lib().qsim_plan_source(self.handle, dt, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().qsim_plan_source(self.handle, dt, buf, need.value, None))
+        return buf.value.decode()
 
     def describe(self) -> str:
         buf = ctypes.create_string_buffer(1 << 20)
@@ -655,6 +676,14 @@ def profile_read() -> dict:
             out[name.value.decode()] = {"launches": l.value, "ms": ms.value, "bytes": by.value,
                                         "flops": fl.value}
     return out
+
+
+def spec_stats() -> dict:
+    """Specialised stage kernels compiled in this process: seconds in the
+    compiler, programs compiled, programs found in the cache."""
+    t, n, h = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().qsim_spec_stats(ctypes.byref(t), ctypes.byref(n), ctypes.byref(h)))
+    return {"compile_s": t.value, "compiles": n.value, "cache_hits": h.value}
 
 
 def launch_count() -> int:

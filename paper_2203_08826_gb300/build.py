@@ -5,7 +5,8 @@ objects are linked into ``_build/libqsim.so``.  Rebuilds only what changed.
 ``build(debug=True)`` builds the same sources with ``-DQSIM_DEBUG`` (index
 bound checks in the sweeps and staged tiles) into
 ``_build_debug/libqsim_debug.so``; the binding loads it when
-``QSIM_LIBRARY=debug``.
+``QSIM_LIBRARY=debug``.  The library links NVRTC, with which it compiles
+the stage kernels of specialised plans at run time.
 """
 from __future__ import annotations
 
@@ -37,7 +38,8 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+          + glob.glob(os.path.join(INCLUDE, "*.h")))
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
@@ -70,7 +72,9 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if (not os.path.exists(lib) or force
             or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(lib)):
         tmp = lib + f".{os.getpid()}.tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        # NVRTC compiles the specialised stage kernels at run time
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker", f"-rpath={cuda_lib}"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

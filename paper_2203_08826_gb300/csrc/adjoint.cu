@@ -821,7 +821,7 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
             // useful flops: the stage's gates on both states, 6 FMAs per
             // amplitude for each gradient op's three sums
             LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2),
-                           (2.0 * stage::stage_flops_per_amp(bwd, sg) + 12.0 * sg.ngradops) * double(N));
+                           (2.0 * stage::stage_exec_flops_per_amp(sg) + 12.0 * sg.ngradops) * double(N));
             k_adj_stage<DUAL_W><<<unsigned(ntiles), 32 << DUAL_W, smem, st>>>(psi, lam, dp, partial);
             QSIM_CUDA_TRY(cudaGetLastError(), "adjoint stage launch");
         }

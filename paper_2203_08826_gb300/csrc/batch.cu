@@ -283,7 +283,7 @@ int pack(qsim_batch &b, int W) {
         BCirc bc{c.n, int(pk.stages.size()), int(st.size()), 0};
         for (const stage::Stage &s : st) {
             if (s.plain) return set_error(QSIM_EUNSUPPORTED, "batch circuits need gates of at most 2 targets");
-            pk.flops += stage::stage_flops_per_amp(c, s) * double(uint64_t(1) << c.n);
+            pk.flops += stage::stage_exec_flops_per_amp(s) * double(uint64_t(1) << c.n);
             BStage bs{};
             int tq[LANE_BITS + MAX_SLOTS];
             int nt = 0;

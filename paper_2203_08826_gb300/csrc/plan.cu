@@ -186,6 +186,10 @@ int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out) 
     *out = nullptr;
     if (kmax < 1 || kmax > QSIM_MAX_TARGETS) return set_error(QSIM_EINVAL, "kmax=%d outside 1..6", kmax);
     if (c->n > 34) return set_error(QSIM_EINVAL, "plans act on states of at most 34 qubits (circuit has %d)", c->n);
+    const bool specialize = (mode & QSIM_PLAN_SPECIALIZE) != 0;
+    mode &= ~QSIM_PLAN_SPECIALIZE;
+    if (specialize && mode != QSIM_FUSE_STAGED)
+        return set_error(QSIM_EINVAL, "QSIM_PLAN_SPECIALIZE applies to staged plans only");
     qsim_plan *p = new qsim_plan();
     p->n = c->n;
     p->mode = mode;
@@ -198,6 +202,7 @@ int qsim_plan_build(const qsim_circuit *c, int kmax, int mode, qsim_plan **out) 
         case QSIM_FUSE_TC: rc = build_tc(*c, *p); break;
         default: rc = set_error(QSIM_EINVAL, "unknown fusion mode %d", mode);
     }
+    if (rc == QSIM_OK && specialize) staged_set_specialized(*p);
     if (rc != QSIM_OK) {
         delete p;
         return rc;
@@ -215,7 +220,7 @@ int qsim_plan_info(const qsim_plan *p, int *nsweeps, int *ngates, int *mode) {
     if (!p) return set_error(QSIM_EINVAL, "plan is NULL");
     if (nsweeps) *nsweeps = p->nsweeps();
     if (ngates) *ngates = p->ngates;
-    if (mode) *mode = p->mode;
+    if (mode) *mode = p->mode | (staged_specialized(*p) ? QSIM_PLAN_SPECIALIZE : 0);
     return QSIM_OK;
 }
 
@@ -284,6 +289,12 @@ static int autotune_impl(const qsim_circuit *c, qsim_state *s, int reps, double 
         int fp32;  // tensor-core plans: -1 every pass at the window's split, -2 every pass in FP32, k >= 0: k passes in FP32
     };
     std::vector<Cand> cands = {{QSIM_FUSE_STAGED, 3, -1}, {QSIM_FUSE_STAGED, 4, -1}};
+    if (c->n >= SPECIALIZE_MIN_QUBITS) {
+        // stage kernels compiled for the plan: worth their compile time on
+        // large states only
+        cands.push_back({QSIM_FUSE_STAGED | QSIM_PLAN_SPECIALIZE, 3, -1});
+        cands.push_back({QSIM_FUSE_STAGED | QSIM_PLAN_SPECIALIZE, 4, -1});
+    }
     if (s->dtype == QSIM_C64) {
         cands.push_back({QSIM_FUSE_TC, 6, -1});
         cands.push_back({QSIM_FUSE_TC, 5, -1});

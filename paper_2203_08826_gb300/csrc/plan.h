@@ -71,6 +71,10 @@ namespace qsim {
 int build_greedy2(const qsim_circuit &c, qsim_plan &p);
 int build_staged(const qsim_circuit &c, qsim_plan &p);
 int run_staged(qsim_state *s, qsim_plan &p);
+// staged plans whose tile stages run as kernels compiled for the plan
+void staged_set_specialized(qsim_plan &p);
+bool staged_specialized(const qsim_plan &p);
+constexpr int SPECIALIZE_MIN_QUBITS = 20;  // the autotuner's specialised candidates
 int staged_nsweeps(const qsim_plan &p);
 void staged_describe(const qsim_plan &p, std::string &out);
 void tc_describe(const qsim_plan &p, std::string &out);

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstring>
+#include <memory>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -579,9 +581,10 @@ struct Stage {
     std::vector<int> gates;  // source gates the stage applies, in schedule order (before merging / batching)
 };
 
-// algorithmic flops per amplitude of a planned stage: those of the circuit's
-// gates it applies, one sweep each (host)
+// flops per amplitude of a planned stage (host): those of the circuit's gates
+// it applies, one sweep each; and those its ops execute after fusion
 double stage_flops_per_amp(const qsim_circuit &c, const Stage &st);
+double stage_exec_flops_per_amp(const Stage &st);
 // Split a circuit into stages for tiles of 2^(9 + W) amplitudes (after pair
 // fusion, when the circuit has no gradient markers).  With `limits` the op,
 // phase and pool counts of a stage stay within one kernel parameter block.
@@ -607,4 +610,38 @@ template <typename C> inline void make_params(const Stage &st, StageParams<C> &p
 }
 
 }  // namespace stage
+
+struct SpecLib;  // specialize.cu
+// A staged plan: its stages, the interpreter's parameter blocks per dtype
+// and, for specialised plans (QSIM_PLAN_SPECIALIZE), the compiled stage
+// kernels with their coefficient blocks.
+struct StagedPlan {
+    int W = 4;
+    bool specialized = false;
+    std::vector<stage::Stage> stages;
+    struct Dev {
+        bool ready = false;
+        std::vector<void *> plain_mats;
+        std::vector<unsigned char> params;  // packed StageParams per tile stage
+        std::vector<size_t> param_off;
+    } dev[2];
+    struct Spec {
+        bool ready = false;
+        std::vector<std::shared_ptr<SpecLib>> libs;     // compiled groups of stages
+        std::vector<cudaKernel_t> kern;                  // per stage (plain stages: null)
+        std::vector<std::vector<unsigned char>> params;  // per stage coefficient block
+    } spec[2];
+    std::vector<double> flops_per_amp;   // flops per amplitude each stage executes
+    double circuit_flops_per_amp = 0.0;  // the circuit's gates, one sweep each, summed
+    ~StagedPlan() {
+        for (Dev &d : dev)
+            for (void *m : d.plain_mats)
+                if (m) cudaFree(m);
+    }
+};
+// specialize.cu: compile (or find cached) the kernels of every tile stage
+// for one dtype; launch tile stage i on psi
+int spec_prepare(StagedPlan &sp, int dtype);
+int spec_launch(StagedPlan &sp, int dtype, size_t i, void *psi, int n, cudaStream_t s);
+std::string spec_source(const StagedPlan &sp, int dtype, size_t i0, size_t i1);
 }  // namespace qsim

@@ -446,6 +446,22 @@ int emit_stage_ops(Stage &st, const std::vector<const GateClass *> &gates, int W
 // per amplitude it touches, none when every factor is +-1 or 1).  Fused
 // 4x4 blocks and merged diagonals do fewer flops than this; the count is
 // the workload's, not the plan's.
+// Flops per amplitude a stage's ops execute (a complex multiply-add is 8
+// flops; a controlled op counts for the fraction of amplitudes it touches;
+// sign flips and exchanges none): the work of the plan as fused.
+double stage_exec_flops_per_amp(const Stage &st) {
+    if (st.plain) return st.op.type == Op::DENSE ? 8.0 * double(1 << st.op.k) / double(1ull << st.op.c) : 0.0;
+    double f = 0;
+    for (const StageOp &o : st.ops) {
+        const double frac = 1.0 / double(1ull << (__builtin_popcountll(o.tmask) + __builtin_popcount(o.rneed)));
+        if (o.type == SOP_U1) f += 16.0 * frac;
+        else if (o.type == SOP_U1R || o.type == SOP_U1L) f += 16.0 * __builtin_popcount(unsigned(o.a));
+        else if (o.type == SOP_U2) f += 32.0 * frac;
+        else if (o.type == SOP_DIAG && !(o.flags & 1)) f += 6.0 * frac;
+    }
+    return f;
+}
+
 double stage_flops_per_amp(const qsim_circuit &c, const Stage &st) {
     double f = 0;
     for (int gi : st.gates) {
@@ -707,23 +723,6 @@ int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stag
 
 using namespace stage;
 
-struct StagedPlan {
-    int W = 4;
-    std::vector<Stage> stages;
-    struct Dev {
-        bool ready = false;
-        std::vector<void *> plain_mats;
-        std::vector<unsigned char> params;  // packed StageParams per tile stage
-        std::vector<size_t> param_off;
-    } dev[2];
-    std::vector<double> flops_per_amp;  // algorithmic flops per amplitude of each stage
-    ~StagedPlan() {
-        for (Dev &d : dev)
-            for (void *m : d.plain_mats)
-                if (m) cudaFree(m);
-    }
-};
-
 int build_staged(const qsim_circuit &c, qsim_plan &p) {
     const int n = c.n;
     if (n < LANE_BITS + REG_BITS) {
@@ -736,7 +735,10 @@ int build_staged(const qsim_circuit &c, qsim_plan &p) {
     // kmax selects the tile: 2^(9 + W) amplitudes with W = min(kmax, 4) warp qubits
     sp->W = std::min(std::min(p.kmax, MAX_WARP_BITS), n - LANE_BITS - REG_BITS);
     QSIM_TRY(plan_stage_list(c, sp->W, true, sp->stages));
-    for (const Stage &st : sp->stages) sp->flops_per_amp.push_back(stage_flops_per_amp(c, st));
+    for (const Stage &st : sp->stages) {
+        sp->flops_per_amp.push_back(stage_exec_flops_per_amp(st));
+        sp->circuit_flops_per_amp += stage_flops_per_amp(c, st);
+    }
     return QSIM_OK;
 }
 
@@ -819,12 +821,17 @@ static int launch_stage(void *psi, int n, int W, const void *params, cudaStream_
 int run_staged(qsim_state *s, qsim_plan &p) {
     if (!p.staged) return run_block_plan(s, p);
     QSIM_TRY(prepare_staged(p, s->dtype));
+    if (p.staged->specialized) QSIM_TRY(spec_prepare(*p.staged, s->dtype));
     StagedPlan &sp = *p.staged;
     const StagedPlan::Dev &d = sp.dev[s->dtype];
     for (size_t i = 0; i < sp.stages.size(); ++i) {
         const Stage &st = sp.stages[i];
         if (st.plain) {
             QSIM_TRY(launch_op(s->amps, s->n, s->dtype, st.op, s->stream, d.plain_mats[i]));
+            continue;
+        }
+        if (sp.specialized) {
+            QSIM_TRY(spec_launch(sp, s->dtype, i, s->amps, s->n, s->stream));
             continue;
         }
         const void *prm = &d.params[d.param_off[i]];
@@ -863,6 +870,20 @@ void staged_describe(const qsim_plan &p, std::string &out) {
                  cnt[SOP_EXCHANGE]);
         out += buf;
     }
+}
+
+void staged_set_specialized(qsim_plan &p) {
+    if (p.staged) p.staged->specialized = true;  // narrower circuits got a greedy plan
+}
+bool staged_specialized(const qsim_plan &p) { return p.staged && p.staged->specialized; }
+
+extern "C" QSIM_API int qsim_plan_flops(const qsim_plan *p, double *executed, double *circuit) {
+    if (!p || !p->staged) return qsim::set_error(QSIM_EINVAL, "not a staged plan");
+    double e = 0;
+    for (double f : p->staged->flops_per_amp) e += f;
+    if (executed) *executed = e;
+    if (circuit) *circuit = p->staged->circuit_flops_per_amp;
+    return QSIM_OK;
 }
 
 int staged_nsweeps(const qsim_plan &p) { return p.staged ? int(p.staged->stages.size()) : int(p.blocks.size()); }

@@ -123,10 +123,12 @@ def golden30():
 # greedy and plain sweeps <= 1.2e-10, tensor-core blocks 9.5e-9, complex128
 # 1.1e-17) times a margin of about 10; all far inside the stated bars (1e-5
 # complex64, 1e-12 complex128)
-R30_TOL = {"c64": {"staged": 1e-9, "tc": 5e-8, "greedy2": 1e-9, "plain": 1e-9}, "c128": {"plain": 1e-15}}
+R30_TOL = {"c64": {"staged": 1e-9, "staged-spec": 1e-9, "tc": 5e-8, "greedy2": 1e-9, "plain": 1e-9},
+           "c128": {"plain": 1e-15}}
 
 
-@pytest.mark.parametrize("dtype,mode,kmax", [("c64", "staged", 3), ("c64", "staged", 4), ("c64", "tc", 6),
+@pytest.mark.parametrize("dtype,mode,kmax", [("c64", "staged", 3), ("c64", "staged", 4), ("c64", "staged-spec", 3),
+                                             ("c64", "staged-spec", 4), ("c64", "tc", 6),
                                              ("c64", "tc", 5), ("c64", "greedy2", 2), ("c64", "plain", 0),
                                              ("c128", "plain", 0)])
 def test_random30_benchmark_circuit_against_oracle(q, golden30, dtype, mode, kmax):
@@ -141,7 +143,8 @@ def test_random30_benchmark_circuit_against_oracle(q, golden30, dtype, mode, kma
         s.run(c)
     else:
         s.run_fused(q.Plan(c, kmax=kmax, mode={"staged": q.FUSE_STAGED, "tc": q.FUSE_TC,
-                                                "greedy2": q.FUSE_GREEDY2}[mode]))
+                                                "greedy2": q.FUSE_GREEDY2,
+                                                "staged-spec": q.FUSE_STAGED | q.SPECIALIZE}[mode]))
     idx = np.concatenate([golden30["amp_index"], golden30["top_index"]])
     want = np.concatenate([golden30["amp_value"], golden30["top_value"]])
     got = s.tensor[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)

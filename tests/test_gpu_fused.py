@@ -116,6 +116,54 @@ def test_staged_two_qubit_gates_on_lanes(q, orc, dtype, kmax, n):
     assert err <= TOL[dtype], f"lane pairs n={n} {dtype} kmax={kmax}: {err:.3e}"
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("kmax", [1, 3, 4])
+@pytest.mark.parametrize("maker", ["random", "variational", "qft", "mixed", "lanes"])
+def test_specialized_stages_match_oracle(q, orc, dtype, kmax, maker):
+    """Stage kernels compiled for the plan (QSIM_PLAN_SPECIALIZE): every op
+    kind, lane and register targets, controls, exchanges, both precisions."""
+    n = {"random": 15, "variational": 14, "qft": 13, "mixed": 14, "lanes": 14}[maker]
+    circ = {"random": lambda: inputs.random_circuit(n, 8, seed=5),
+            "variational": lambda: inputs.variational(n, 5, seed=6),
+            "qft": lambda: inputs.qft(n),
+            "mixed": lambda: mixed_circuit(n, seed=7),
+            "lanes": lambda: lane_pair_circuit(n, seed=8)}[maker]()
+    psi0 = inputs.gaussian_state(n, seed=8)
+    want = orc.simulate(circ, psi0)
+    got = run_plan(q, circ, dtype, psi0, q.FUSE_STAGED | q.SPECIALIZE, kmax)
+    err = np.max(np.abs(got - want))
+    assert err <= TOL[dtype], f"specialized {maker} {dtype} kmax={kmax}: {err:.3e}"
+
+
+def test_specialized_plan_many_tiles_and_cache(q, orc):
+    """21 qubits (hundreds of tiles, warp and tile qubits high); a second
+    circuit of the same structure with other angles reuses the compiled
+    kernels (cache hit, no compile) and still matches the oracle."""
+    n = 21
+    a = inputs.random_circuit(n, 5, seed=9)
+    rng = np.random.default_rng(3)
+    b = inputs.Circuit(n, [inputs.Gate(g.name, g.targets, g.controls, inputs.haar_su2_quaternion(rng))
+                           if g.name == "su2" else g for g in a.gates])
+    psi0 = inputs.gaussian_state(n, seed=12)
+    pa = q.Plan(a, kmax=3, mode=q.FUSE_STAGED | q.SPECIALIZE)
+    assert pa.info()["mode"] == q.FUSE_STAGED | q.SPECIALIZE
+    s = q.State(n, "c64")
+    s.from_host(psi0)
+    s.run_fused(pa)
+    assert np.max(np.abs(s.to_host() - orc.simulate(a, psi0))) <= TOL["c64"]
+    st0 = q.spec_stats()
+    s.from_host(psi0)
+    s.run_fused(q.Plan(b, kmax=3, mode=q.FUSE_STAGED | q.SPECIALIZE))
+    st1 = q.spec_stats()
+    assert st1["compiles"] == st0["compiles"] and st1["cache_hits"] > st0["cache_hits"]
+    assert np.max(np.abs(s.to_host() - orc.simulate(b, psi0))) <= TOL["c64"]
+
+
+def test_specialized_rejects_other_modes(q):
+    with pytest.raises(q.QsimError):
+        q.Plan(inputs.random_circuit(14, 2, seed=1), kmax=6, mode=q.FUSE_TC | q.SPECIALIZE)
+
+
 @pytest.mark.parametrize("n", [5, 9, 10, 12])
 def test_staged_small_widths(q, orc, n):
     """n < 9 falls back to the greedy plan; n = 9..12 uses tiles with fewer warps."""

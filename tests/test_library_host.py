@@ -214,6 +214,39 @@ def test_pair_fusion_absorbs_the_random_circuits_one_qubit_gates(q):
     count = lambda key: sum(int(x) for x in re.findall(key + r"=(\d+)", d))
     assert count("u2") == 150
     assert count("u1") == 0 and count("reg") == 0 and count("lane") == 0
+    # arithmetic per amplitude: the circuit's 600 dense 1-qubit gates one
+    # sweep each (16 flops, the CZ none) against 150 fused 4x4 (32 flops)
+    fl = q.Plan(inputs.random_circuit(30, 20, seed=2022), kmax=3, mode=q.FUSE_STAGED).flops()
+    assert fl == {"executed": 150 * 32.0, "circuit": 600 * 16.0}
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_specialized_stage_source_compiles(q, tmp_path, dtype):
+    """The source the library writes for a plan's specialised stage kernels
+    (one kernel per tile stage, here with lane and register 4x4 ops,
+    controls, diagonals, sign flips and exchanges) compiles for sm_103a, and
+    the plan reports the flag; the source holds no coefficient values."""
+    import shutil
+    import subprocess
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_gpu_fused import lane_pair_circuit, mixed_circuit
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    for circ in (mixed_circuit(14, seed=7), lane_pair_circuit(14, seed=8)):
+        p = q.Plan(circ, kmax=3, mode=q.FUSE_STAGED | q.SPECIALIZE)
+        assert p.info()["mode"] == q.FUSE_STAGED | q.SPECIALIZE
+        src = p.source(dtype)
+        nst = sum(1 for st in p.stages() if not st["plain"])
+        assert src.count("__global__") == nst > 0
+        f = tmp_path / f"stages_{dtype}.cu"
+        f.write_text(src)
+        r = subprocess.run([nvcc, "-cubin", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17",
+                            str(f), "-o", str(tmp_path / "stages.cubin")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+    with pytest.raises(q.QsimError):
+        q.Plan(inputs.random_circuit(14, 2, seed=1), kmax=6, mode=q.FUSE_TC | q.SPECIALIZE)
 
 
 def test_plan_block_only_for_greedy_plans(q):
