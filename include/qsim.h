@@ -418,6 +418,13 @@ QSIM_API int qsim_expectation_pauli(qsim_state *s, int nterms, const uint64_t *x
 QSIM_API int qsim_adjoint_grad(const qsim_circuit *c, const qsim_state *psi0, int dtype, int nsets,
                                const double *params, int nterms, const uint64_t *xmask, const uint64_t *zmask,
                                const double *coeff, double *grads, double *energies, void *cuda_stream);
+/* Whether qsim_adjoint_grad (complex64, n >= 12) runs its forward and
+ * reverse stages through kernels compiled for the circuit's structure (as
+ * QSIM_PLAN_SPECIALIZE does for staged plans; compiled once per structure,
+ * reused for every parameter set and later call): 1 always, -1 never, 0
+ * (default) from 20 qubits.  Process-wide; *previous (may be NULL) receives
+ * the mode it replaces; QSIM_EINVAL for another value. */
+QSIM_API int qsim_adjoint_specialize(int mode, int *previous);
 
 /* ---------------------------------------------------------------- batches */
 typedef struct qsim_batch qsim_batch;

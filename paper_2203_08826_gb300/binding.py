@@ -69,6 +69,7 @@ _SIGS = {
     "qsim_plan_source": ([P, I, P, ctypes.c_size_t, P], I),
     "qsim_spec_stats": ([P, P, P], I),
     "qsim_plan_flops": ([P, P, P], I),
+    "qsim_adjoint_specialize": ([I, P], I),
     "qsim_plan_tc_pass": ([P, I, P, P, P, P, P, P, P], I),
     "qsim_plan_tc_epilogue": ([P, I, I, P, P, P, P, P], I),
     "qsim_plan_stage": ([P, I, P, P, P, P, P], I),
@@ -602,6 +603,14 @@ def adjoint_grad(circuit, ham: inputs.PauliSum, params: np.ndarray, dtype: str =
                                    C64 if dtype == "c64" else C128, nsets, _p(params), len(c),
                                    _p(xm), _p(zm), _p(c), _p(grads), _p(en), _stream_ptr(stream)))
     return grads, en
+
+
+def adjoint_specialize(mode: int) -> int:
+    """Stage kernels compiled for the circuit in adjoint_grad: 1 always, -1
+    never, 0 from 20 qubits.  Returns the previous mode."""
+    prev = ctypes.c_int()
+    _check(lib().qsim_adjoint_specialize(int(mode), ctypes.byref(prev)))
+    return prev.value
 
 
 def adjoint_energy(circuit, ham: inputs.PauliSum, dtype: str = "c64"):

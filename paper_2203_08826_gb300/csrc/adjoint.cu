@@ -11,6 +11,7 @@
 // un-applied to both states with the plain sweeps.  The paper differentiates
 // only through TensorFlow's automatic differentiation (Sec. 2); this is the
 // GPU-native replacement.
+#include <atomic>
 #include <cstring>
 
 #include "internal.h"
@@ -607,6 +608,9 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
 // adds its warps' sums in double and writes one partial per tile, reduced per
 // rotation afterwards.
 constexpr int DUAL_W = 3;
+// stage kernels compiled for the circuit: 1 always, -1 never, 0 from
+// SPECIALIZE_MIN_QUBITS qubits (qsim_adjoint_specialize)
+std::atomic<int> g_adj_specialize{0};
 
 struct DualParams {
     stage::StageParams<float2> sp;
@@ -777,7 +781,8 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
         hoist_markers(bwd.gates);
         // forward sweep (staged plan) from |0>
         qsim_plan *fp = nullptr;
-        QSIM_TRY(qsim_plan_build(&fwd, DUAL_W, QSIM_FUSE_STAGED, &fp));
+        const bool spec = g_adj_specialize > 0 || (g_adj_specialize == 0 && n >= SPECIALIZE_MIN_QUBITS);
+        QSIM_TRY(qsim_plan_build(&fwd, DUAL_W, QSIM_FUSE_STAGED | (spec ? QSIM_PLAN_SPECIALIZE : 0), &fp));
         struct PGuard {
             qsim_plan *p;
             ~PGuard() { qsim_plan_destroy(p); }
@@ -799,12 +804,21 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
         // reverse sweep as two-state stages
         std::vector<stage::Stage> stages;
         QSIM_TRY(stage::plan_stage_list(bwd, DUAL_W, true, stages));
-        for (const stage::Stage &sg : stages) {
+        DualSpec dspec;
+        if (spec) QSIM_TRY(spec_dual_prepare(stages, n, DUAL_W, dspec));
+        for (size_t si = 0; si < stages.size(); ++si) {
+            const stage::Stage &sg = stages[si];
             if (sg.plain) {
                 if (sg.op.type == Op::DENSE && sg.op.k >= 2)
                     return set_error(QSIM_EUNSUPPORTED, "adjoint: gates of more than 2 targets");
                 QSIM_TRY(launch_op(psi, n, QSIM_C64, sg.op, st, nullptr));
                 QSIM_TRY(launch_op(lam, n, QSIM_C64, sg.op, st, nullptr));
+                continue;
+            }
+            if (spec) {
+                LaunchScope ls(K_ADJ_STEP, st, 4.0 * double(N) * sizeof(float2),
+                               (2.0 * stage::stage_exec_flops_per_amp(sg) + 12.0 * sg.ngradops) * double(N));
+                QSIM_TRY(spec_dual_launch(dspec, sg, si, psi, lam, partial, n, DUAL_W, st));
                 continue;
             }
             DualParams dp;
@@ -896,4 +910,11 @@ extern "C" int qsim_adjoint_grad(const qsim_circuit *c, const qsim_state *psi0, 
         return adjoint_fused_c64(*c, a0, nsets, params, hp, grads, energies, st);
     return dtype == QSIM_C64 ? adjoint_t<float>(*c, a0, nsets, params, hp, grads, energies, st)
                              : adjoint_t<double>(*c, a0, nsets, params, hp, grads, energies, st);
+}
+
+extern "C" QSIM_API int qsim_adjoint_specialize(int mode, int *previous) {
+    if (mode < -1 || mode > 1) return set_error(QSIM_EINVAL, "mode must be -1, 0 or 1");
+    const int old = qsim::g_adj_specialize.exchange(mode);
+    if (previous) *previous = old;
+    return QSIM_OK;
 }

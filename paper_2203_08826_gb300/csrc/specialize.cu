@@ -23,6 +23,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -94,7 +95,10 @@ template <typename C> __device__ __forceinline__ C neg(C a) {
 }
 )";
 
-// Writes the source of one tile stage as kernel `name`.
+// Writes the source of tile-stage kernels.  Every op is emitted for the
+// tile in `v` and, for the two-state stages of the adjoint reverse sweep
+// (dual), once more for the tile in `w`, as the interpreter's apply_op2
+// applies one decoded op to both.
 struct Gen {
     std::ostringstream o;
     const char *C;  // "float2" / "double2"
@@ -118,36 +122,39 @@ struct Gen {
         for (int i = 0; i < W; ++i) o << " | ((u64)((warp >> " << i << ") & 1) << " << int(P.wq[i]) << ")";
         o << ";\n";
     }
+    std::string tcond(uint64_t tm) const {
+        std::ostringstream c;
+        c << "(base & 0x" << std::hex << tm << "ull) == 0x" << tm << "ull";
+        return c.str();
+    }
     void ctrl_open(const StageOp &op) {
-        if (op.tmask) o << "    if ((base & 0x" << std::hex << op.tmask << std::dec << "ull) == 0x" << std::hex
-                        << op.tmask << std::dec << "ull) {\n";
+        if (op.tmask) o << "    if (" << tcond(op.tmask) << ") {\n";
         else o << "    {\n";
     }
     static bool rok(int j, int rneed) { return (j & rneed) == rneed; }
     std::string coef(int i) const { return "p.c[" + std::to_string(i) + "]"; }
 
-    void u1_reg(int rb, int moff, int rneed) {
+    void u1_reg(const char *A, int rb, int moff, int rneed) {
         for (int i = 0; i < (1 << REG_BITS); ++i) {
             if ((i >> rb) & 1 || !rok(i, rneed)) continue;
-            o << "        u1(v[" << i << "], v[" << (i | (1 << rb)) << "], " << coef(moff) << ", " << coef(moff + 1)
-              << ", " << coef(moff + 2) << ", " << coef(moff + 3) << ");\n";
+            o << "        u1(" << A << "[" << i << "], " << A << "[" << (i | (1 << rb)) << "], " << coef(moff) << ", "
+              << coef(moff + 1) << ", " << coef(moff + 2) << ", " << coef(moff + 3) << ");\n";
         }
     }
     // 1-qubit gate on lane bit l; `ok` guards the update (every lane shuffles)
-    void u1_lane(int l, int moff, int rneed, bool guarded) {
+    void u1_lane(const char *A, int l, int moff, int rneed, bool guarded) {
         o << "    {\n        const bool hi = (lane >> " << l << ") & 1;\n";
         o << "        const " << C << " cs = hi ? " << coef(moff + 3) << " : " << coef(moff) << ";\n";
         o << "        const " << C << " co = hi ? " << coef(moff + 2) << " : " << coef(moff + 1) << ";\n";
         for (int j = 0; j < (1 << REG_BITS); ++j) {
             if (!rok(j, rneed)) continue;
-            o << "        { const " << C << " t = shfl_c(v[" << j << "], " << (1 << l) << "); ";
+            o << "        { const " << C << " t = shfl_c(" << A << "[" << j << "], " << (1 << l) << "); ";
             if (guarded) o << "if (ok) ";
-            o << "v[" << j << "] = cmad(co, t, cmul(cs, v[" << j << "])); }\n";
+            o << A << "[" << j << "] = cmad(co, t, cmul(cs, " << A << "[" << j << "])); }\n";
         }
         o << "    }\n";
     }
-
-    void op_u2(const StageOp &op) {
+    void op_u2(const char *A, const StageOp &op) {
         const bool la = op.a < POS_REG, lb = op.b < POS_REG;
         const int m = op.moff;
         if (!la && !lb) {  // two register targets: the interpreter's u2_reg
@@ -156,16 +163,13 @@ struct Gen {
             o << "        const " << C << " *m = &" << coef(m) << ";\n";
             for (int i = 0; i < (1 << REG_BITS); ++i) {
                 if (i & ((1 << JA) | (1 << JB)) || !rok(i, op.rneed)) continue;
-                o << "        u2(v[" << i << "], v[" << (i | (1 << JB)) << "], v[" << (i | (1 << JA)) << "], v["
-                  << (i | (1 << JA) | (1 << JB)) << "], m);\n";
+                o << "        u2(" << A << "[" << i << "], " << A << "[" << (i | (1 << JB)) << "], " << A << "["
+                  << (i | (1 << JA)) << "], " << A << "[" << (i | (1 << JA) | (1 << JB)) << "], m);\n";
             }
             o << "    }\n";
             return;
         }
-        o << "    {\n";
-        o << "        const bool ok = " << (op.tmask ? "" : "true") ;
-        if (op.tmask) o << "(base & 0x" << std::hex << op.tmask << "ull) == 0x" << op.tmask << std::dec << "ull";
-        o << ";\n";
+        o << "    {\n        const bool ok = " << (op.tmask ? tcond(op.tmask) : std::string("true")) << ";\n";
         if (la != lb) {
             // one lane bit and one register bit (coefficients per lane-bit value)
             const int l = la ? op.a : op.b, rb = (la ? op.b : op.a) - POS_REG;
@@ -176,11 +180,13 @@ struct Gen {
             for (int i = 0; i < (1 << REG_BITS); ++i) {
                 if ((i >> rb) & 1 || !rok(i, op.rneed)) continue;
                 const int i1 = i | (1 << rb);
-                o << "        { const " << C << " x0 = v[" << i << "], x1 = v[" << i1 << "];\n";
+                o << "        { const " << C << " x0 = " << A << "[" << i << "], x1 = " << A << "[" << i1 << "];\n";
                 o << "          const " << C << " y0 = shfl_c(x0, " << (1 << l) << "), y1 = shfl_c(x1, " << (1 << l)
                   << ");\n";
-                o << "          if (ok) { v[" << i << "] = cmad(m3, y1, cmad(m2, y0, cmad(m1, x1, cmul(m0, x0))));\n";
-                o << "                    v[" << i1 << "] = cmad(m7, y1, cmad(m6, y0, cmad(m5, x1, cmul(m4, x0)))); } }\n";
+                o << "          if (ok) { " << A << "[" << i
+                  << "] = cmad(m3, y1, cmad(m2, y0, cmad(m1, x1, cmul(m0, x0))));\n";
+                o << "                    " << A << "[" << i1
+                  << "] = cmad(m7, y1, cmad(m6, y0, cmad(m5, x1, cmul(m4, x0)))); } }\n";
             }
         } else {
             // two lane bits: own amplitude and the lanes across a, b and both
@@ -192,22 +198,23 @@ struct Gen {
                   << coef(m + 4 + e) << " : sel == 2 ? " << coef(m + 8 + e) << " : " << coef(m + 12 + e) << ";\n";
             for (int j = 0; j < (1 << REG_BITS); ++j) {
                 if (!rok(j, op.rneed)) continue;
-                o << "        { const " << C << " p1 = shfl_c(v[" << j << "], " << ma << "), p2 = shfl_c(v[" << j
-                  << "], " << mb << "), p3 = shfl_c(v[" << j << "], " << (ma | mb) << ");\n";
-                o << "          if (ok) v[" << j << "] = cmad(m3, p3, cmad(m2, p2, cmad(m1, p1, cmul(m0, v[" << j
-                  << "])))); }\n";
+                o << "        { const " << C << " p1 = shfl_c(" << A << "[" << j << "], " << ma << "), p2 = shfl_c("
+                  << A << "[" << j << "], " << mb << "), p3 = shfl_c(" << A << "[" << j << "], " << (ma | mb)
+                  << ");\n";
+                o << "          if (ok) " << A << "[" << j << "] = cmad(m3, p3, cmad(m2, p2, cmad(m1, p1, cmul(m0, "
+                  << A << "[" << j << "])))); }\n";
             }
         }
         o << "    }\n";
     }
 
-    void op_diag(const StageOp &op) {
+    void op_diag(const char *A, const StageOp &op) {
         ctrl_open(op);
         if (op.k == 0) {
             for (int j = 0; j < (1 << REG_BITS); ++j) {
                 if (!rok(j, op.rneed)) continue;
-                if (op.flags & 1) o << "        v[" << j << "] = neg(v[" << j << "]);\n";
-                else o << "        v[" << j << "] = cmul(" << coef(op.moff) << ", v[" << j << "]);\n";
+                if (op.flags & 1) o << "        " << A << "[" << j << "] = neg(" << A << "[" << j << "]);\n";
+                else o << "        " << A << "[" << j << "] = cmul(" << coef(op.moff) << ", " << A << "[" << j << "]);\n";
             }
             o << "    }\n";
             return;
@@ -227,46 +234,164 @@ struct Gen {
             int sj = 0;
             for (int r = 0; r < REG_BITS; ++r)
                 if ((j >> r) & 1) sj |= rsel[r];
-            o << "        v[" << j << "] = cmul(p.c[" << op.moff << " + (st | " << sj << ")], v[" << j << "]);\n";
+            o << "        " << A << "[" << j << "] = cmul(p.c[" << op.moff << " + (st | " << sj << ")], " << A << "["
+              << j << "]);\n";
         }
         o << "    }\n";
     }
 
-    void op_neg(const Stage &st, const StageOp &op) {
+    void op_neg(const Stage &st, const StageOp &op, bool dual) {
         o << "    {\n        unsigned flip = 0u;\n";
         for (int e = 0; e < op.k; ++e) {
             const uint64_t tm = st.aux[size_t(op.moff + 2 * e)];
             const uint32_t pat = uint32_t(st.aux[size_t(op.moff + 2 * e + 1)]);
             if (tm == 0) o << "        flip ^= " << pat << "u;\n";
-            else o << "        if ((base & 0x" << std::hex << tm << "ull) == 0x" << tm << std::dec << "ull) flip ^= " << pat
-                   << "u;\n";
+            else o << "        if (" << tcond(tm) << ") flip ^= " << pat << "u;\n";
         }
-        for (int j = 0; j < (1 << REG_BITS); ++j)
-            o << "        if (flip & " << (1u << j) << "u) v[" << j << "] = neg(v[" << j << "]);\n";
+        for (int j = 0; j < (1 << REG_BITS); ++j) {
+            o << "        if (flip & " << (1u << j) << "u) { v[" << j << "] = neg(v[" << j << "]);";
+            if (dual) o << " w[" << j << "] = neg(w[" << j << "]);";
+            o << " }\n";
+        }
         o << "    }\n";
     }
 
-    void exchange(const Phase &from, const Phase &to) {
+    void exchange_one(const char *A, const Phase &from, const Phase &to) {
         o << "    {\n        unsigned lb = (unsigned)lane";
         for (int i = 0; i < W; ++i) o << " | (((unsigned)warp >> " << i << " & 1u) << " << (LANE_BITS + from.wslot[i]) << ")";
         o << ";\n";
-        for (int j = 0; j < (1 << REG_BITS); ++j) o << "        tile[lb | " << smem_offset(from, j) << "u] = v[" << j << "];\n";
+        for (int j = 0; j < (1 << REG_BITS); ++j)
+            o << "        tile[lb | " << smem_offset(from, j) << "u] = " << A << "[" << j << "];\n";
         o << "        __syncthreads();\n        lb = (unsigned)lane";
         for (int i = 0; i < W; ++i) o << " | (((unsigned)warp >> " << i << " & 1u) << " << (LANE_BITS + to.wslot[i]) << ")";
         o << ";\n";
-        for (int j = 0; j < (1 << REG_BITS); ++j) o << "        v[" << j << "] = tile[lb | " << smem_offset(to, j) << "u];\n";
+        for (int j = 0; j < (1 << REG_BITS); ++j)
+            o << "        " << A << "[" << j << "] = tile[lb | " << smem_offset(to, j) << "u];\n";
         o << "        __syncthreads();\n    }\n";
-        set_base(to);
+    }
+    // adjoint gradient op: the warp's share of (Sx, Sy, Sz) over the pairs
+    // of position a (as grad3_t in stage_common.cuh), added to gw
+    void op_grad(const StageOp &op) {
+        o << "    {\n        float sx = 0.f, sy = 0.f, sz = 0.f;\n";
+        if (op.a >= POS_REG) {
+            const int rb = op.a - POS_REG;
+            for (int j = 0; j < (1 << REG_BITS); ++j) {
+                if ((j >> rb) & 1) continue;
+                const int j1 = j | (1 << rb);
+                o << "        { const " << C << " p0 = v[" << j << "], p1 = v[" << j1 << "], l0 = w[" << j
+                  << "], l1 = w[" << j1 << "];\n";
+                o << "          sz += float(l0.x) * float(p0.y) - float(l0.y) * float(p0.x) - float(l1.x) * float(p1.y) + "
+                     "float(l1.y) * float(p1.x);\n";
+                o << "          sx += float(l0.x) * float(p1.y) - float(l0.y) * float(p1.x) + float(l1.x) * float(p0.y) - "
+                     "float(l1.y) * float(p0.x);\n";
+                o << "          sy += float(l1.x) * float(p0.x) + float(l1.y) * float(p0.y) - float(l0.x) * float(p1.x) - "
+                     "float(l0.y) * float(p1.y); }\n";
+            }
+        } else {
+            o << "        float tx = 0.f, ty = 0.f, tz = 0.f;\n";
+            for (int j = 0; j < (1 << REG_BITS); ++j) {
+                o << "        { const " << C << " pp = v[" << j << "], l = w[" << j << "], qq = shfl_c(v[" << j << "], "
+                  << (1 << op.a) << ");\n";
+                o << "          tz += float(l.x) * float(pp.y) - float(l.y) * float(pp.x);\n";
+                o << "          tx += float(l.x) * float(qq.y) - float(l.y) * float(qq.x);\n";
+                o << "          ty += float(l.x) * float(qq.x) + float(l.y) * float(qq.y); }\n";
+            }
+            o << "        const bool one = (lane >> " << int(op.a) << ") & 1;\n";
+            o << "        sx += tx;\n        sy += one ? ty : -ty;\n        sz += one ? -tz : tz;\n";
+        }
+        o << "        for (int s = 16; s > 0; s >>= 1) {\n"
+             "            sx += __shfl_xor_sync(0xffffffffu, sx, s);\n"
+             "            sy += __shfl_xor_sync(0xffffffffu, sy, s);\n"
+             "            sz += __shfl_xor_sync(0xffffffffu, sz, s);\n"
+             "        }\n";
+        o << "        if (lane == 0) {\n            float *g = gw + " << ((3 * int(op.k)) << W) << " + warp;\n"
+          << "            g[0] += sx;\n            g[" << (1 << W) << "] += sy;\n            g[" << (2 << W)
+          << "] += sz;\n        }\n    }\n";
     }
 
-    // the whole kernel of one tile stage; its parameter block holds ncoef
-    // coefficients (at least one)
-    void stage(const Stage &st, const std::string &name, int ncoef, int min_blocks) {
-        o << "struct P_" << name << " { " << C << " c[" << ncoef << "]; };\n";
+    void op_any(const Stage &st, const StageOp &op, bool dual) {
+        const char *arrs[2] = {"v", "w"};
+        const int na = dual ? 2 : 1;
+        switch (op.type) {
+            case SOP_U1:
+                for (int t = 0; t < na; ++t) {
+                    if (op.a >= POS_REG) {
+                        ctrl_open(op);
+                        u1_reg(arrs[t], op.a - POS_REG, op.moff, op.rneed);
+                        o << "    }\n";
+                    } else {
+                        o << "    {\n        const bool ok = " << (op.tmask ? tcond(op.tmask) : std::string("true"))
+                          << ";\n";
+                        u1_lane(arrs[t], op.a, op.moff, op.rneed, op.tmask != 0);
+                        o << "    }\n";
+                    }
+                }
+                break;
+            case SOP_U1R:
+                for (int t = 0; t < na; ++t) {
+                    int off = op.moff;
+                    o << "    {\n";
+                    for (int b = 0; b < REG_BITS; ++b)
+                        if (op.a & (1 << b)) {
+                            u1_reg(arrs[t], b, off, 0);
+                            off += 4;
+                        }
+                    o << "    }\n";
+                }
+                break;
+            case SOP_U1L:
+                for (int t = 0; t < na; ++t) {
+                    int off = op.moff;
+                    for (int l = 0; l < LANE_BITS; ++l)
+                        if (op.a & (1 << l)) {
+                            u1_lane(arrs[t], l, off, 0, false);
+                            off += 4;
+                        }
+                }
+                break;
+            case SOP_U2:
+                for (int t = 0; t < na; ++t) op_u2(arrs[t], op);
+                break;
+            case SOP_DIAG:
+                for (int t = 0; t < na; ++t) op_diag(arrs[t], op);
+                break;
+            case SOP_NEG: op_neg(st, op, dual); break;
+            case SOP_GRAD:
+                if (dual) op_grad(op);
+                break;
+            default: break;
+        }
+    }
+    // the kernel of one tile stage; its parameter block holds ncoef
+    // coefficients (at least one) and, for a dual stage, the Pauli vectors of
+    // its gradient terms.  A dual stage (n qubits, ntiles tiles) writes each
+    // gradient term's per-tile sum to partial[slot * ntiles + tile].
+    void stage(const Stage &st, const std::string &name, int ncoef, int min_blocks, bool dual, uint64_t ntiles) {
+        const int ng = std::max<int>(1, int(st.grads.size()));
+        o << "struct P_" << name << " { " << C << " c[" << ncoef << "];";
+        if (dual) o << " float gv[" << ng << "][3];";
+        o << " };\n";
+        if (dual) {
+            o << "__constant__ int " << name << "_gslot[" << ng << "] = {";
+            for (size_t g = 0; g < st.grads.size(); ++g) o << (g ? ", " : "") << st.grads[g].slot;
+            if (st.grads.empty()) o << "0";
+            o << "};\n__constant__ int " << name << "_gop[" << ng << "] = {";
+            for (size_t g = 0; g < st.grads.size(); ++g) o << (g ? ", " : "") << st.grads[g].op;
+            if (st.grads.empty()) o << "0";
+            o << "};\n";
+        }
         o << "extern \"C\" __global__ void __launch_bounds__(" << (32 << W) << ", " << min_blocks << ") " << name
-          << "(" << C << " *__restrict__ psi, const __grid_constant__ P_" << name << " p) {\n";
+          << "(" << C << " *__restrict__ psi, ";
+        if (dual) o << C << " *__restrict__ lam, double *__restrict__ partial, ";
+        o << "const __grid_constant__ P_" << name << " p) {\n";
         o << "    extern __shared__ " << C << " tile[];\n";
         o << "    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n";
+        const int gwn = (3 * std::max(1, st.ngradops)) << W;
+        if (dual) {
+            o << "    __shared__ float gw[" << gwn << "];\n";
+            o << "    for (int g = threadIdx.x; g < " << gwn << "; g += blockDim.x) gw[g] = 0.f;\n";
+            o << "    __syncthreads();\n";
+        }
         // tile id -> base index: a zero inserted at every tile qubit (ascending)
         std::vector<int> tq;
         for (int q = 0; q < LANE_BITS; ++q) tq.push_back(q);
@@ -280,60 +405,41 @@ struct Gen {
         int ph = st.phase0;
         set_base(st.phases[size_t(ph)]);
         o << "    " << C << " v[" << (1 << REG_BITS) << "];\n";
-        o << "    {\n        const " << C << " *g = psi + base;\n";
-        for (int j = 0; j < (1 << REG_BITS); ++j)
-            o << "        v[" << j << "] = g[0x" << std::hex << reg_offset(st.phases[size_t(ph)], j) << std::dec << "ull];\n";
-        o << "    }\n";
-        for (const StageOp &op : st.ops) {
-            switch (op.type) {
-                case SOP_EXCHANGE:
-                    exchange(st.phases[size_t(ph)], st.phases[size_t(op.a)]);
-                    ph = op.a;
-                    break;
-                case SOP_U1:
-                    if (op.a >= POS_REG) {
-                        ctrl_open(op);
-                        u1_reg(op.a - POS_REG, op.moff, op.rneed);
-                        o << "    }\n";
-                    } else {
-                        o << "    {\n        const bool ok = ";
-                        if (op.tmask) o << "(base & 0x" << std::hex << op.tmask << "ull) == 0x" << op.tmask << std::dec << "ull";
-                        else o << "true";
-                        o << ";\n";
-                        u1_lane(op.a, op.moff, op.rneed, op.tmask != 0);
-                        o << "    }\n";
-                    }
-                    break;
-                case SOP_U1R: {
-                    int off = op.moff;
-                    o << "    {\n";
-                    for (int b = 0; b < REG_BITS; ++b)
-                        if (op.a & (1 << b)) {
-                            u1_reg(b, off, 0);
-                            off += 4;
-                        }
-                    o << "    }\n";
-                    break;
-                }
-                case SOP_U1L: {
-                    int off = op.moff;
-                    for (int l = 0; l < LANE_BITS; ++l)
-                        if (op.a & (1 << l)) {
-                            u1_lane(l, off, 0, false);
-                            off += 4;
-                        }
-                    break;
-                }
-                case SOP_U2: op_u2(op); break;
-                case SOP_DIAG: op_diag(op); break;
-                case SOP_NEG: op_neg(st, op); break;
-                default: break;  // gradient ops never reach a specialised plan
+        if (dual) o << "    " << C << " w[" << (1 << REG_BITS) << "];\n";
+        auto io = [&](const char *ptr, const char *A, bool store) {
+            o << "    {\n        " << (store ? "" : "const ") << C << " *g = " << ptr << " + base;\n";
+            for (int j = 0; j < (1 << REG_BITS); ++j) {
+                const uint64_t off = reg_offset(st.phases[size_t(ph)], j);
+                if (store) o << "        g[0x" << std::hex << off << std::dec << "ull] = " << A << "[" << j << "];\n";
+                else o << "        " << A << "[" << j << "] = g[0x" << std::hex << off << std::dec << "ull];\n";
             }
+            o << "    }\n";
+        };
+        io("psi", "v", false);
+        if (dual) io("lam", "w", false);
+        for (const StageOp &op : st.ops) {
+            if (op.type == SOP_EXCHANGE) {
+                exchange_one("v", st.phases[size_t(ph)], st.phases[size_t(op.a)]);
+                if (dual) exchange_one("w", st.phases[size_t(ph)], st.phases[size_t(op.a)]);
+                ph = op.a;
+                set_base(st.phases[size_t(ph)]);
+                continue;
+            }
+            op_any(st, op, dual);
         }
-        o << "    {\n        " << C << " *g = psi + base;\n";
-        for (int j = 0; j < (1 << REG_BITS); ++j)
-            o << "        g[0x" << std::hex << reg_offset(st.phases[size_t(ph)], j) << std::dec << "ull] = v[" << j << "];\n";
-        o << "    }\n}\n";
+        io("psi", "v", true);
+        if (dual) {
+            io("lam", "w", true);
+            o << "    __syncthreads();\n";
+            o << "    for (int g = threadIdx.x; g < " << int(st.grads.size()) << "; g += blockDim.x) {\n";
+            o << "        const float *s = gw + ((3 * " << name << "_gop[g]) << " << W << ");\n";
+            o << "        double t = 0.0;\n";
+            o << "        for (int i = 0; i < " << (1 << W) << "; ++i)\n";
+            o << "            t += double(p.gv[g][0]) * s[i] + double(p.gv[g][1]) * s[" << (1 << W)
+              << " + i] + double(p.gv[g][2]) * s[" << (2 << W) << " + i];\n";
+            o << "        partial[(u64)" << name << "_gslot[g] * " << ntiles << "ull + blockIdx.x] = t;\n    }\n";
+        }
+        o << "}\n";
     }
 };
 
@@ -365,6 +471,122 @@ int compile(const std::string &src, std::string &cubin, std::string &log) {
 }
 
 std::string kernel_name(size_t i) { return "qsim_spec_stage_" + std::to_string(i); }
+std::string dual_kernel_name(size_t i) { return "qsim_spec_dual_" + std::to_string(i); }
+
+// Structural fingerprint of a stage: everything its generated source depends
+// on, and nothing of the coefficient values (cache key; far cheaper to form
+// than the source).
+template <typename T> void put(std::string &k, const T &v) { k.append(reinterpret_cast<const char *>(&v), sizeof v); }
+void put_stage(std::string &k, const Stage &st) {
+    put(k, int(st.plain));
+    if (st.plain) return;
+    put(k, int(st.slots.size()));
+    for (int q : st.slots) put(k, q);
+    put(k, st.phase0);
+    put(k, int(st.phases.size()));
+    for (const Phase &P : st.phases) put(k, P);  // int8 arrays only
+    put(k, int(st.ops.size()));
+    for (const StageOp &op : st.ops) {
+        put(k, op.tmask);
+        put(k, op.moff);
+        const int8_t f[6] = {op.type, op.a, op.b, op.k, op.rneed, op.flags};
+        put(k, f);
+        put(k, op.dq);
+    }
+    put(k, int(st.aux.size()));
+    for (uint64_t a : st.aux) put(k, a);
+    put(k, int(st.pool.size()));
+    put(k, st.ngradops);
+    put(k, int(st.grads.size()));
+    for (const Stage::GradRef &g : st.grads) {
+        put(k, g.slot);
+        put(k, g.op);
+    }
+}
+
+// The libraries for groups of stages [first, second): looked up by key,
+// the missing ones generated and compiled in parallel host threads.
+int get_libs(const std::vector<std::pair<size_t, size_t>> &groups, const std::vector<std::string> &keys,
+             const std::function<std::string(size_t)> &source_of, std::vector<std::shared_ptr<SpecLib>> &libs) {
+    libs.assign(groups.size(), nullptr);
+    std::vector<size_t> todo;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            auto it = g_cache.find(keys[gi]);
+            if (it != g_cache.end()) {
+                libs[gi] = it->second;
+                ++g_hits;
+            } else {
+                todo.push_back(gi);
+            }
+        }
+    }
+    if (todo.empty()) return QSIM_OK;
+    std::vector<std::string> cubins(groups.size()), logs(groups.size());
+    std::vector<int> rcs(groups.size(), QSIM_OK);
+    const auto t0 = std::chrono::steady_clock::now();
+    {
+        std::vector<std::thread> th;
+        const size_t nthreads =
+            std::max<size_t>(1, std::min<size_t>(todo.size(), std::max(1u, std::thread::hardware_concurrency())));
+        std::atomic<size_t> next{0};
+        for (size_t t = 0; t < nthreads; ++t)
+            th.emplace_back([&] {
+                for (size_t k; (k = next.fetch_add(1)) < todo.size();) {
+                    const size_t gi = todo[k];
+                    rcs[gi] = compile(source_of(gi), cubins[gi], logs[gi]);
+                }
+            });
+        for (std::thread &t : th) t.join();
+    }
+    for (size_t gi : todo)
+        if (rcs[gi] != QSIM_OK)
+            return set_error(QSIM_ECUDA, "specialised stage compile failed: %.400s", logs[gi].c_str());
+    for (size_t gi : todo) {
+        auto L = std::make_shared<SpecLib>();
+        QSIM_CUDA_TRY(cudaLibraryLoadData(&L->lib, cubins[gi].data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
+                      "load specialised stages");
+        libs[gi] = L;
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (g_cache.size() >= CACHE_MAX) g_cache.erase(g_cache.begin());
+        g_cache[keys[gi]] = L;
+        ++g_compiles;
+    }
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_compile_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QSIM_OK;
+}
+
+std::vector<std::pair<size_t, size_t>> stage_groups(size_t ns) {
+    const size_t per = 4;  // stages per program: compiled in parallel, cached separately
+    std::vector<std::pair<size_t, size_t>> groups;
+    for (size_t i = 0; i < ns; i += per) groups.push_back({i, std::min(ns, i + per)});
+    return groups;
+}
+
+void pack_coefficients(const Stage &st, int dtype, std::vector<unsigned char> &b, size_t extra) {
+    const size_t eb = dtype == QSIM_C64 ? 8 : 16;
+    const size_t nc = std::max<size_t>(1, st.pool.size());
+    b.assign(nc * eb + extra, 0);
+    for (size_t e = 0; e < st.pool.size(); ++e) {
+        if (dtype == QSIM_C64) {
+            const float v[2] = {float(st.pool[e].real()), float(st.pool[e].imag())};
+            memcpy(&b[e * eb], v, 8);
+        } else {
+            const double v[2] = {st.pool[e].real(), st.pool[e].imag()};
+            memcpy(&b[e * eb], v, 16);
+        }
+    }
+}
+
+int min_blocks_for(int dtype, int W) {
+    // complex64: 1024 resident threads per SM (64 registers a thread; the
+    // coefficients live in the constant bank, not in registers).  Measured
+    // on the random 30-qubit circuit, tiles of 2^12: 3.56 ms per stage at
+    // four CTAs per SM, 3.81 ms at three, 3.86 ms at five.
+    return dtype == QSIM_C64 ? 32 >> W : 1;
+}
 
 }  // namespace
 
@@ -374,11 +596,10 @@ std::string spec_source(const StagedPlan &sp, int dtype, size_t i0, size_t i1) {
     g.C = dtype == QSIM_C64 ? "float2" : "double2";
     g.W = sp.W;
     g.o << kPrelude;
-    const int min_blocks = dtype == QSIM_C64 ? (sp.W <= 3 ? 3 : 2) : 1;
     for (size_t i = i0; i < i1; ++i) {
         const Stage &st = sp.stages[i];
         if (st.plain) continue;
-        g.stage(st, kernel_name(i), std::max<int>(1, int(st.pool.size())), min_blocks);
+        g.stage(st, kernel_name(i), std::max<int>(1, int(st.pool.size())), min_blocks_for(dtype, sp.W), false, 0);
     }
     return g.o.str();
 }
@@ -389,58 +610,24 @@ int spec_prepare(StagedPlan &sp, int dtype) {
     StagedPlan::Spec &S = sp.spec[dtype];
     if (S.ready) return QSIM_OK;
     const size_t ns = sp.stages.size();
-    // groups of about 4 stages: compiled in parallel, cached separately
-    const size_t per = 4;
-    std::vector<std::pair<size_t, size_t>> groups;
-    for (size_t i = 0; i < ns; i += per) groups.push_back({i, std::min(ns, i + per)});
-    std::vector<std::string> srcs(groups.size());
-    std::vector<std::shared_ptr<SpecLib>> libs(groups.size());
-    std::vector<size_t> todo;
+    const auto groups = stage_groups(ns);
+    std::vector<std::string> keys(groups.size());
     for (size_t gi = 0; gi < groups.size(); ++gi) {
-        srcs[gi] = spec_source(sp, dtype, groups[gi].first, groups[gi].second);
-        std::lock_guard<std::mutex> lk(g_cache_mu);
-        auto it = g_cache.find(srcs[gi]);
-        if (it != g_cache.end()) {
-            libs[gi] = it->second;
-            ++g_hits;
-        } else {
-            todo.push_back(gi);
+        std::string &k = keys[gi];
+        k = "single";
+        put(k, dtype);
+        put(k, sp.W);
+        for (size_t i = groups[gi].first; i < groups[gi].second; ++i) {
+            put(k, i);
+            put_stage(k, sp.stages[i]);
         }
     }
-    std::vector<std::string> cubins(groups.size()), logs(groups.size());
-    std::vector<int> rcs(groups.size(), QSIM_OK);
-    const auto t0 = std::chrono::steady_clock::now();
-    {
-        std::vector<std::thread> th;
-        const size_t nthreads = std::max<size_t>(1, std::min<size_t>(todo.size(), std::thread::hardware_concurrency()));
-        std::atomic<size_t> next{0};
-        for (size_t t = 0; t < nthreads; ++t)
-            th.emplace_back([&] {
-                for (size_t k; (k = next.fetch_add(1)) < todo.size();) {
-                    const size_t gi = todo[k];
-                    rcs[gi] = compile(srcs[gi], cubins[gi], logs[gi]);
-                }
-            });
-        for (std::thread &t : th) t.join();
-    }
-    for (size_t gi : todo) {
-        if (rcs[gi] != QSIM_OK)
-            return set_error(QSIM_ECUDA, "specialised stage compile failed: %.400s", logs[gi].c_str());
-        auto L = std::make_shared<SpecLib>();
-        QSIM_CUDA_TRY(cudaLibraryLoadData(&L->lib, cubins[gi].data(), nullptr, nullptr, 0, nullptr, nullptr, 0),
-                      "load specialised stages");
-        libs[gi] = L;
-        std::lock_guard<std::mutex> lk(g_cache_mu);
-        if (g_cache.size() >= CACHE_MAX) g_cache.erase(g_cache.begin());
-        g_cache[srcs[gi]] = L;
-        ++g_compiles;
-    }
-    if (!todo.empty())
-        g_compile_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::vector<std::shared_ptr<SpecLib>> libs;
+    QSIM_TRY(get_libs(groups, keys,
+                      [&](size_t gi) { return spec_source(sp, dtype, groups[gi].first, groups[gi].second); }, libs));
     S.libs.assign(libs.begin(), libs.end());
     S.kern.assign(ns, nullptr);
     S.params.assign(ns, {});
-    const size_t eb = dtype == QSIM_C64 ? 8 : 16;
     for (size_t gi = 0; gi < groups.size(); ++gi)
         for (size_t i = groups[gi].first; i < groups[gi].second; ++i) {
             const Stage &st = sp.stages[i];
@@ -448,17 +635,7 @@ int spec_prepare(StagedPlan &sp, int dtype) {
             cudaKernel_t k = nullptr;
             QSIM_CUDA_TRY(cudaLibraryGetKernel(&k, libs[gi]->lib, kernel_name(i).c_str()), "specialised stage kernel");
             S.kern[i] = k;
-            std::vector<unsigned char> &b = S.params[i];
-            b.assign(std::max<size_t>(1, st.pool.size()) * eb, 0);
-            for (size_t e = 0; e < st.pool.size(); ++e) {
-                if (dtype == QSIM_C64) {
-                    const float v[2] = {float(st.pool[e].real()), float(st.pool[e].imag())};
-                    memcpy(&b[e * eb], v, 8);
-                } else {
-                    const double v[2] = {st.pool[e].real(), st.pool[e].imag()};
-                    memcpy(&b[e * eb], v, 16);
-                }
-            }
+            pack_coefficients(st, dtype, S.params[i], 0);
         }
     S.ready = true;
     return QSIM_OK;
@@ -478,6 +655,72 @@ int spec_launch(StagedPlan &sp, int dtype, size_t i, void *psi, int n, cudaStrea
     LaunchScope ls(K_STAGE, s, 2.0 * double(uint64_t(1) << n) * double(eb), sp.flops_per_amp[i] * double(uint64_t(1) << n));
     QSIM_CUDA_TRY(cudaLaunchKernel(f, dim3(unsigned(ntiles)), dim3(32u << sp.W), args, smem, s),
                   "specialised stage launch");
+    return QSIM_OK;
+}
+
+
+// Two-state stages of the adjoint reverse sweep (complex64, tiles of
+// 2^(9 + W)): kernels for every tile stage, compiled or found in the cache.
+int spec_dual_prepare(const std::vector<Stage> &stages, int n, int W, DualSpec &out) {
+    const auto groups = stage_groups(stages.size());
+    const uint64_t ntiles = uint64_t(1) << (n - (LANE_BITS + REG_BITS + W));
+    std::vector<std::string> keys(groups.size());
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        std::string &k = keys[gi];
+        k = "dual";
+        put(k, n);
+        put(k, W);
+        for (size_t i = groups[gi].first; i < groups[gi].second; ++i) {
+            put(k, i);
+            put_stage(k, stages[i]);
+        }
+    }
+    auto source_of = [&](size_t gi) {
+        Gen g;
+        g.C = "float2";
+        g.W = W;
+        g.o << kPrelude;
+        for (size_t i = groups[gi].first; i < groups[gi].second; ++i) {
+            const Stage &st = stages[i];
+            if (st.plain) continue;
+            g.stage(st, dual_kernel_name(i), std::max<int>(1, int(st.pool.size())), 2, true, ntiles);
+        }
+        return g.o.str();
+    };
+    std::vector<std::shared_ptr<SpecLib>> libs;
+    QSIM_TRY(get_libs(groups, keys, source_of, libs));
+    out.libs.assign(libs.begin(), libs.end());
+    out.kern.assign(stages.size(), nullptr);
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        for (size_t i = groups[gi].first; i < groups[gi].second; ++i) {
+            if (stages[i].plain) continue;
+            cudaKernel_t k = nullptr;
+            QSIM_CUDA_TRY(cudaLibraryGetKernel(&k, libs[gi]->lib, dual_kernel_name(i).c_str()),
+                          "specialised two-state stage kernel");
+            out.kern[i] = k;
+        }
+    return QSIM_OK;
+}
+
+int spec_dual_launch(const DualSpec &d, const Stage &st, size_t i, float2 *psi, float2 *lam, double *partial, int n,
+                     int W, cudaStream_t s) {
+    // parameter block: { float2 c[max(1, pool)]; float gv[max(1, grads)][3]; }
+    std::vector<unsigned char> b;
+    const size_t ng = std::max<size_t>(1, st.grads.size());
+    pack_coefficients(st, QSIM_C64, b, ng * 12);
+    const size_t off = std::max<size_t>(1, st.pool.size()) * 8;
+    for (size_t g = 0; g < st.grads.size(); ++g) {
+        const float gv[3] = {float(st.grads[g].v[0]), float(st.grads[g].v[1]), float(st.grads[g].v[2])};
+        memcpy(&b[off + g * 12], gv, 12);
+    }
+    b.resize((b.size() + 7) / 8 * 8, 0);  // the struct's size: a multiple of its 8-byte alignment
+    const int nt = LANE_BITS + REG_BITS + W;
+    const uint64_t ntiles = uint64_t(1) << (n - nt);
+    const size_t smem = (size_t(1) << nt) * sizeof(float2);
+    const void *f = reinterpret_cast<const void *>(d.kern[i]);
+    void *args[4] = {&psi, &lam, &partial, b.data()};
+    QSIM_CUDA_TRY(cudaLaunchKernel(f, dim3(unsigned(ntiles)), dim3(32u << W), args, smem, s),
+                  "specialised two-state stage launch");
     return QSIM_OK;
 }
 

@@ -644,4 +644,12 @@ struct StagedPlan {
 int spec_prepare(StagedPlan &sp, int dtype);
 int spec_launch(StagedPlan &sp, int dtype, size_t i, void *psi, int n, cudaStream_t s);
 std::string spec_source(const StagedPlan &sp, int dtype, size_t i0, size_t i1);
+// specialize.cu: the two-state stages of the adjoint reverse sweep
+struct DualSpec {
+    std::vector<std::shared_ptr<SpecLib>> libs;
+    std::vector<cudaKernel_t> kern;  // per stage (plain stages: null)
+};
+int spec_dual_prepare(const std::vector<stage::Stage> &stages, int n, int W, DualSpec &out);
+int spec_dual_launch(const DualSpec &d, const stage::Stage &st, size_t i, float2 *psi, float2 *lam, double *partial,
+                     int n, int W, cudaStream_t s);
 }  // namespace qsim

@@ -119,17 +119,24 @@ def stacked_ansatz(n, layers, seed):
     return inputs.Circuit(n, gates)
 
 
+@pytest.mark.parametrize("specialize", [-1, 1])
 @pytest.mark.parametrize("maker", ["variational", "mixed", "stacked"])
-def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker):
+def test_fused_adjoint_complex64_matches_parameter_shift(q, orc, maker, specialize):
     """complex64 from 12 qubits runs the reverse sweep as two-state register
-    tiles (gradient terms accumulated per CTA): all gradients vs the oracle."""
+    tiles (gradient terms accumulated per CTA), through the op-list
+    interpreter or through kernels compiled for the circuit: all gradients
+    vs the oracle."""
     circ = {"variational": lambda: inputs.variational(13, 2, seed=7),
             "mixed": lambda: mixed_ansatz(13, 2, seed=8),
             "stacked": lambda: stacked_ansatz(12, 2, seed=10)}[maker]()
     ham = inputs.tfim(circ.n)
     rng = np.random.default_rng(9)
     thetas = rng.uniform(0, 2 * np.pi, size=(2, circ.nparams))
-    grads, en = q.adjoint_grad(circ, ham, thetas, "c64")
+    prev = q.adjoint_specialize(specialize)
+    try:
+        grads, en = q.adjoint_grad(circ, ham, thetas, "c64")
+    finally:
+        q.adjoint_specialize(prev)
     g128, e128 = q.adjoint_grad(circ, ham, thetas, "c128")   # the plain sweeps path
     for s in range(2):
         want = orc.parameter_shift_gradient(circ, ham, thetas[s])
@@ -192,7 +199,8 @@ def test_adjoint_from_a_start_state(q, orc, n, dtype, tol):
 
 
 @pytest.mark.parametrize("dtype,tol", [("c64", 2e-6), ("c128", 1e-11)])  # measured 2.5e-7 / 6.4e-13
-def test_adjoint_24q_config_against_oracle(q, dtype, tol):
+@pytest.mark.parametrize("specialize", [0, -1])
+def test_adjoint_24q_config_against_oracle(q, dtype, tol, specialize):
     """The gradient workload's own configuration (24 qubits, 10 layers, 480
     parameters, H = sum(Z_i Z_i+1 + 0.5 X_i), parameter set 0 of the seeded
     64): energy and gradient entries against the oracle's parameter-shift
@@ -204,7 +212,13 @@ def test_adjoint_24q_config_against_oracle(q, dtype, tol):
     circ = inputs.variational(24, 10, seed=5)
     ham = inputs.tfim(24)
     th = np.random.default_rng(0).uniform(0, 2 * np.pi, size=(64, circ.nparams))[:1]
-    grads, en = q.adjoint_grad(circ, ham, th, dtype)
+    if dtype == "c128" and specialize:
+        pytest.skip("complex128 runs the plain sweeps either way")
+    prev = q.adjoint_specialize(specialize)  # 0: compiled stage kernels at 24 qubits
+    try:
+        grads, en = q.adjoint_grad(circ, ham, th, dtype)
+    finally:
+        q.adjoint_specialize(prev)
     errs = [abs(grads[0, p] - v) for p, v in g["grad"]]
     print(f"adjoint24 {dtype}: energy err {abs(en[0] - g['energy']):.3e}, gradient errs "
           + " ".join(f"{e:.2e}" for e in errs))
