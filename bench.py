@@ -332,6 +332,19 @@ def run_reference(args, ws, rank):
 PLAN_KMAX = {"greedy2": 2, "staged": 4, "tc": 6, "staged-spec": 3}
 
 
+# DRAM bytes (read + write) of one launch of the 4096-circuit batch kernel,
+# ncu on `bench.py --only batch4096` (66.92 + 67.34 GB); the algorithmic
+# figure counts each stage's pass over a circuit's amplitudes once.
+NCU_TRAFFIC_BATCH4096 = 134.26e9
+
+
+def batch_roofline(bprof, peak, peak_src):
+    r = roofline_of(bprof, peak, peak_src, 2070.0, 30, 8)
+    if r is not None:
+        r["traffic"] = NCU_TRAFFIC_BATCH4096
+    return r
+
+
 def add_circuit_flops(roof, plan):
     """For a staged plan: the same launches counted with the flops of the
     circuit's gates applied one sweep each (what the fused plan replaces)."""
@@ -771,7 +784,7 @@ def other_workloads(q, torch, peak, peak_src):
     upd = sum((1 << cc.n) * len(cc.gates) for cc in circs)
     out["batch4096_c64"] = {"s_per_batch": ms / 1e3, "circuits_per_s": len(circs) / (ms / 1e3),
                             "amp_gate_updates_per_s": upd / (ms / 1e3), "config": cfg,
-                            "roofline": roofline_of(bprof, peak, peak_src, 2070.0, 30, 8),
+                            "roofline": batch_roofline(bprof, peak, peak_src),
                             "workload": "4096 variational circuits, n ~ U{12..20}, 4..12 layers, <sum Z_i Z_i+1>"}
     del b, g
     torch.cuda.empty_cache()

@@ -476,7 +476,9 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
     cudaError_t e = dev_alloc(&psi, N * sizeof(C));
     if (e == cudaSuccess) e = dev_alloc(&lam, N * sizeof(C));
     if (e == cudaSuccess) e = dev_alloc(&partial, (size_t(nrot) + 1) * prow * sizeof(double));
-    if (e == cudaSuccess) e = dev_alloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    // result rows (gradient terms + energy), two as in the fused path
+    const size_t nrow = size_t(nrot) + 1;
+    if (e == cudaSuccess) e = dev_alloc(&rows, 2 * nrow * sizeof(double));
     struct Guard {
         void *p[4];
         ~Guard() {
@@ -485,7 +487,29 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
         }
     } guard{{psi, lam, partial, rows}};
     if (e != cudaSuccess) return cuda_error(e, "adjoint buffers");
-    std::vector<double> host_rows(size_t(nrot) + 1);
+    // pinned host rows and one event per buffer
+    struct HostRows {
+        double *h = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~HostRows() {
+            if (h) cudaFreeHost(h);
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+        }
+    } hr;
+    QSIM_CUDA_TRY(cudaMallocHost(&hr.h, 2 * nrow * sizeof(double)), "adjoint host rows");
+    for (cudaEvent_t &x : hr.ev) QSIM_CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "adjoint event");
+    auto finish = [&](int set) -> int {
+        const int b = set & 1;
+        QSIM_CUDA_TRY(cudaEventSynchronize(hr.ev[b]), "adjoint sync");
+        const double *row = hr.h + size_t(b) * nrow;
+        double *gset = grads + size_t(set) * size_t(c.nparams);
+        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
+        for (size_t i = 0; i < c.gates.size(); ++i)
+            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += row[rot_of_gate[i]];
+        if (energies) energies[set] = row[nrot];
+        return QSIM_OK;
+    };
     std::vector<void *> mats;  // dense k >= 2 matrices (uploaded per set)
     HPlan<C> hplan;
     QSIM_TRY(hplan.build(hp, n, st));
@@ -585,17 +609,15 @@ int adjoint_t(const qsim_circuit &c, const void *psi0, int nsets, const double *
             k_rows<<<std::min(nrot + 1, 1024), 256, 0, st>>>(partial, nrot + 1, int(prow), rows);
             QSIM_CUDA_TRY(cudaGetLastError(), "adjoint reduce launch");
         }
-        QSIM_CUDA_TRY(cudaMemcpyAsync(host_rows.data(), rows, host_rows.size() * sizeof(double),
+        // this path uploads matrices per set and frees them after it: one set
+        // at a time
+        QSIM_CUDA_TRY(cudaMemcpyAsync(hr.h + size_t(set & 1) * nrow, rows, nrow * sizeof(double),
                                       cudaMemcpyDeviceToHost, st),
                       "adjoint result copy");
-        QSIM_CUDA_TRY(cudaStreamSynchronize(st), "adjoint sync");
+        QSIM_CUDA_TRY(cudaEventRecord(hr.ev[set & 1], st), "adjoint event record");
+        QSIM_TRY(finish(set));
         for (void *m : mats) cudaFree(m);
         mats.clear();
-        double *gset = grads + size_t(set) * size_t(c.nparams);
-        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
-        for (size_t i = 0; i < c.gates.size(); ++i)
-            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += host_rows[rot_of_gate[i]];
-        if (energies) energies[set] = host_rows[nrot];
     }
     return QSIM_OK;
 }
@@ -723,7 +745,10 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
     cudaError_t e = dev_alloc(&psi, N * sizeof(float2));
     if (e == cudaSuccess) e = dev_alloc(&lam, N * sizeof(float2));
     if (e == cudaSuccess) e = dev_alloc(&partial, std::max<size_t>(1, size_t(nrot) * ntiles) * sizeof(double));
-    if (e == cudaSuccess) e = dev_alloc(&rows, (size_t(nrot) + 1) * sizeof(double));
+    // two result rows (gradient terms + energy): set k's are read back while
+    // set k + 1 runs
+    const size_t nrow = size_t(nrot) + 1;
+    if (e == cudaSuccess) e = dev_alloc(&rows, 2 * nrow * sizeof(double));
     if (e == cudaSuccess) e = dev_alloc(&epart, size_t(blocks) * sizeof(double));
     struct Guard {
         void *p[5];
@@ -739,7 +764,30 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
         qsim_state *s;
         ~SGuard() { qsim_state_destroy(s); }
     } sguard{ps};
-    std::vector<double> host_rows(size_t(nrot) + 1);
+    // pinned host rows and one event per buffer: the host plans set k + 1
+    // while the GPU runs set k, and reads set k's rows when it is done
+    struct HostRows {
+        double *h = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~HostRows() {
+            if (h) cudaFreeHost(h);
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+        }
+    } hr;
+    QSIM_CUDA_TRY(cudaMallocHost(&hr.h, 2 * nrow * sizeof(double)), "adjoint host rows");
+    for (cudaEvent_t &x : hr.ev) QSIM_CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "adjoint event");
+    auto finish = [&](int set) -> int {
+        const int b = set & 1;
+        QSIM_CUDA_TRY(cudaEventSynchronize(hr.ev[b]), "adjoint sync");
+        const double *row = hr.h + size_t(b) * nrow;
+        double *gset = grads + size_t(set) * size_t(c.nparams);
+        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
+        for (size_t i = 0; i < c.gates.size(); ++i)
+            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += row[rot_of_gate[i]];
+        if (energies) energies[set] = row[nrot];
+        return QSIM_OK;
+    };
     const size_t smem = (size_t(1) << TB) * sizeof(float2);
     static bool attr = false;
     if (!attr) {
@@ -840,21 +888,19 @@ int adjoint_fused_c64(const qsim_circuit &c, const void *psi0, int nsets, const 
             QSIM_CUDA_TRY(cudaGetLastError(), "adjoint stage launch");
         }
         {
+            double *row = rows + size_t(set & 1) * nrow;
             LaunchScope ls(K_REDUCE, st, double(nrot) * ntiles * 8.0);
-            if (nrot) k_rows<<<std::min(nrot, 1024), 256, 0, st>>>(partial, nrot, int(ntiles), rows);
-            k_rows<<<1, 256, 0, st>>>(epart, 1, blocks, rows + nrot);
+            if (nrot) k_rows<<<std::min(nrot, 1024), 256, 0, st>>>(partial, nrot, int(ntiles), row);
+            k_rows<<<1, 256, 0, st>>>(epart, 1, blocks, row + nrot);
             QSIM_CUDA_TRY(cudaGetLastError(), "adjoint reduce launch");
+            QSIM_CUDA_TRY(cudaMemcpyAsync(hr.h + size_t(set & 1) * nrow, row, nrow * sizeof(double),
+                                          cudaMemcpyDeviceToHost, st),
+                          "adjoint result copy");
+            QSIM_CUDA_TRY(cudaEventRecord(hr.ev[set & 1], st), "adjoint event record");
         }
-        QSIM_CUDA_TRY(cudaMemcpyAsync(host_rows.data(), rows, host_rows.size() * sizeof(double),
-                                      cudaMemcpyDeviceToHost, st),
-                      "adjoint result copy");
-        QSIM_CUDA_TRY(cudaStreamSynchronize(st), "adjoint sync");
-        double *gset = grads + size_t(set) * size_t(c.nparams);
-        for (int p = 0; p < c.nparams; ++p) gset[p] = 0.0;
-        for (size_t i = 0; i < c.gates.size(); ++i)
-            if (rot_of_gate[i] >= 0) gset[c.gates[i].pindex] += host_rows[rot_of_gate[i]];
-        if (energies) energies[set] = host_rows[nrot];
+        if (set > 0) QSIM_TRY(finish(set - 1));
     }
+    QSIM_TRY(finish(nsets - 1));
     return QSIM_OK;
 }
 
