@@ -871,13 +871,32 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // accumulated in fp32 per warp and once per CTA in double
 template <int SRC>
 __global__ void __launch_bounds__(256) k_sample_chunk(const void *__restrict__ src, uint64_t N, uint64_t nchunks,
-                                                      uint64_t *__restrict__ sums, double *__restrict__ psum) {
+                                                      uint64_t *__restrict__ sums, double *__restrict__ psum,
+                                                      int vec) {
     __shared__ float ps[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t c = uint64_t(blockIdx.x) * 8 + w;
     uint64_t wsum = 0;
     float pf = 0.f;
-    if (c < nchunks) {
+    if (SRC == SRC_C64 && vec && c < nchunks) {
+        // whole chunks of a 16-byte aligned complex64 state: lane l takes the
+        // amplitude pairs l, l + 32, ... of the chunk, eight 16-byte loads in
+        // flight before their weights are formed (the integer weights add up
+        // exactly in any order)
+        const float4 *p4 = reinterpret_cast<const float4 *>(static_cast<const float2 *>(src) + c * CHUNK);
+        constexpr int U = 8, PER_LANE = CHUNK / 2 / 32;
+#pragma unroll 1
+        for (int j0 = 0; j0 < PER_LANE; j0 += U) {
+            float4 a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = __ldcs(p4 + (j0 + u) * 32 + lane);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                wsum += weight_c64(a[u].x, a[u].y) + weight_c64(a[u].z, a[u].w);
+                pf += a[u].x * a[u].x + a[u].y * a[u].y + a[u].z * a[u].z + a[u].w * a[u].w;
+            }
+        }
+    } else if (c < nchunks) {
         const uint64_t x0 = c * CHUNK;
 #pragma unroll 8
         for (int j = 0; j < CHUNK / 32; ++j) {
@@ -1050,7 +1069,9 @@ static int launch_sample_t(const void *src, uint64_t N, uint64_t nshots, uint64_
     QSIM_CUDA_TRY(cudaMemsetAsync(psum, 0, sizeof(double), st), "sampler zero");
     {
         LaunchScope ls(K_SAMPLE_CHUNK, st, double(N) * S);
-        k_sample_chunk<SRC><<<unsigned((nchunks + 7) / 8), 256, 0, st>>>(src, N, nchunks, scratch, psum);
+        // 16-byte loads when every chunk is whole and the state 16-byte aligned
+        const int vec = N % CHUNK == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        k_sample_chunk<SRC><<<unsigned((nchunks + 7) / 8), 256, 0, st>>>(src, N, nchunks, scratch, psum, vec);
         QSIM_CUDA_TRY(cudaGetLastError(), "sampler chunk launch");
     }
     {
