@@ -93,6 +93,17 @@ template <typename C> __device__ __forceinline__ C neg(C a) {
     a.y = -a.y;
     return a;
 }
+// a with its sign flipped where sb (0 or 0x80000000) says so
+__device__ __forceinline__ float2 xsign(float2 a, unsigned sb) {
+    a.x = __uint_as_float(__float_as_uint(a.x) ^ sb);
+    a.y = __uint_as_float(__float_as_uint(a.y) ^ sb);
+    return a;
+}
+__device__ __forceinline__ double2 xsign(double2 a, unsigned sb) {
+    a.x = __hiloint2double(__double2hiint(a.x) ^ int(sb), __double2loint(a.x));
+    a.y = __hiloint2double(__double2hiint(a.y) ^ int(sb), __double2loint(a.y));
+    return a;
+}
 )";
 
 // Writes the source of tile-stage kernels.  Every op is emitted for the
@@ -209,13 +220,19 @@ struct Gen {
     }
 
     void op_diag(const char *A, const StageOp &op) {
+        if (op.k == 0 && (op.flags & 1)) {  // a sign flip: branch free, the control as a sign mask
+            o << "    {\n        const unsigned sb = " << (op.tmask ? "(" + tcond(op.tmask) + ") ? 0x80000000u : 0u"
+                                                           : std::string("0x80000000u")) << ";\n";
+            for (int j = 0; j < (1 << REG_BITS); ++j)
+                if (rok(j, op.rneed)) o << "        " << A << "[" << j << "] = xsign(" << A << "[" << j << "], sb);\n";
+            o << "    }\n";
+            return;
+        }
         ctrl_open(op);
         if (op.k == 0) {
-            for (int j = 0; j < (1 << REG_BITS); ++j) {
-                if (!rok(j, op.rneed)) continue;
-                if (op.flags & 1) o << "        " << A << "[" << j << "] = neg(" << A << "[" << j << "]);\n";
-                else o << "        " << A << "[" << j << "] = cmul(" << coef(op.moff) << ", " << A << "[" << j << "]);\n";
-            }
+            for (int j = 0; j < (1 << REG_BITS); ++j)
+                if (rok(j, op.rneed))
+                    o << "        " << A << "[" << j << "] = cmul(" << coef(op.moff) << ", " << A << "[" << j << "]);\n";
             o << "    }\n";
             return;
         }
@@ -248,9 +265,12 @@ struct Gen {
             if (tm == 0) o << "        flip ^= " << pat << "u;\n";
             else o << "        if (" << tcond(tm) << ") flip ^= " << pat << "u;\n";
         }
+        // branch free: flip's bit j moved to the sign bit and XORed in (the
+        // lanes of a warp flip different registers)
         for (int j = 0; j < (1 << REG_BITS); ++j) {
-            o << "        if (flip & " << (1u << j) << "u) { v[" << j << "] = neg(v[" << j << "]);";
-            if (dual) o << " w[" << j << "] = neg(w[" << j << "]);";
+            o << "        { const unsigned sb = (flip << " << (31 - j) << ") & 0x80000000u; v[" << j << "] = xsign(v["
+              << j << "], sb);";
+            if (dual) o << " w[" << j << "] = xsign(w[" << j << "], sb);";
             o << " }\n";
         }
         o << "    }\n";
