@@ -721,9 +721,11 @@ def other_workloads(q, torch, peak, peak_src):
         s = q.State(30, dt).init_zero()
         res = {}
         if dt == "c64":
-            p = q.Plan(qc, kmax=4, mode=q.FUSE_STAGED)
-            ms, _ = ev_time(lambda: s.run_fused(p), 3, 3)
-            res["staged"] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3)}
+            for label, mode in (("staged", q.FUSE_STAGED), ("staged_spec", q.FUSE_STAGED | q.SPECIALIZE)):
+                p = q.Plan(qc, kmax=4, mode=mode)
+                ms, _ = ev_time(lambda: s.run_fused(p), 3, 3)
+                res[label] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3),
+                              "sweeps": p.info()["sweeps"]}
         ms, _ = ev_time(lambda: s.run(qc), 1 if dt == "c128" else 3, 1 if dt == "c128" else 3)
         res["plain"] = {"s_per_circuit": ms / 1e3, "gates_per_s": len(c) / (ms / 1e3)}
         out[f"qft30_{dt}"] = res
@@ -817,6 +819,22 @@ def other_workloads(q, torch, peak, peak_src):
     tuned = q.Plan.autotune(qc, s, reps=1, max_err=1e-5)
     ms_f, prof = ev_time(lambda: s.run_fused(tuned), 1, 2, profile=True)
     e_final = s.expectation(inputs.tfim_target(30, 1.0))
+    # the fastest candidate whose largest amplitude error is within 1e-5 (the
+    # stated amplitude-error bar; the 2-norm bound above rejects every FP32
+    # plan of these 3590 gates), rebuilt and timed
+    amp_ok = [e for e in tuned.table if e["ms"] > 0 and 0 <= e["max_abs"] <= 1e-5 and e["nfp32"] == 0]
+    amp_best = min(amp_ok, key=lambda e: e["ms"]) if amp_ok else None
+    amp_run = None
+    if amp_best is not None:
+        ids = {"staged": q.FUSE_STAGED, "staged-spec": q.FUSE_STAGED | q.SPECIALIZE, "tc": q.FUSE_TC,
+               "greedy2": q.FUSE_GREEDY2}
+        pa = q.Plan(qc, kmax=amp_best["kmax"], mode=ids[amp_best["mode"]])
+        ms_a, prof_a = ev_time(lambda: s.run_fused(pa), 1, 2, profile=True)
+        amp_run = {"s_per_evolution": ms_a / 1e3, "gates_per_s": len(c) / (ms_a / 1e3), "mode": amp_best["mode"],
+                   "kmax": amp_best["kmax"], "max_abs": amp_best["max_abs"], "err": amp_best["err"],
+                   "roofline": roofline_of(prof_a, peak, peak_src, 2070.0, 30, 8)}
+        add_circuit_flops(amp_run["roofline"], pa)
+        del pa
     ms_p, _ = ev_time(lambda: s.run(qc), 0, 1)
     nsteps = len(inputs.adiabatic_schedule(2.0, 0.05))
     # the whole ZZ layer of one step as a single diagonal sweep
@@ -829,6 +847,7 @@ def other_workloads(q, torch, peak, peak_src):
                   "mode": mode_name(q, tuned.mode),
                   "kmax": tuned.kmax, "autotune_table": tuned.table,
                   "roofline": roofline_of(prof, peak, peak_src, 2070.0, 30, 8)},
+        "fused_within_amplitude_bound_1e-5": amp_run,
         "plain": {"s_per_evolution": ms_p / 1e3, "gates_per_s": len(c) / (ms_p / 1e3)},
         "zz_layer_phase_sweep": {"ms": ms_z, "terms": len(zz), "roofline": zroof},
         "final_energy": e_final,
@@ -842,7 +861,7 @@ def other_workloads(q, torch, peak, peak_src):
     qc = q.QCircuit(c)
     res = {}
     for loc in ("device", "host"):
-        plan = q.SlicePlan(qc, 3, kmax=4, mode=q.FUSE_STAGED)
+        plan = q.SlicePlan(qc, 3, kmax=3, mode=q.FUSE_STAGED | q.SPECIALIZE)
         stt = sliced.SlicedState(30, 3, "c64", loc).init_zero()
         ms, prof = ev_time(lambda: stt.run(plan), 1, 2, profile=True)
         info = plan.info()
@@ -855,7 +874,8 @@ def other_workloads(q, torch, peak, peak_src):
         del stt
         torch.cuda.empty_cache()
     out["sliced30_c64_g3"] = dict(res, workload="random 30 qubits depth 20, 3 global qubits (8 slices of 27), "
-                                                "staged segments; host = page-locked host slices streamed")
+                                                "specialised staged segments (kmax 3); host = page-locked host "
+                                                "slices streamed")
     return out
 
 

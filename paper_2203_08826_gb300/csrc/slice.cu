@@ -294,7 +294,8 @@ int qsim_slice_plan_build(const qsim_circuit *c, int n_global, int kmax, int mod
     const int L = n - n_global;
     if (L > 34) return set_error(QSIM_EINVAL, "slices of %d qubits exceed the 34-qubit state limit", L);
     if (kmax < 1 || kmax > QSIM_MAX_TARGETS) return set_error(QSIM_EINVAL, "kmax=%d outside 1..6", kmax);
-    if (mode != QSIM_FUSE_GREEDY2 && mode != QSIM_FUSE_STAGED && mode != QSIM_FUSE_TC)
+    if (mode != QSIM_FUSE_GREEDY2 && mode != QSIM_FUSE_STAGED && mode != QSIM_FUSE_TC &&
+        mode != (QSIM_FUSE_STAGED | QSIM_PLAN_SPECIALIZE))
         return set_error(QSIM_EINVAL, "unknown fusion mode %d", mode);
     std::unique_ptr<qsim_slice_plan> P(new qsim_slice_plan());
     P->n = n;

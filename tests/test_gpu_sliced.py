@@ -67,7 +67,8 @@ def test_sliced_state_matches_oracle(q, orc, location, dtype, maker):
     circ = CIRCUITS[maker](n)
     psi0 = inputs.gaussian_state(n, seed=9)
     want = orc.simulate(circ, psi0)
-    for g, mode, kmax in ((1, q.FUSE_GREEDY2, 2), (3, q.FUSE_STAGED, 4), (5, q.FUSE_STAGED, 3)):
+    for g, mode, kmax in ((1, q.FUSE_GREEDY2, 2), (3, q.FUSE_STAGED, 4), (5, q.FUSE_STAGED, 3),
+                          (3, q.FUSE_STAGED | q.SPECIALIZE, 3)):
         plan = q.SlicePlan(circ, g, kmax=kmax, mode=mode)
         st = sliced.SlicedState(n, g, dtype, location).from_host(psi0).run(plan)
         err = np.max(np.abs(st.to_host().astype(np.complex128) - want))
