@@ -279,7 +279,7 @@ int pack(qsim_batch &b, int W) {
     pk.flops = 0;
     for (const qsim_circuit &c : b.circuits) {
         std::vector<stage::Stage> st;
-        QSIM_TRY(stage::plan_stage_list(c, W, false, st));
+        QSIM_TRY(stage::plan_stage_list(c, W, false, st, false));
         BCirc bc{c.n, int(pk.stages.size()), int(st.size()), 0};
         for (const stage::Stage &s : st) {
             if (s.plain) return set_error(QSIM_EUNSUPPORTED, "batch circuits need gates of at most 2 targets");

@@ -588,7 +588,10 @@ double stage_exec_flops_per_amp(const Stage &st);
 // Split a circuit into stages for tiles of 2^(9 + W) amplitudes (after pair
 // fusion, when the circuit has no gradient markers).  With `limits` the op,
 // phase and pool counts of a stage stay within one kernel parameter block.
-int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out);
+// With `lookahead` each stage repeatedly takes the gate that adds the fewest
+// new tile qubits (fewer stages on random circuits); without it, one pass in
+// circuit order (the batch kernel's plans, where it measured faster).
+int plan_stage_list(const qsim_circuit &c, int W, bool limits, std::vector<Stage> &out, bool lookahead = true);
 
 // Kernel parameter block of one tile stage.
 template <typename C> inline void make_params(const Stage &st, StageParams<C> &prm) {

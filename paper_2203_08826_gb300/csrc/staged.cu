@@ -580,7 +580,7 @@ static void pair_fuse(const qsim_circuit &c, std::vector<GateRec> &gates, std::v
     }
 }
 
-int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stage> &out) {
+int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stage> &out, bool lookahead) {
     // pair fusion first, except for the reverse sweep of the adjoint method,
     // whose gradient markers must stay between the gates they sit between
     qsim_circuit fused;
@@ -643,55 +643,87 @@ int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stag
     for (size_t i = 0; i < remaining.size(); ++i) remaining[i] = int(i);
     size_t limit = remaining.size();  // largest number of gates one stage may take
     while (!remaining.empty()) {
-        uint64_t blocked = 0;
-        std::vector<int> tile;
-        std::vector<int> sched, rest;
-        bool plain_emitted = false;
-        for (size_t r = 0; r < remaining.size(); ++r) {
-            const int gi = remaining[r];
-            const GateClass &g = cls[gi];
-            const uint64_t qs = qmask(g.op.targets, g.op.k) | qmask(g.op.controls, g.op.c);
-            if ((qs & blocked) || sched.size() >= limit) {
-                blocked |= qs;
-                rest.push_back(gi);
-                continue;
-            }
-            if (g.kind == GateClass::DIAG) {
-                sched.push_back(gi);
-                continue;
-            }
-            if (g.kind == GateClass::OTHER) {
-                if (sched.empty() && !plain_emitted && r == 0) {
-                    Stage st;
-                    st.plain = true;
-                    st.op = g.op;
-                    source(gi, st.gates);
-                    out.push_back(std::move(st));
-                    plain_emitted = true;
-                    continue;
-                }
-                blocked |= qs;
-                rest.push_back(gi);
-                continue;
-            }
-            std::vector<int> add;
-            for (int t = 0; t < g.op.k; ++t) {
-                const int q = g.op.targets[t];
-                if (q >= LANE_BITS && std::find(tile.begin(), tile.end(), q) == tile.end()) add.push_back(q);
-            }
-            if (int(tile.size() + add.size()) <= cap) {
-                tile.insert(tile.end(), add.begin(), add.end());
-                sched.push_back(gi);
-            } else {
-                blocked |= qs;
-                rest.push_back(gi);
-            }
-        }
-        if (sched.empty()) {
-            remaining.swap(rest);
+        // a leading gate no tile holds (more than two dense targets) runs as a
+        // plain sweep of its own
+        if (cls[size_t(remaining[0])].kind == GateClass::OTHER) {
+            const int g0 = remaining[0];
+            Stage st;
+            st.plain = true;
+            st.op = cls[size_t(g0)].op;
+            source(g0, st.gates);
+            out.push_back(std::move(st));
+            remaining.erase(remaining.begin());
             limit = remaining.size();
             continue;
         }
+        // Fill the tile (lookahead): repeatedly take, among the gates that
+        // commute with every earlier gate not yet taken (none of those touches
+        // their qubits), the one that adds the fewest new tile qubits (gates
+        // already inside the tile and diagonal gates first, in circuit order).
+        // Any prefix of the picks is an order-respecting schedule.
+        std::vector<int> tile, sched, rest;
+        if (!lookahead) {
+            // one pass in circuit order: each gate that fits joins the tile;
+            // one that does not is deferred and blocks its qubits
+            uint64_t blocked = 0;
+            for (int gi : remaining) {
+                const GateClass &g = cls[size_t(gi)];
+                const uint64_t qs = qmask(g.op.targets, g.op.k) | qmask(g.op.controls, g.op.c);
+                bool take = !(qs & blocked) && sched.size() < limit && g.kind != GateClass::OTHER;
+                std::vector<int> add;
+                if (take && g.kind != GateClass::DIAG) {
+                    for (int t = 0; t < g.op.k; ++t) {
+                        const int q = g.op.targets[t];
+                        if (q >= LANE_BITS && std::find(tile.begin(), tile.end(), q) == tile.end()) add.push_back(q);
+                    }
+                    take = int(tile.size() + add.size()) <= cap;
+                }
+                if (take) {
+                    tile.insert(tile.end(), add.begin(), add.end());
+                    sched.push_back(gi);
+                } else {
+                    blocked |= qs;
+                    rest.push_back(gi);
+                }
+            }
+        } else {
+            rest = remaining;
+        }
+        while (lookahead && sched.size() < limit) {
+            uint64_t blocked = 0;
+            int best = -1, best_add = 1 << 30;
+            for (size_t r = 0; r < rest.size(); ++r) {
+                const GateClass &g = cls[size_t(rest[r])];
+                const uint64_t qs = qmask(g.op.targets, g.op.k) | qmask(g.op.controls, g.op.c);
+                if (qs & blocked) {
+                    blocked |= qs;
+                    continue;
+                }
+                blocked |= qs;  // later gates on these qubits wait for this one
+                if (g.kind == GateClass::OTHER) continue;
+                int add = 0;
+                if (g.kind != GateClass::DIAG)
+                    for (int t = 0; t < g.op.k; ++t) {
+                        const int q = g.op.targets[t];
+                        if (q >= LANE_BITS && std::find(tile.begin(), tile.end(), q) == tile.end()) ++add;
+                    }
+                if (int(tile.size()) + add > cap || add >= best_add) continue;
+                best = int(r);
+                best_add = add;
+                if (add == 0) break;
+            }
+            if (best < 0) break;
+            const int gi = rest[size_t(best)];
+            rest.erase(rest.begin() + best);
+            const GateClass &g = cls[size_t(gi)];
+            if (g.kind != GateClass::DIAG)
+                for (int t = 0; t < g.op.k; ++t) {
+                    const int q = g.op.targets[t];
+                    if (q >= LANE_BITS && std::find(tile.begin(), tile.end(), q) == tile.end()) tile.push_back(q);
+                }
+            sched.push_back(gi);
+        }
+        if (sched.empty()) return set_error(QSIM_EINVAL, "staged planner: no gate fits a tile");
         for (int q = LANE_BITS; q < n && int(tile.size()) < cap; ++q)
             if (std::find(tile.begin(), tile.end(), q) == tile.end()) tile.push_back(q);
         Stage st;
@@ -702,8 +734,8 @@ int plan_stage_list(const qsim_circuit &c0, int W, bool limits, std::vector<Stag
         const int rc = emit_stage_ops(st, gl, W, limits);
         if (rc == QSIM_EUNSUPPORTED) {
             // too many ops for one parameter block: retry with half the gates
-            // (any prefix of an order-respecting schedule is one too); a plain
-            // stage emitted in this scan stays, its gate is not in `merged`
+            // (the same picks, cut short: a prefix of the picks is an
+            // order-respecting schedule too)
             limit = std::max<size_t>(1, sched.size() / 2);
             std::vector<int> merged(sched);
             merged.insert(merged.end(), rest.begin(), rest.end());
