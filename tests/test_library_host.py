@@ -249,6 +249,34 @@ def test_specialized_stage_source_compiles(q, tmp_path, dtype):
         q.Plan(inputs.random_circuit(14, 2, seed=1), kmax=6, mode=q.FUSE_TC | q.SPECIALIZE)
 
 
+def test_specialized_source_depends_on_structure_only(q):
+    """The generated stage kernels take the coefficients as parameters: two
+    random circuits that differ only in their 1-qubit gates' angles give the
+    same source (one compiled module serves both), and a different
+    structure gives another."""
+    a = inputs.random_circuit(16, 6, seed=3)
+    rng = np.random.default_rng(11)
+    b = inputs.Circuit(16, [inputs.Gate(g.name, g.targets, g.controls, inputs.haar_su2_quaternion(rng))
+                            if g.name == "su2" else g for g in a.gates])
+    c = inputs.random_circuit(16, 6, seed=4)
+    src = lambda circ: q.Plan(circ, kmax=3, mode=q.FUSE_STAGED | q.SPECIALIZE).source("c64")
+    assert src(a) == src(b)
+    assert src(a) != src(c)
+    assert "p.c[" in src(a) and not re.search(r"\d\.\d{4,}", src(a))  # no coefficient value in the text
+
+
+def test_lookahead_planner_stage_counts(q):
+    """The lookahead planner on the 30-qubit depth-20 random circuit: 26
+    stages at kmax 3 and 22 at kmax 4 (the one-pass schedule needed 31 and
+    27), each stage's tile within 4 + kmax slots."""
+    c = inputs.random_circuit(30, 20, seed=2022)
+    for kmax, want in ((3, 26), (4, 22)):
+        p = q.Plan(c, kmax=kmax, mode=q.FUSE_STAGED)
+        stages = p.stages()
+        assert len(stages) == want
+        assert all(len(st["slots"]) == 4 + kmax for st in stages if not st["plain"])
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
