@@ -93,6 +93,52 @@ template <typename C> __device__ __forceinline__ C neg(C a) {
     a.y = -a.y;
     return a;
 }
+// paired FP32 arithmetic (fma.rn.f32x2): two lanes of a 64-bit register
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(u64 r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// complex products with each coefficient m given as the pairs (m.x, m.x) and
+// (-m.y, m.y) (cc[2e], cc[2e + 1]): m x = (m.x, m.x) (x.x, x.y) + (-m.y, m.y) (x.y, x.x),
+// in the order of cmul / cmad above
+__device__ __forceinline__ void u1p(float2 &a, float2 &b, const u64 *cc) {
+    const u64 X = pk2(a.x, a.y), Xs = pk2(a.y, a.x), Y = pk2(b.x, b.y), Ys = pk2(b.y, b.x);
+    a = up2(fma2(cc[3], Ys, fma2(cc[2], Y, fma2(cc[1], Xs, mul2(cc[0], X)))));
+    b = up2(fma2(cc[7], Ys, fma2(cc[6], Y, fma2(cc[5], Xs, mul2(cc[4], X)))));
+}
+__device__ __forceinline__ void u2p(float2 &a0, float2 &a1, float2 &a2, float2 &a3, const u64 *cc) {
+    const u64 X0 = pk2(a0.x, a0.y), S0 = pk2(a0.y, a0.x), X1 = pk2(a1.x, a1.y), S1 = pk2(a1.y, a1.x);
+    const u64 X2 = pk2(a2.x, a2.y), S2 = pk2(a2.y, a2.x), X3 = pk2(a3.x, a3.y), S3 = pk2(a3.y, a3.x);
+#define QSIM_U2P_ROW(R, OUT)                                   \
+    {                                                          \
+        const u64 *m = cc + 8 * R;                             \
+        u64 t = fma2(m[1], S0, mul2(m[0], X0));                \
+        t = fma2(m[3], S1, fma2(m[2], X1, t));                 \
+        t = fma2(m[5], S2, fma2(m[4], X2, t));                 \
+        OUT = up2(fma2(m[7], S3, fma2(m[6], X3, t)));          \
+    }
+    QSIM_U2P_ROW(0, a0)
+    QSIM_U2P_ROW(1, a1)
+    QSIM_U2P_ROW(2, a2)
+    QSIM_U2P_ROW(3, a3)
+#undef QSIM_U2P_ROW
+}
 // a with its sign flipped where sb (0 or 0x80000000) says so
 __device__ __forceinline__ float2 xsign(float2 a, unsigned sb) {
     a.x = __uint_as_float(__float_as_uint(a.x) ^ sb);
@@ -114,6 +160,7 @@ struct Gen {
     std::ostringstream o;
     const char *C;  // "float2" / "double2"
     int W;
+    bool paired = false;  // register ops in paired FP32 (complex64 single-state stages)
 
     // global index bits of register index j in phase P
     static uint64_t reg_offset(const Phase &P, int j) {
@@ -148,6 +195,10 @@ struct Gen {
     void u1_reg(const char *A, int rb, int moff, int rneed) {
         for (int i = 0; i < (1 << REG_BITS); ++i) {
             if ((i >> rb) & 1 || !rok(i, rneed)) continue;
+            if (paired)
+                o << "        u1p(" << A << "[" << i << "], " << A << "[" << (i | (1 << rb)) << "], &p.cc["
+                  << 2 * moff << "]);\n";
+            else
             o << "        u1(" << A << "[" << i << "], " << A << "[" << (i | (1 << rb)) << "], " << coef(moff) << ", "
               << coef(moff + 1) << ", " << coef(moff + 2) << ", " << coef(moff + 3) << ");\n";
         }
@@ -171,11 +222,13 @@ struct Gen {
         if (!la && !lb) {  // two register targets: the interpreter's u2_reg
             const int JA = op.a - POS_REG, JB = op.b - POS_REG;
             ctrl_open(op);
-            o << "        const " << C << " *m = &" << coef(m) << ";\n";
+            if (paired) o << "        const u64 *m = &p.cc[" << 2 * m << "];\n";
+            else o << "        const " << C << " *m = &" << coef(m) << ";\n";
             for (int i = 0; i < (1 << REG_BITS); ++i) {
                 if (i & ((1 << JA) | (1 << JB)) || !rok(i, op.rneed)) continue;
-                o << "        u2(" << A << "[" << i << "], " << A << "[" << (i | (1 << JB)) << "], " << A << "["
-                  << (i | (1 << JA)) << "], " << A << "[" << (i | (1 << JA) | (1 << JB)) << "], m);\n";
+                o << "        " << (paired ? "u2p(" : "u2(") << A << "[" << i << "], " << A << "[" << (i | (1 << JB))
+                  << "], " << A << "[" << (i | (1 << JA)) << "], " << A << "[" << (i | (1 << JA) | (1 << JB))
+                  << "], m);\n";
             }
             o << "    }\n";
             return;
@@ -389,6 +442,7 @@ struct Gen {
     void stage(const Stage &st, const std::string &name, int ncoef, int min_blocks, bool dual, uint64_t ntiles) {
         const int ng = std::max<int>(1, int(st.grads.size()));
         o << "struct P_" << name << " { " << C << " c[" << ncoef << "];";
+        if (paired) o << " u64 cc[" << 2 * ncoef << "];";
         if (dual) o << " float gv[" << ng << "][3];";
         o << " };\n";
         if (dual) {
@@ -579,7 +633,10 @@ int get_libs(const std::vector<std::pair<size_t, size_t>> &groups, const std::ve
 }
 
 std::vector<std::pair<size_t, size_t>> stage_groups(size_t ns) {
-    const size_t per = 4;  // stages per program: compiled in parallel, cached separately
+    // stages per program: programs compile in parallel host threads and are
+    // cached separately; two keeps a 26-stage plan's 13 programs within the
+    // host's cores
+    const size_t per = 2;
     std::vector<std::pair<size_t, size_t>> groups;
     for (size_t i = 0; i < ns; i += per) groups.push_back({i, std::min(ns, i + per)});
     return groups;
@@ -600,12 +657,19 @@ void pack_coefficients(const Stage &st, int dtype, std::vector<unsigned char> &b
     }
 }
 
-int min_blocks_for(int dtype, int W) {
-    // complex64: 1024 resident threads per SM (64 registers a thread; the
-    // coefficients live in the constant bank, not in registers).  Measured
-    // on the random 30-qubit circuit, tiles of 2^12: 3.56 ms per stage at
-    // four CTAs per SM, 3.81 ms at three, 3.86 ms at five.
-    return dtype == QSIM_C64 ? 32 >> W : 1;
+// Resident CTAs per SM the kernels are compiled for.  With scalar FMAs four
+// CTAs of 256 (64 registers; the coefficients are constant-bank operands)
+// measured best (random 30-qubit circuit, one-pass plan: 3.56 ms per stage,
+// 3.81 ms at three CTAs, 3.86 ms at five).  The complex64 single-state
+// stages run their register ops in paired FP32 (fma.rn.f32x2 on (re, im)
+// pairs, the coefficients as host-made pairs in the parameter block), which
+// wants more registers: 768 resident threads per SM for tiles of up to 2^12
+// (lookahead plan: three CTAs of 256, 3.79 ms per stage, against 3.94 ms at
+// four CTAs with spills and 3.98 ms for the scalar FMAs at four), 1024 for
+// tiles of 2^13.
+int min_blocks_single(int dtype, int W) {
+    if (dtype != QSIM_C64) return 1;
+    return W >= 4 ? 2 : 24 >> W;
 }
 
 }  // namespace
@@ -615,11 +679,12 @@ std::string spec_source(const StagedPlan &sp, int dtype, size_t i0, size_t i1) {
     Gen g;
     g.C = dtype == QSIM_C64 ? "float2" : "double2";
     g.W = sp.W;
+    g.paired = dtype == QSIM_C64;
     g.o << kPrelude;
     for (size_t i = i0; i < i1; ++i) {
         const Stage &st = sp.stages[i];
         if (st.plain) continue;
-        g.stage(st, kernel_name(i), std::max<int>(1, int(st.pool.size())), min_blocks_for(dtype, sp.W), false, 0);
+        g.stage(st, kernel_name(i), std::max<int>(1, int(st.pool.size())), min_blocks_single(dtype, sp.W), false, 0);
     }
     return g.o.str();
 }
@@ -656,6 +721,16 @@ int spec_prepare(StagedPlan &sp, int dtype) {
             QSIM_CUDA_TRY(cudaLibraryGetKernel(&k, libs[gi]->lib, kernel_name(i).c_str()), "specialised stage kernel");
             S.kern[i] = k;
             pack_coefficients(st, dtype, S.params[i], 0);
+            if (dtype == QSIM_C64) {  // the coefficient pairs of the paired register ops
+                std::vector<unsigned char> &b = S.params[i];
+                const size_t nc = std::max<size_t>(1, st.pool.size());
+                b.resize(nc * 8 + nc * 16, 0);
+                for (size_t e = 0; e < st.pool.size(); ++e) {
+                    const float mx = float(st.pool[e].real()), my = float(st.pool[e].imag());
+                    const float pr[4] = {mx, mx, -my, my};
+                    memcpy(&b[nc * 8 + e * 16], pr, 16);
+                }
+            }
         }
     S.ready = true;
     return QSIM_OK;
