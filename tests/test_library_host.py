@@ -240,6 +240,10 @@ def test_specialized_stage_source_compiles(q, tmp_path, dtype):
         src = p.source(dtype)
         nst = sum(1 for st in p.stages() if not st["plain"])
         assert src.count("__global__") == nst > 0
+        # complex64 register ops in paired FP32 with host-made coefficient
+        # pairs; complex128 in scalar FP64
+        paired = ("u2p(" in src or "u1p(" in src) and " u64 cc[" in src
+        assert paired == (dtype == "c64")
         f = tmp_path / f"stages_{dtype}.cu"
         f.write_text(src)
         r = subprocess.run([nvcc, "-cubin", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17",
