@@ -9,9 +9,12 @@
 // every position, control mask, register index and coefficient offset a
 // constant of the source -- and compiles the plan's kernels with NVRTC for
 // sm_103a.  The coefficients stay out of the source: each kernel takes them
-// as a by-value parameter block (read straight from the constant bank by the
-// FMAs), so two circuits of the same structure with other angles share one
-// compiled module.  Modules are cached by their source text.
+// as a by-value parameter block (scalar FP64 / lane ops read them from the
+// constant bank; the complex64 register ops read host-made coefficient pairs
+// for the paired FP32 instructions), so two circuits of the same structure
+// with other angles share one compiled module.  Modules are cached by a
+// structural fingerprint of their stages.  The adjoint method's reverse
+// sweep gets two-state kernels from the same generator (dual).
 //
 // The arithmetic per op is the interpreter's (same products, same order), so
 // both executors give the same amplitudes up to the compiler's contraction
@@ -518,7 +521,7 @@ struct Gen {
 };
 
 std::mutex g_cache_mu;
-std::map<std::string, std::shared_ptr<SpecLib>> g_cache;  // program source -> library
+std::map<std::string, std::shared_ptr<SpecLib>> g_cache;  // structural key -> library
 constexpr size_t CACHE_MAX = 64;
 double g_compile_s = 0.0;  // seconds spent in NVRTC since load
 uint64_t g_compiles = 0, g_hits = 0;
