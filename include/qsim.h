@@ -200,7 +200,9 @@ typedef struct qsim_plan qsim_plan;
  * position, mask and coefficient offset a constant) and compiled with NVRTC
  * for sm_103a when the plan first runs on a dtype; the coefficients are
  * kernel parameters, so circuits of the same structure with other angles
- * reuse the compiled code (an in-process cache keyed by the source).  The
+ * reuse the compiled code (an in-process cache keyed by the stages'
+ * structure).  Complex64 register ops run in paired FP32 (fma.rn.f32x2 on
+ * (re, im) pairs), with the scalar kernels' products in the same order.  The
  * first run pays the compile (about a second per few stages, in parallel
  * threads); QSIM_ECUDA with the compiler's log if it fails.  qsim_plan_info
  * reports the flag in *mode.
@@ -222,8 +224,10 @@ QSIM_API int qsim_plan_flops(const qsim_plan *p, double *executed, double *circu
 QSIM_API int qsim_spec_stats(double *compile_s, uint64_t *compiles, uint64_t *cache_hits);
 /* CUDA source of the specialised kernels of a staged plan's tile stages
  * (one kernel per stage, `qsim_spec_stage_<i>`) for dtype, NUL-terminated
- * and truncated to len bytes; *needed receives the full length + 1.
- * Host-only (works on any staged plan, specialised or not). */
+ * and truncated to len bytes; *needed (may be NULL) receives the full length
+ * + 1, and buf may be NULL with len 0 to ask for it.  Host-only (works on any
+ * staged plan, specialised or not); QSIM_EINVAL for a plan that is not
+ * staged or a dtype other than QSIM_C64 / QSIM_C128. */
 QSIM_API int qsim_plan_source(const qsim_plan *p, int dtype, char *buf, size_t len, size_t *needed);
 QSIM_API int qsim_plan_destroy(qsim_plan *p);
 /* Number of sweeps (HBM passes) and of source gates the plan covers. */
