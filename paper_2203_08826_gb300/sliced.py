@@ -134,7 +134,10 @@ def run_distributed(plan: "_b.SlicePlan", slices: dict, engine, group=None):
     local bit differs from the slice's global bit, swaps it with the partner
     rank (send and receive posted together, slices in increasing order on
     both sides, so the pairs line up) and unpacks what arrived into the same
-    half.
+    half.  The slices are pipelined two deep: slice i is packed and its
+    transfer posted before the host waits for slice i - 1's transfer, whose
+    half is unpacked while slice i's is in flight (two send and two receive
+    buffers at a time).
     """
     torch = _torch()
     import torch.distributed as dist
@@ -163,13 +166,24 @@ def run_distributed(plan: "_b.SlicePlan", slices: dict, engine, group=None):
             peer = dist.get_global_rank(group, peer)
         mybit = (rank >> peer_bit) & 1
         half_bit = 1 - mybit  # the half this rank gives away and receives
+        pending = None  # (slice, send, recv, requests) of the transfer in flight
         for i in own:
             send = engine.pack(slices[i], l, half_bit)
             recv = torch.empty_like(send)
             engine.synchronize()
             ops = [dist.P2POp(dist.isend, torch.view_as_real(send), peer, group),
                    dist.P2POp(dist.irecv, torch.view_as_real(recv), peer, group)]
-            for req in dist.batch_isend_irecv(ops):
-                req.wait()
-            engine.unpack(slices[i], l, half_bit, recv)
+            reqs = dist.batch_isend_irecv(ops)
+            if pending is not None:
+                _finish_transfer(engine, slices, l, half_bit, pending)
+            pending = (i, send, recv, reqs)
+        if pending is not None:
+            _finish_transfer(engine, slices, l, half_bit, pending)
     engine.synchronize()
+
+
+def _finish_transfer(engine, slices, l, half_bit, pending):
+    i, _send, recv, reqs = pending  # the send buffer lives until its request is done
+    for req in reqs:
+        req.wait()
+    engine.unpack(slices[i], l, half_bit, recv)
