@@ -269,6 +269,29 @@ def test_specialized_source_depends_on_structure_only(q):
     assert "p.c[" in src(a) and not re.search(r"\d\.\d{4,}", src(a))  # no coefficient value in the text
 
 
+def test_staged_plan_splits_a_stage_over_the_parameter_limit(q, orc):
+    """120 dense 2-qubit gates that all fit one tile outgrow one kernel
+    parameter block (768 complex coefficients, 16 per 4x4): the planner
+    retries with a prefix of its picks, and the stages still replay the
+    circuit."""
+    rng = np.random.default_rng(1)
+    n = 12
+    gates = []
+    for _ in range(120):
+        a, b = (int(v) for v in rng.choice(range(5, 12), 2, replace=False))
+        gates.append(inputs.Gate("matrix", (a, b), (), (), -1, inputs.random_dense_gate(rng, 2)))
+    circ = inputs.Circuit(n, gates)
+    stages = q.Plan(circ, kmax=3, mode=q.FUSE_STAGED).stages()
+    assert len(stages) >= 3 and all(len(st["gates"]) <= 48 for st in stages)
+    order = [gi for st in stages for gi in st["gates"]]
+    assert sorted(order) == list(range(len(circ)))
+    psi0 = inputs.gaussian_state(n, seed=2)
+    psi = psi0.copy()
+    for gi in order:
+        orc.apply_gate(psi, circ.gates[gi])
+    assert np.max(np.abs(psi - orc.simulate(circ, psi0))) < 1e-12
+
+
 def test_lookahead_planner_stage_counts(q):
     """The lookahead planner on the 30-qubit depth-20 random circuit: 26
     stages at kmax 3 and 22 at kmax 4 (the one-pass schedule needed 31 and
