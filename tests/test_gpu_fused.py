@@ -159,6 +159,25 @@ def test_specialized_plan_many_tiles_and_cache(q, orc):
     assert np.max(np.abs(s.to_host() - orc.simulate(b, psi0))) <= TOL["c64"]
 
 
+@pytest.mark.parametrize("specialize", [False, True])
+def test_staged_stages_split_over_the_parameter_limit(q, orc, specialize):
+    """120 dense 2-qubit gates inside one tile's qubits: more coefficients than
+    one kernel parameter block holds, so the planner splits the stage; both
+    executors against the oracle."""
+    rng = np.random.default_rng(1)
+    n = 12
+    gates = []
+    for _ in range(120):
+        a, b = (int(v) for v in rng.choice(range(5, 12), 2, replace=False))
+        gates.append(inputs.Gate("matrix", (a, b), (), (), -1, inputs.random_dense_gate(rng, 2)))
+    circ = inputs.Circuit(n, gates)
+    psi0 = inputs.gaussian_state(n, seed=2)
+    want = orc.simulate(circ, psi0)
+    mode = q.FUSE_STAGED | (q.SPECIALIZE if specialize else 0)
+    got = run_plan(q, circ, "c64", psi0, mode, 3)
+    assert np.max(np.abs(got - want)) <= TOL["c64"]
+
+
 def test_specialized_rejects_other_modes(q):
     with pytest.raises(q.QsimError):
         q.Plan(inputs.random_circuit(14, 2, seed=1), kmax=6, mode=q.FUSE_TC | q.SPECIALIZE)
