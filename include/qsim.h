@@ -282,6 +282,15 @@ QSIM_API int qsim_plan_tc_set_precision(qsim_plan *p, int npasses, const int *pr
  * gates on distinct qubits).  QSIM_EINVAL for other plans (a staged request
  * on fewer than 9 qubits builds a greedy plan). */
 QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, int *ngates, int *gates, int *nslots, int *slots);
+/* Stage i of a QSIM_FUSE_STAGED plan as text: the op list its kernels run
+ * (positions, masks, coefficient offsets), the phases (register, warp and
+ * shared-memory assignments of the tile qubits) and the coefficient pool in
+ * full precision; one item per line, the format documented at the
+ * definition.  NUL-terminated and truncated to len bytes; *needed receives
+ * the full length + 1.  Host-only (for checking the op lists against the
+ * gate-by-gate result without a GPU); QSIM_EINVAL for other plans or i out
+ * of range. */
+QSIM_API int qsim_plan_stage_dump(const qsim_plan *p, int i, char *buf, size_t len, size_t *needed);
 /* Autotuner: builds the candidate plans (staged tiles of 2^12 and 2^13
  * amplitudes; for complex64 also tensor-core blocks of 5 and 6 qubits, for
  * complex128 one sweep per gate (greedy fusion with kmax = 1)), runs each on

@@ -67,6 +67,7 @@ _SIGS = {
     "qsim_plan_block": ([P, I, P, P, P], I),
     "qsim_plan_describe": ([P, P, ctypes.c_size_t], I),
     "qsim_plan_source": ([P, I, P, ctypes.c_size_t, P], I),
+    "qsim_plan_stage_dump": ([P, I, P, ctypes.c_size_t, P], I),
     "qsim_spec_stats": ([P, P, P], I),
     "qsim_plan_flops": ([P, P, P], I),
     "qsim_adjoint_specialize": ([I, P], I),
@@ -305,6 +306,14 @@ class Plan:
         e, c = ctypes.c_double(), ctypes.c_double()
         _check(lib().qsim_plan_flops(self.handle, ctypes.byref(e), ctypes.byref(c)))
         return {"executed": e.value, "circuit": c.value}
+
+    def stage_dump(self, i: int) -> str:
+        """Stage i of a staged plan as text (op list, phases, coefficients)."""
+        need = ctypes.c_size_t()
+        _check(lib().qsim_plan_stage_dump(self.handle, i, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().qsim_plan_stage_dump(self.handle, i, buf, need.value, None))
+        return buf.value.decode()
 
     def source(self, dtype: str = "c64") -> str:
         """CUDA source of the plan's specialised stage kernels (staged plans)."""

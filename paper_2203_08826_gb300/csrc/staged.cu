@@ -965,3 +965,57 @@ extern "C" QSIM_API int qsim_plan_stage(const qsim_plan *p, int i, int *plain, i
         for (size_t j = 0; j < st.slots.size(); ++j) slots[j] = st.slots[j];
     return QSIM_OK;
 }
+
+// Stage i of a staged plan as text: the op list the kernels run (for
+// checking the planner and the op lists against the gate-by-gate result on
+// the host).  Lines:
+//   stage <i> plain <0|1> W <W> phase0 <p>
+//   slots <q ...>
+//   phase <rq0..rq3> | <wq0..wq{W-1}> | <rslot0..3> | <wslot0..>
+//   op <type> <a> <b> <k> <rneed> <flags> <tmask> <moff> <dq0..dq5>
+//   pool <re> <im>
+//   aux <u64>
+extern "C" QSIM_API int qsim_plan_stage_dump(const qsim_plan *p, int i, char *buf, size_t len, size_t *needed) {
+    using namespace qsim;
+    if (!p || !p->staged) return set_error(QSIM_EINVAL, "not a staged plan");
+    const std::vector<stage::Stage> &stages = p->staged->stages;
+    if (i < 0 || i >= int(stages.size())) return set_error(QSIM_EINVAL, "stage %d outside the plan", i);
+    const stage::Stage &st = stages[size_t(i)];
+    const int W = p->staged->W;
+    std::string o;
+    char line[512];
+    snprintf(line, sizeof line, "stage %d plain %d W %d phase0 %d\nslots", i, st.plain ? 1 : 0, W, st.phase0);
+    o += line;
+    for (int q : st.slots) o += " " + std::to_string(q);
+    o += "\n";
+    for (const stage::Phase &P : st.phases) {
+        o += "phase";
+        for (int b = 0; b < stage::REG_BITS; ++b) o += " " + std::to_string(int(P.rq[b]));
+        o += " |";
+        for (int b = 0; b < W; ++b) o += " " + std::to_string(int(P.wq[b]));
+        o += " |";
+        for (int b = 0; b < stage::REG_BITS; ++b) o += " " + std::to_string(int(P.rslot[b]));
+        o += " |";
+        for (int b = 0; b < W; ++b) o += " " + std::to_string(int(P.wslot[b]));
+        o += "\n";
+    }
+    for (const stage::StageOp &op : st.ops) {
+        snprintf(line, sizeof line, "op %d %d %d %d %d %d %llu %d", int(op.type), int(op.a), int(op.b), int(op.k),
+                 int(op.rneed), int(op.flags), (unsigned long long)op.tmask, op.moff);
+        o += line;
+        for (int t = 0; t < QSIM_MAX_TARGETS; ++t) o += " " + std::to_string(int(op.dq[t]));
+        o += "\n";
+    }
+    for (const cd &c : st.pool) {
+        snprintf(line, sizeof line, "pool %.17g %.17g\n", c.real(), c.imag());
+        o += line;
+    }
+    for (uint64_t a : st.aux) o += "aux " + std::to_string((unsigned long long)a) + "\n";
+    if (needed) *needed = o.size() + 1;
+    if (buf && len) {
+        const size_t m = std::min(len - 1, o.size());
+        memcpy(buf, o.data(), m);
+        buf[m] = 0;
+    }
+    return QSIM_OK;
+}

@@ -304,6 +304,30 @@ def test_lookahead_planner_stage_counts(q):
         assert all(len(st["slots"]) == 4 + kmax for st in stages if not st["plain"])
 
 
+@pytest.mark.parametrize("kmax", [1, 3, 4])
+@pytest.mark.parametrize("maker", ["random", "variational", "qft", "mixed", "lanes"])
+def test_stage_op_lists_replay_the_circuit(q, orc, maker, kmax):
+    """The op lists a staged plan gives its kernels (qsim_plan_stage_dump:
+    fused 4x4 blocks, batched 1-qubit ops, lane ops with their coefficient
+    layouts, controls, diagonals, sign-flip batches, exchanges between
+    phases), run by a host model of the kernels' data layout in complex128,
+    against the oracle's gate-by-gate result."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import stage_emulator
+    from test_gpu_fused import lane_pair_circuit, mixed_circuit
+    n = 14
+    circ = {"random": lambda: inputs.random_circuit(n, 5, seed=3),
+            "variational": lambda: inputs.variational(n, 3, seed=4),
+            "qft": lambda: inputs.qft(n),
+            "mixed": lambda: mixed_circuit(n, seed=7),
+            "lanes": lambda: lane_pair_circuit(n, seed=8)}[maker]()
+    psi0 = inputs.gaussian_state(n, seed=6)
+    plan = q.Plan(circ, kmax=kmax, mode=q.FUSE_STAGED)
+    got = stage_emulator.run_plan(plan, circ, psi0, orc)
+    assert np.max(np.abs(got - orc.simulate(circ, psi0))) < 1e-12
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
