@@ -328,6 +328,24 @@ def test_stage_op_lists_replay_the_circuit(q, orc, maker, kmax):
     assert np.max(np.abs(got - orc.simulate(circ, psi0))) < 1e-12
 
 
+@pytest.mark.parametrize("n", [9, 10, 12, 17])
+@pytest.mark.parametrize("maker", ["random", "mixed"])
+def test_stage_op_lists_replay_at_other_widths(q, orc, maker, n):
+    """The host model of the stage kernels at tile widths below the default
+    (n = 9..12: fewer warp qubits than kmax asks for) and with tile qubits
+    up to qubit 16 (many tiles), against the oracle."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import stage_emulator
+    from test_gpu_fused import mixed_circuit
+    circ = inputs.random_circuit(n, 4, seed=n) if maker == "random" else mixed_circuit(n, seed=n, depth=3)
+    psi0 = inputs.gaussian_state(n, seed=1)
+    for kmax in (3, 4):
+        plan = q.Plan(circ, kmax=kmax, mode=q.FUSE_STAGED)
+        got = stage_emulator.run_plan(plan, circ, psi0, orc)
+        assert np.max(np.abs(got - orc.simulate(circ, psi0))) < 1e-12, (maker, n, kmax)
+
+
 def test_plan_block_only_for_greedy_plans(q):
     c = inputs.random_circuit(14, 3, seed=1)
     for mode, k in ((q.FUSE_STAGED, 3), (q.FUSE_TC, 6)):
